@@ -1,0 +1,177 @@
+/*
+ * mg.h -- C ABI of the GB300 (sm_103a) setup path of the chiral rank-k
+ * multigrid preconditioner for Wilson fermions (Whyte, Stathopoulos,
+ * Romero, arXiv:2502.03091, LATTICE2024).
+ *
+ * One level of the setup, as the paper states it:
+ *   mg_smooth_testvecs    smoother on D psi = 0 from m' random starts   (Sec. 2, Eq. 1)
+ *   mg_chiral_truncate    chiral split + per-block SVD, keep rank k    (Sec. 2 Eq. 2; Sec. 3 Eq. 4)
+ *   mg_build_prolongator  block-diagonal prolongator P, R = P^dagger   (Sec. 3 Eq. 5; Sec. 2)
+ *   mg_coarsen            Galerkin coarse operator D_c = R D P          (Sec. 2 Eq. 3)
+ *   mg_coarse_apply       D_c v on the coarse nearest-neighbour stencil (Sec. 2 Eq. 3; Sec. 1)
+ * plus the operator preparation mg_clover_field (the clover term of the
+ * ensembles of Sec. 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Memory.  Every array argument is a DEVICE pointer owned by the caller
+ *    (the library never allocates or frees device memory).  Scratch space is
+ *    passed in as (ws, ws_bytes); mg_workspace_size() gives the size.  A
+ *    NULL required pointer, or ws_bytes smaller than required, returns
+ *    MG_ERR_INVALID before anything is launched.
+ *  Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Calls only enqueue work on that stream and return;
+ *    outputs are valid once the stream reaches that point.
+ *  Errors.  Argument and shape checks happen synchronously and are returned.
+ *    Launch failures return MG_ERR_CUDA.  Numerical trouble found on the
+ *    device (non-positive Cholesky pivot) is reported per block in the
+ *    blk_flags output of mg_chiral_truncate.  mg_last_error() gives a
+ *    human-readable message for the calling thread's last failure.  No call
+ *    aborts the process; no exception crosses the ABI.
+ *  Numbers.  Complex numbers are interleaved (re, im).  MG_PREC_FP32 stores
+ *    every field as complex64 (float2); singular values are double.
+ *  Lattice.  Sites are lexicographic, s = x + Lx*(y + Ly*(z + Lz*t)),
+ *    periodic in all four directions.  Gamma matrices are in the chiral
+ *    basis gamma_mu = [[0, B_mu], [B_mu^dag, 0]], B_{x,y,z} = -i sigma_{1,2,3},
+ *    B_t = 1, so gamma_5 = diag(1, 1, -1, -1): chirality alpha = 0 is spins
+ *    {0, 1}, alpha = 1 is spins {2, 3}.
+ *  Operator.  r = 1 Wilson-clover with hop weights w = (1, 1, 1, 1/xi):
+ *    (D psi)(x) = (m0 + sum_mu w_mu) psi(x) + C(x) psi(x)
+ *                 - 1/2 sum_mu w_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                   + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ].
+ *  Blocks.  Aggregate Lambda_j has extents problem.block; its index j is the
+ *    lexicographic index of the coarse coordinate x / block; sites inside
+ *    a block are in local lexicographic order.
+ *
+ * Array layouts (element counts; V = volume, nb = |Lambda|, nblk = V / nb,
+ * m = n_vec, k = problem.k, nc = nblk):
+ *  U      [V][4 mu][3][3]                       links, U_mu(x) joins x -> x + mu
+ *  C      [V][2 alpha][6][6]                    clover, one Hermitian 6x6 per chirality,
+ *                                               row/col index = spin_in_chirality*3 + colour
+ *  psi    [V][4 spin][3 colour][m]              test vectors, right-hand sides fastest
+ *  Uk     [nblk][2 alpha][nb][2 spin][3 col][k] truncated left singular vectors
+ *  sigma  [nblk][2 alpha][k]                    retained singular values (double)
+ *  P      [V][2 alpha][2 spin][3 col][k]        prolongator per site; row (alpha, s, c) is
+ *                                               spin 2*alpha + s, column (alpha, i) is coarse
+ *                                               index alpha*k + i
+ *  X      [nc][2k][2k]                          coarse self coupling
+ *  Y      [nc][8][2k][2k]                       coarse hops, d = 0..3: to xc + mu_d,
+ *                                               d = 4..7: to xc - mu_{d-4}
+ *  v      [nc][2k][nrhs]                        coarse vectors
+ */
+#ifndef MG_H_
+#define MG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID = 1,     /* NULL pointer, bad parameter value, workspace too small */
+  MG_ERR_SHAPE = 2,       /* dims not divisible by block, k out of range, ... */
+  MG_ERR_NOMEM = 3,       /* reserved: the library itself never allocates */
+  MG_ERR_CUDA = 4,        /* a CUDA launch or runtime call failed */
+  MG_ERR_NUMERICAL = 5,   /* reserved for host-visible numerical failure */
+  MG_ERR_TIMEOUT = 6,     /* reserved for bounded device waits */
+  MG_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+} mg_status;
+
+typedef enum {
+  MG_PREC_FP32 = 0,  /* complex64 storage, FP32 arithmetic; FP64 for the small
+                        Cholesky / R-factor eigen problems */
+  MG_PREC_MIXED = 1  /* reserved: FP16 smoother storage, BF16 contractions */
+} mg_precision;
+
+typedef struct {
+  int32_t dims[4];    /* Lx, Ly, Lz, Lt */
+  int32_t block[4];   /* aggregate extents, each must divide dims[i] */
+  double m0;          /* bare mass */
+  double csw;         /* clover coefficient (used only by mg_clover_field) */
+  double xi;          /* anisotropy: temporal hop weight 1/xi (xi = 1 isotropic) */
+  int32_t n_vec;      /* m' test vectors; 4 <= m' <= 64, m' % 4 == 0, 6*nb >= m' */
+  int32_t k;          /* kept per chirality, 1 <= k <= m' */
+  int32_t mr_iters;   /* smoother iterations N >= 1 */
+  int32_t precision;  /* mg_precision */
+  uint64_t seed;      /* reserved (inputs are always passed in) */
+} mg_problem;
+
+/* Which call a workspace size is asked for. */
+typedef enum {
+  MG_CALL_SMOOTH = 0,
+  MG_CALL_TRUNCATE = 1,
+  MG_CALL_COARSEN = 2
+} mg_call;
+
+/* Bytes of scratch the call `which` (mg_call) needs for this problem; 0 for
+ * an invalid problem (mg_last_error() says why). */
+size_t mg_workspace_size(const mg_problem* prob, int which);
+
+/* Clover field of the ensembles' clover action (Sec. 4 of the paper; the
+ * normalisation is this library's reading):
+ *   C(x) = csw (i/2) sum_{mu<nu} sigma_mu_nu F_mu_nu(x),
+ *   sigma_mu_nu = (i/2)[gamma_mu, gamma_nu], F = (Q - Q^dag)/8,
+ * Q the sum of the four plaquette leaves in the mu-nu plane at x.
+ * In: U.  Out: C (layout above).  FP32 arithmetic. */
+mg_status mg_clover_field(const mg_problem* prob, const void* U, void* C, void* stream);
+
+/* Smoother on the homogeneous system D psi_i ~ 0 (Sec. 2, Eq. 1): minimal
+ * residual with one step length per vector, mr_iters iterations, starting
+ * from psi0, then every vector scaled to unit 2-norm.  In exact arithmetic:
+ *   r = -D psi; repeat N times { w = D r; a = <w,r>/<w,w>; psi += a r; r -= a w };
+ *   psi_i /= |psi_i|.
+ * In: U, C (NULL for pure Wilson), psi0.  Out: psi (may alias psi0).
+ * ws: mg_workspace_size(prob, MG_CALL_SMOOTH) bytes. */
+mg_status mg_smooth_testvecs(const mg_problem* prob, const void* U, const void* C,
+                             const void* psi0, void* psi, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/* Chiral split and rank-k truncation (Sec. 2 Eq. 2, Sec. 3 Eq. 4).  For
+ * every block Lambda_j and chirality alpha the 6*nb x m' matrix
+ * Psi^(alpha)(Lambda_j) (rows: site, spin in chirality, colour) is factored
+ * by CholeskyQR2 and the SVD of its m' x m' R factor; the k leading left
+ * singular vectors U_k and singular values Sigma_k are kept.
+ * In: psi.  Out: Uk, sigma (double), optional coarse_tv (NULL to skip):
+ * Sigma_k V_k^dag as [nblk][2][k][m'] complex64, and blk_flags[nblk*2]
+ * (int32; 0 = clean, bit 0 = Cholesky of the Gram needed a diagonal shift,
+ * bit 1 = the shifted Cholesky failed as well, results of that block are
+ * not meaningful).  ws: mg_workspace_size(prob, MG_CALL_TRUNCATE) bytes. */
+mg_status mg_chiral_truncate(const mg_problem* prob, const void* psi, void* Uk,
+                             double* sigma, void* coarse_tv, int32_t* blk_flags, void* ws,
+                             size_t ws_bytes, void* stream);
+
+/* Prolongator (Sec. 3, Eq. 5): P_{alpha i j}(x) = u_i^(alpha)(x) for x in
+ * Lambda_j, zero elsewhere; R = P^dagger is never stored.  Re-packs the
+ * block-major Uk into the site-major P.  In: Uk.  Out: P. */
+mg_status mg_build_prolongator(const mg_problem* prob, const void* Uk, void* P, void* stream);
+
+/* Galerkin coarse operator D_c = R D P, R = P^dagger (Sec. 2, Eq. 3), as the
+ * coarse nearest-neighbour stencil X, Y (layouts above).  Y for the -mu
+ * directions is obtained from gamma_5-hermiticity, Y_{-mu}(xc + mu) =
+ * sigma_3 Y_{+mu}(xc)^dag sigma_3 with sigma_3 = diag(1_k, -1_k).
+ * In: U, C (NULL for pure Wilson), P.  Out: X, Y.
+ * ws: mg_workspace_size(prob, MG_CALL_COARSEN) bytes (may be 0). */
+mg_status mg_coarsen(const mg_problem* prob, const void* U, const void* C, const void* P,
+                     void* X, void* Y, void* ws, size_t ws_bytes, void* stream);
+
+/* Coarse operator apply: out(xc) = X v(xc) + sum_{d<4} Y[d] v(xc + mu_d)
+ * + Y[4+d] v(xc - mu_d) on the periodic coarse lattice dims/block.
+ * In: X, Y, v_in [nc][2k][nrhs].  Out: v_out (must not alias v_in).
+ * 1 <= nrhs <= 64. */
+mg_status mg_coarse_apply(const mg_problem* prob, const void* X, const void* Y,
+                          const void* v_in, void* v_out, int32_t nrhs, void* stream);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char* mg_last_error(void);
+
+/* Library version string. */
+const char* mg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H_ */

@@ -1,0 +1,157 @@
+"""Seeded synthetic inputs for the chiral rank-k multigrid setup.
+
+This module is the only code shared by the FP64 oracle side (tests) and the
+CUDA side (tests, bench, server).  It draws random numbers and builds the
+inputs the method starts from; it holds none of the method's arithmetic
+(no Dirac operator, no smoother, no SVD, no coarsening).
+
+Random numbers (counter based, so any element can be drawn independently):
+  * SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+    generators", OOPSLA 2014) hashes (seed, stream, counter) to 64 bits.
+  * The top 53 bits give a uniform double in (0, 1).
+  * Box-Muller (Box & Muller, Ann. Math. Stat. 29, 1958) turns the uniform
+    pair with counters (2n, 2n+1) into normal number n (cosine branch).
+
+Inputs (the paper's ensembles are not available; these are stand-ins with
+the same shapes, see Sec. 4 of the paper for the lattices they mimic):
+  * gauge links U_mu(x) = exp(i eps H), H = sum_a h_a lambda_a / 2 with
+    h_a ~ N(0,1) i.i.d. and lambda_a the Gell-Mann matrices (traceless
+    Hermitian H, so U is in SU(3));
+  * complex Gaussian test-vector starts psi0 (the "m random initial guesses"
+    of Eq. (1) of the paper);
+  * random SU(3) gauge transformations (for covariance tests).
+
+Layouts (lexicographic site index s = x + Lx*(y + Ly*(z + Lz*t))):
+  U    complex128 [V][4 mu][3][3]          (U_mu(x) links x -> x + mu)
+  psi  complex128 [V][4 spin][3 colour][m] (right-hand sides fastest)
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_MASK = np.uint64(0xFFFFFFFFFFFFFFFF)
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# stream ids: independent sub-sequences per input kind
+STREAM_GAUGE = 1
+STREAM_PSI0 = 2
+STREAM_GAUGE_TRANSFORM = 3
+STREAM_COARSE_VEC = 4
+STREAM_MISC = 5
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser applied to x + golden gamma (uint64, wraps mod 2^64)."""
+    with np.errstate(over="ignore"):
+        z = (np.asarray(x, dtype=np.uint64) + _GOLDEN) & _MASK
+        z = ((z ^ (z >> np.uint64(30))) * _M1) & _MASK
+        z = ((z ^ (z >> np.uint64(27))) * _M2) & _MASK
+        return z ^ (z >> np.uint64(31))
+
+
+def stream_key(seed: int, stream: int) -> np.uint64:
+    """64-bit key of the (seed, stream) sub-sequence."""
+    s = splitmix64(np.array([stream], dtype=np.uint64))[0]
+    return splitmix64(np.array([np.uint64(seed & 0xFFFFFFFFFFFFFFFF) ^ s],
+                               dtype=np.uint64))[0]
+
+
+def uniforms(seed: int, stream: int, start: int, count: int) -> np.ndarray:
+    """Uniform doubles in (0, 1) for counters start .. start+count-1."""
+    key = stream_key(seed, stream)
+    ctr = np.arange(start, start + count, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        bits = splitmix64((ctr + key) & _MASK)
+    return ((bits >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def normals(seed: int, stream: int, start: int, count: int) -> np.ndarray:
+    """Standard normal doubles n_start .. n_{start+count-1} (Box-Muller, cosine branch)."""
+    u = uniforms(seed, stream, 2 * start, 2 * count).reshape(count, 2)
+    return np.sqrt(-2.0 * np.log(u[:, 0])) * np.cos(2.0 * np.pi * u[:, 1])
+
+
+def volume(dims) -> int:
+    return int(dims[0]) * int(dims[1]) * int(dims[2]) * int(dims[3])
+
+
+def gell_mann() -> np.ndarray:
+    """The eight Gell-Mann matrices, shape (8, 3, 3)."""
+    lam = np.zeros((8, 3, 3), dtype=np.complex128)
+    lam[0][0, 1] = lam[0][1, 0] = 1
+    lam[1][0, 1] = -1j
+    lam[1][1, 0] = 1j
+    lam[2][0, 0], lam[2][1, 1] = 1, -1
+    lam[3][0, 2] = lam[3][2, 0] = 1
+    lam[4][0, 2] = -1j
+    lam[4][2, 0] = 1j
+    lam[5][1, 2] = lam[5][2, 1] = 1
+    lam[6][1, 2] = -1j
+    lam[6][2, 1] = 1j
+    lam[7] = np.diag([1, 1, -2]) / np.sqrt(3.0)
+    return lam
+
+
+def _expi_hermitian(H: np.ndarray, eps) -> np.ndarray:
+    """exp(i eps H) for a batch of 3x3 Hermitian H, via the eigendecomposition."""
+    w, Q = np.linalg.eigh(H)
+    ph = np.exp(1j * np.asarray(eps)[..., None] * w)
+    return np.einsum("nij,nj,nkj->nik", Q, ph, Q.conj())
+
+
+def random_su3(seed: int, stream: int, n: int, eps, start: int = 0,
+               chunk: int = 1 << 20) -> np.ndarray:
+    """n SU(3) matrices exp(i eps H_j), H_j = sum_a h_{j,a} lambda_a / 2.
+
+    Matrix j uses normals 8*(start+j) .. 8*(start+j)+7 of the stream.  eps is a
+    scalar or an array of length n.
+    """
+    lam = gell_mann() / 2.0
+    out = np.empty((n, 3, 3), dtype=np.complex128)
+    eps_arr = np.broadcast_to(np.asarray(eps, dtype=np.float64), (n,))
+    for lo in range(0, n, chunk):
+        hi = min(n, lo + chunk)
+        h = normals(seed, stream, 8 * (start + lo), 8 * (hi - lo)).reshape(hi - lo, 8)
+        H = np.einsum("na,aij->nij", h, lam)
+        out[lo:hi] = _expi_hermitian(H, eps_arr[lo:hi])
+    return out
+
+
+def gauge_field(dims, eps: float, seed: int) -> np.ndarray:
+    """Random SU(3) gauge field U[V][4][3][3] (complex128), U_mu(x) = exp(i eps H)."""
+    V = volume(dims)
+    return random_su3(seed, STREAM_GAUGE, 4 * V, eps).reshape(V, 4, 3, 3)
+
+
+def unit_gauge_field(dims) -> np.ndarray:
+    """Free field: every link is the identity."""
+    V = volume(dims)
+    U = np.zeros((V, 4, 3, 3), dtype=np.complex128)
+    U[:, :, 0, 0] = U[:, :, 1, 1] = U[:, :, 2, 2] = 1.0
+    return U
+
+
+def gauge_transform(dims, seed: int, eps: float = 1.0) -> np.ndarray:
+    """Random site-local SU(3) matrices G[V][3][3]."""
+    return random_su3(seed, STREAM_GAUGE_TRANSFORM, volume(dims), eps)
+
+
+def psi0(dims, m: int, seed: int, stream: int = STREAM_PSI0) -> np.ndarray:
+    """m complex Gaussian vectors, layout [V][4][3][m]; re and im are N(0,1)."""
+    n = volume(dims) * 12 * m
+    g = normals(seed, stream, 0, 2 * n)
+    return (g[0::2] + 1j * g[1::2]).reshape(volume(dims), 4, 3, m)
+
+
+def coarse_vectors(n_coarse: int, two_k: int, nrhs: int, seed: int) -> np.ndarray:
+    """Complex Gaussian coarse vectors, layout [nc][2k][nrhs]."""
+    n = n_coarse * two_k * nrhs
+    g = normals(seed, STREAM_COARSE_VEC, 0, 2 * n)
+    return (g[0::2] + 1j * g[1::2]).reshape(n_coarse, two_k, nrhs)
+
+
+def round_to_c64(a: np.ndarray) -> np.ndarray:
+    """Round complex128 values to complex64 and back, so both sides see the same numbers."""
+    return np.asarray(a, dtype=np.complex64).astype(np.complex128)
