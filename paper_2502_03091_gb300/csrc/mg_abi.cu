@@ -1,0 +1,214 @@
+// mg_abi.cu -- the extern "C" entry points declared in include/mg.h:
+// argument validation, workspace layout and kernel dispatch.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "mg_common.cuh"
+
+namespace mg {
+
+namespace {
+thread_local char g_err[512] = "";
+
+mg_status fail(mg_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+mg_status cuda_status(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return MG_OK;
+  return fail(MG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Validate the problem and fill the geometry.
+mg_status make_geom(const mg_problem* p, Geom* g) {
+  if (!p) return fail(MG_ERR_INVALID, "problem is NULL");
+  long V = 1;
+  int nb = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (p->dims[i] < 1 || p->block[i] < 1)
+      return fail(MG_ERR_SHAPE, "dims and block extents must be >= 1");
+    if (p->dims[i] % p->block[i] != 0)
+      return fail(MG_ERR_SHAPE, "block extent %d does not divide lattice extent %d (direction %d)",
+                  p->block[i], p->dims[i], i);
+    V *= p->dims[i];
+    nb *= p->block[i];
+  }
+  if (V > (1L << 30)) return fail(MG_ERR_SHAPE, "volume %ld too large", V);
+  if (p->precision != MG_PREC_FP32)
+    return fail(MG_ERR_UNSUPPORTED, "precision %d not implemented", p->precision);
+  if (p->n_vec < 4 || p->n_vec > kMaxM || p->n_vec % 4 != 0)
+    return fail(MG_ERR_UNSUPPORTED, "n_vec must be a multiple of 4 in [4, %d], got %d", kMaxM,
+                p->n_vec);
+  if (6 * nb < p->n_vec)
+    return fail(MG_ERR_SHAPE, "block has 6*|Lambda| = %d rows < n_vec = %d", 6 * nb, p->n_vec);
+  if (p->k < 1 || p->k > p->n_vec || p->k > kMaxK)
+    return fail(MG_ERR_SHAPE, "k = %d must be in [1, min(n_vec, %d)]", p->k, kMaxK);
+  if (!(p->xi > 0)) return fail(MG_ERR_INVALID, "xi must be positive");
+  for (int i = 0; i < 4; ++i) {
+    g->L[i] = p->dims[i];
+    g->b[i] = p->block[i];
+    g->Lc[i] = p->dims[i] / p->block[i];
+  }
+  g->V = V;
+  g->nb = nb;
+  g->nblk = V / nb;
+  g->m = p->n_vec;
+  g->k = p->k;
+  g->niter = p->mr_iters;
+  g->m0 = p->m0;
+  g->xi = p->xi;
+  double wsum = 0;
+  for (int i = 0; i < 4; ++i) {
+    const double w = i == 3 ? 1.0 / p->xi : 1.0;
+    g->hw[i] = (float)(-0.5 * w);
+    wsum += w;
+  }
+  g->diag = (float)(p->m0 + wsum);
+  return MG_OK;
+}
+
+}  // namespace
+
+SmoothWs smooth_ws_layout(const Geom& g) {
+  SmoothWs w{};
+  const size_t field = sizeof(float2) * (size_t)g.V * 12 * g.m;
+  size_t o = 0;
+  w.ra = o; o = align256(o + field);
+  w.rb = o; o = align256(o + field);
+  w.wa = o; o = align256(o + field);
+  w.wb = o; o = align256(o + field);
+  w.part = o; o = align256(o + sizeof(double) * 4 * (size_t)kMaxPersistentGrid * g.m);
+  w.alpha = o; o = align256(o + sizeof(float2) * g.m);
+  w.scale = o; o = align256(o + sizeof(float) * g.m);
+  w.bytes = o;
+  return w;
+}
+
+TruncWs trunc_ws_layout(const Geom& g) {
+  TruncWs w{};
+  const size_t nbc = 2 * (size_t)g.nblk;
+  const size_t mm = (size_t)g.m * g.m;
+  size_t o = 0;
+  w.gram = o; o = align256(o + sizeof(double2) * nbc * mm);
+  w.r1 = o; o = align256(o + sizeof(double2) * nbc * mm);
+  w.z1 = o; o = align256(o + sizeof(float2) * nbc * mm);
+  w.w2 = o; o = align256(o + sizeof(float2) * nbc * g.m * g.k);
+  w.flags = o; o = align256(o + sizeof(int32_t) * nbc);
+  w.bytes = o;
+  return w;
+}
+
+}  // namespace mg
+
+using namespace mg;
+
+extern "C" {
+
+const char* mg_last_error(void) { return g_err; }
+
+const char* mg_version(void) { return "chiral-mg-gb300 0.1 (sm_103a)"; }
+
+size_t mg_workspace_size(const mg_problem* prob, int which) {
+  Geom g;
+  if (make_geom(prob, &g) != MG_OK) return 0;
+  switch (which) {
+    case MG_CALL_SMOOTH: return smooth_ws_layout(g).bytes;
+    case MG_CALL_TRUNCATE: return trunc_ws_layout(g).bytes;
+    case MG_CALL_COARSEN: return 0;
+    default: fail(MG_ERR_INVALID, "unknown call id %d", which); return 0;
+  }
+}
+
+mg_status mg_clover_field(const mg_problem* prob, const void* U, void* C, void* stream) {
+  Geom g;
+  mg_status st = make_geom(prob, &g);
+  if (st != MG_OK) return st;
+  if (!U || !C) return fail(MG_ERR_INVALID, "mg_clover_field: NULL array");
+  return cuda_status(launch_clover(g, prob->csw, static_cast<const float2*>(U),
+                                   static_cast<float2*>(C), static_cast<cudaStream_t>(stream)),
+                     "mg_clover_field");
+}
+
+mg_status mg_smooth_testvecs(const mg_problem* prob, const void* U, const void* C,
+                             const void* psi0, void* psi, void* ws, size_t ws_bytes,
+                             void* stream) {
+  Geom g;
+  mg_status st = make_geom(prob, &g);
+  if (st != MG_OK) return st;
+  if (g.niter < 1) return fail(MG_ERR_INVALID, "mr_iters must be >= 1");
+  if (!U || !psi0 || !psi || !ws) return fail(MG_ERR_INVALID, "mg_smooth_testvecs: NULL array");
+  const size_t need = smooth_ws_layout(g).bytes;
+  if (ws_bytes < need)
+    return fail(MG_ERR_INVALID, "mg_smooth_testvecs: workspace %zu < %zu bytes", ws_bytes, need);
+  return cuda_status(launch_smoother(g, static_cast<const float2*>(U),
+                                     static_cast<const float2*>(C),
+                                     static_cast<const float2*>(psi0), static_cast<float2*>(psi),
+                                     static_cast<char*>(ws), static_cast<cudaStream_t>(stream)),
+                     "mg_smooth_testvecs");
+}
+
+mg_status mg_chiral_truncate(const mg_problem* prob, const void* psi, void* Uk, double* sigma,
+                             void* coarse_tv, int32_t* blk_flags, void* ws, size_t ws_bytes,
+                             void* stream) {
+  Geom g;
+  mg_status st = make_geom(prob, &g);
+  if (st != MG_OK) return st;
+  if (!psi || !Uk || !sigma || !blk_flags || !ws)
+    return fail(MG_ERR_INVALID, "mg_chiral_truncate: NULL array");
+  const size_t need = trunc_ws_layout(g).bytes;
+  if (ws_bytes < need)
+    return fail(MG_ERR_INVALID, "mg_chiral_truncate: workspace %zu < %zu bytes", ws_bytes, need);
+  return cuda_status(
+      launch_truncate(g, static_cast<const float2*>(psi), static_cast<float2*>(Uk), sigma,
+                      static_cast<float2*>(coarse_tv), blk_flags, static_cast<char*>(ws),
+                      static_cast<cudaStream_t>(stream)),
+      "mg_chiral_truncate");
+}
+
+mg_status mg_build_prolongator(const mg_problem* prob, const void* Uk, void* P, void* stream) {
+  Geom g;
+  mg_status st = make_geom(prob, &g);
+  if (st != MG_OK) return st;
+  if (!Uk || !P) return fail(MG_ERR_INVALID, "mg_build_prolongator: NULL array");
+  return cuda_status(launch_prolongator(g, static_cast<const float2*>(Uk),
+                                        static_cast<float2*>(P), static_cast<cudaStream_t>(stream)),
+                     "mg_build_prolongator");
+}
+
+mg_status mg_coarsen(const mg_problem* prob, const void* U, const void* C, const void* P,
+                     void* X, void* Y, void* ws, size_t ws_bytes, void* stream) {
+  (void)ws;
+  (void)ws_bytes;
+  Geom g;
+  mg_status st = make_geom(prob, &g);
+  if (st != MG_OK) return st;
+  if (!U || !P || !X || !Y) return fail(MG_ERR_INVALID, "mg_coarsen: NULL array");
+  return cuda_status(launch_coarsen(g, static_cast<const float2*>(U),
+                                    static_cast<const float2*>(C), static_cast<const float2*>(P),
+                                    static_cast<float2*>(X), static_cast<float2*>(Y),
+                                    static_cast<cudaStream_t>(stream)),
+                     "mg_coarsen");
+}
+
+mg_status mg_coarse_apply(const mg_problem* prob, const void* X, const void* Y,
+                          const void* v_in, void* v_out, int32_t nrhs, void* stream) {
+  Geom g;
+  mg_status st = make_geom(prob, &g);
+  if (st != MG_OK) return st;
+  if (!X || !Y || !v_in || !v_out) return fail(MG_ERR_INVALID, "mg_coarse_apply: NULL array");
+  if (nrhs < 1 || nrhs > 64) return fail(MG_ERR_INVALID, "nrhs = %d must be in [1, 64]", nrhs);
+  if (v_in == v_out) return fail(MG_ERR_INVALID, "mg_coarse_apply: v_out aliases v_in");
+  return cuda_status(launch_coarse_apply(g, static_cast<const float2*>(X),
+                                         static_cast<const float2*>(Y),
+                                         static_cast<const float2*>(v_in),
+                                         static_cast<float2*>(v_out), nrhs,
+                                         static_cast<cudaStream_t>(stream)),
+                     "mg_coarse_apply");
+}
+
+}  // extern "C"

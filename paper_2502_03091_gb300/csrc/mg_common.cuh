@@ -1,0 +1,120 @@
+// mg_common.cuh -- internal definitions shared by the CUDA translation units
+// of the chiral rank-k multigrid setup (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mg.h"
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// problem geometry, validated on the host
+// ---------------------------------------------------------------------------
+struct Geom {
+  int L[4];       // fine extents
+  int b[4];       // block extents
+  int Lc[4];      // coarse extents
+  long V;         // fine volume
+  int nb;         // sites per block
+  long nblk;      // number of blocks = coarse volume
+  int m;          // test vectors m'
+  int k;          // kept per chirality
+  int niter;      // smoother iterations
+  double m0, xi;  // mass, anisotropy
+  float hw[4];    // hop weights -1/2 w_mu
+  float diag;     // m0 + sum_mu w_mu
+};
+
+// Largest grid of the persistent smoother kernels (bounds the partial-sum
+// scratch).
+constexpr int kMaxPersistentGrid = 2048;
+constexpr int kMaxM = 64;  // largest m' this build supports
+constexpr int kMaxK = 32;  // largest k this build supports
+
+// ---------------------------------------------------------------------------
+// workspace layout (byte offsets, 256-aligned), see mg_abi.cu
+// ---------------------------------------------------------------------------
+struct SmoothWs {
+  size_t ra, rb, wa, wb, part, alpha, scale, bytes;
+};
+struct TruncWs {
+  size_t gram, r1, z1, w2, flags, bytes;
+};
+
+SmoothWs smooth_ws_layout(const Geom& g);
+TruncWs trunc_ws_layout(const Geom& g);
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in the .cu files); each returns cudaGetLastError()
+// ---------------------------------------------------------------------------
+cudaError_t launch_clover(const Geom& g, double csw, const float2* U, float2* C,
+                          cudaStream_t s);
+
+cudaError_t launch_smoother(const Geom& g, const float2* U, const float2* C,
+                            const float2* psi0, float2* psi, char* ws, cudaStream_t s);
+
+cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double* sigma,
+                            float2* coarse_tv, int32_t* flags, char* ws, cudaStream_t s);
+
+cudaError_t launch_prolongator(const Geom& g, const float2* Uk, float2* P, cudaStream_t s);
+
+cudaError_t launch_coarsen(const Geom& g, const float2* U, const float2* C, const float2* P,
+                           float2* X, float2* Y, cudaStream_t s);
+
+cudaError_t launch_coarse_apply(const Geom& g, const float2* X, const float2* Y,
+                                const float2* vin, float2* vout, int nrhs, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// small complex helpers (float2 / double2 as complex numbers)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
+  return make_float2(a.x * s, a.y * s);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// acc += a * b
+__host__ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+// acc += conj(a) * b
+__host__ __device__ __forceinline__ void cfmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
+}
+
+__host__ __device__ __forceinline__ double2 zadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ double2 zsub(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 zmulc(double2 a, double2 b) {  // conj(a) b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 zscale(double2 a, double s) {
+  return make_double2(a.x * s, a.y * s);
+}
+__host__ __device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double zabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+}  // namespace mg

@@ -1,0 +1,324 @@
+"""ctypes binding of libmg.so (include/mg.h).
+
+Argument marshalling only: every step of the setup runs in the CUDA kernels
+behind the C ABI.  Device arrays are torch tensors (complex64 / float64 /
+int32, contiguous, on the current CUDA device); the current torch stream is
+passed to the library unless a stream is given.  If the library is missing
+or a call fails, an exception is raised -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmg.so")
+
+MG_OK = 0
+STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_SHAPE", 3: "MG_ERR_NOMEM",
+                4: "MG_ERR_CUDA", 5: "MG_ERR_NUMERICAL", 6: "MG_ERR_TIMEOUT",
+                7: "MG_ERR_UNSUPPORTED"}
+MG_PREC_FP32 = 0
+MG_PREC_MIXED = 1
+MG_CALL_SMOOTH, MG_CALL_TRUNCATE, MG_CALL_COARSEN = 0, 1, 2
+
+# every symbol include/mg.h declares
+EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_smooth_testvecs", "mg_chiral_truncate",
+           "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply", "mg_last_error",
+           "mg_version")
+
+
+class MgError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 4), ("block", ctypes.c_int32 * 4),
+                ("m0", ctypes.c_double), ("csw", ctypes.c_double), ("xi", ctypes.c_double),
+                ("n_vec", ctypes.c_int32), ("k", ctypes.c_int32), ("mr_iters", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+@dataclass
+class Problem:
+    """Python mirror of mg_problem."""
+    dims: Sequence[int]
+    block: Sequence[int]
+    m0: float
+    n_vec: int
+    k: int
+    mr_iters: int
+    csw: float = 0.0
+    xi: float = 1.0
+    precision: int = MG_PREC_FP32
+    seed: int = 0
+
+    def c(self) -> _Problem:
+        p = _Problem()
+        p.dims[:] = [int(v) for v in self.dims]
+        p.block[:] = [int(v) for v in self.block]
+        p.m0, p.csw, p.xi = float(self.m0), float(self.csw), float(self.xi)
+        p.n_vec, p.k, p.mr_iters = int(self.n_vec), int(self.k), int(self.mr_iters)
+        p.precision, p.seed = int(self.precision), int(self.seed)
+        return p
+
+    # derived sizes
+    @property
+    def volume(self) -> int:
+        v = 1
+        for d in self.dims:
+            v *= int(d)
+        return v
+
+    @property
+    def block_volume(self) -> int:
+        v = 1
+        for d in self.block:
+            v *= int(d)
+        return v
+
+    @property
+    def coarse_dims(self):
+        return [int(self.dims[i]) // int(self.block[i]) for i in range(4)]
+
+    @property
+    def n_blocks(self) -> int:
+        return self.volume // self.block_volume
+
+
+_lib = None
+
+
+def library(path: str = LIB_PATH):
+    """Load libmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with `python -m paper_2502_03091_gb300.build`")
+    lib = ctypes.CDLL(path)
+    P, Pp = ctypes.c_void_p, ctypes.POINTER(_Problem)
+    lib.mg_workspace_size.argtypes = [Pp, ctypes.c_int]
+    lib.mg_workspace_size.restype = ctypes.c_size_t
+    lib.mg_clover_field.argtypes = [Pp, P, P, P]
+    lib.mg_smooth_testvecs.argtypes = [Pp, P, P, P, P, P, ctypes.c_size_t, P]
+    lib.mg_chiral_truncate.argtypes = [Pp, P, P, P, P, P, P, ctypes.c_size_t, P]
+    lib.mg_build_prolongator.argtypes = [Pp, P, P, P]
+    lib.mg_coarsen.argtypes = [Pp, P, P, P, P, P, P, ctypes.c_size_t, P]
+    lib.mg_coarse_apply.argtypes = [Pp, P, P, P, P, ctypes.c_int32, P]
+    for f in ("mg_clover_field", "mg_smooth_testvecs", "mg_chiral_truncate",
+              "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply"):
+        getattr(lib, f).restype = ctypes.c_int
+    lib.mg_last_error.restype = ctypes.c_char_p
+    lib.mg_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != MG_OK:
+        raise MgError(st, library().mg_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+
+
+def _expect(t, shape, dtype, name):
+    if t is None:
+        return
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype} != {dtype}")
+
+
+def version() -> str:
+    return library().mg_version().decode()
+
+
+def mg_workspace_size(prob: Problem, which: int) -> int:
+    pc = prob.c()
+    n = library().mg_workspace_size(ctypes.byref(pc), which)
+    if n == 0 and which != MG_CALL_COARSEN:
+        raise MgError(1, library().mg_last_error().decode())
+    return int(n)
+
+
+def workspace(prob: Problem, which: int, device=None):
+    """A uint8 CUDA tensor of mg_workspace_size(prob, which) bytes (at least 256)."""
+    import torch
+    return torch.empty(max(256, mg_workspace_size(prob, which)), dtype=torch.uint8,
+                       device=device or "cuda")
+
+
+# ---------------------------------------------------------------------------
+# shapes of the ABI arrays
+# ---------------------------------------------------------------------------
+def shape_U(p: Problem):
+    return (p.volume, 4, 3, 3)
+
+
+def shape_C(p: Problem):
+    return (p.volume, 2, 6, 6)
+
+
+def shape_psi(p: Problem):
+    return (p.volume, 4, 3, p.n_vec)
+
+
+def shape_Uk(p: Problem):
+    return (p.n_blocks, 2, p.block_volume, 2, 3, p.k)
+
+
+def shape_sigma(p: Problem):
+    return (p.n_blocks, 2, p.k)
+
+
+def shape_P(p: Problem):
+    return (p.volume, 2, 2, 3, p.k)
+
+
+def shape_X(p: Problem):
+    return (p.n_blocks, 2 * p.k, 2 * p.k)
+
+
+def shape_Y(p: Problem):
+    return (p.n_blocks, 8, 2 * p.k, 2 * p.k)
+
+
+# ---------------------------------------------------------------------------
+# the ABI calls
+# ---------------------------------------------------------------------------
+def mg_clover_field(prob: Problem, U, C, stream=None):
+    import torch
+    _expect(U, shape_U(prob), torch.complex64, "U")
+    _expect(C, shape_C(prob), torch.complex64, "C")
+    pc = prob.c()
+    _check(library().mg_clover_field(ctypes.byref(pc), _ptr(U), _ptr(C), _stream(stream)))
+
+
+def mg_smooth_testvecs(prob: Problem, U, C, psi0, psi, ws, stream=None):
+    import torch
+    _expect(U, shape_U(prob), torch.complex64, "U")
+    _expect(C, shape_C(prob), torch.complex64, "C")
+    _expect(psi0, shape_psi(prob), torch.complex64, "psi0")
+    _expect(psi, shape_psi(prob), torch.complex64, "psi")
+    pc = prob.c()
+    _check(library().mg_smooth_testvecs(ctypes.byref(pc), _ptr(U), _ptr(C), _ptr(psi0), _ptr(psi),
+                                        _ptr(ws), ws.numel() * ws.element_size(),
+                                        _stream(stream)))
+
+
+def mg_chiral_truncate(prob: Problem, psi, Uk, sigma, coarse_tv, blk_flags, ws, stream=None):
+    import torch
+    _expect(psi, shape_psi(prob), torch.complex64, "psi")
+    _expect(Uk, shape_Uk(prob), torch.complex64, "Uk")
+    _expect(sigma, shape_sigma(prob), torch.float64, "sigma")
+    _expect(coarse_tv, (prob.n_blocks, 2, prob.k, prob.n_vec), torch.complex64, "coarse_tv")
+    _expect(blk_flags, (prob.n_blocks, 2), torch.int32, "blk_flags")
+    pc = prob.c()
+    _check(library().mg_chiral_truncate(ctypes.byref(pc), _ptr(psi), _ptr(Uk), _ptr(sigma),
+                                        _ptr(coarse_tv), _ptr(blk_flags), _ptr(ws),
+                                        ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def mg_build_prolongator(prob: Problem, Uk, P, stream=None):
+    import torch
+    _expect(Uk, shape_Uk(prob), torch.complex64, "Uk")
+    _expect(P, shape_P(prob), torch.complex64, "P")
+    pc = prob.c()
+    _check(library().mg_build_prolongator(ctypes.byref(pc), _ptr(Uk), _ptr(P), _stream(stream)))
+
+
+def mg_coarsen(prob: Problem, U, C, P, X, Y, ws=None, stream=None):
+    import torch
+    _expect(U, shape_U(prob), torch.complex64, "U")
+    _expect(C, shape_C(prob), torch.complex64, "C")
+    _expect(P, shape_P(prob), torch.complex64, "P")
+    _expect(X, shape_X(prob), torch.complex64, "X")
+    _expect(Y, shape_Y(prob), torch.complex64, "Y")
+    pc = prob.c()
+    nbytes = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(library().mg_coarsen(ctypes.byref(pc), _ptr(U), _ptr(C), _ptr(P), _ptr(X), _ptr(Y),
+                                _ptr(ws), nbytes, _stream(stream)))
+
+
+def mg_coarse_apply(prob: Problem, X, Y, v_in, v_out, stream=None):
+    import torch
+    nrhs = int(v_in.shape[-1])
+    _expect(X, shape_X(prob), torch.complex64, "X")
+    _expect(Y, shape_Y(prob), torch.complex64, "Y")
+    _expect(v_in, (prob.n_blocks, 2 * prob.k, nrhs), torch.complex64, "v_in")
+    _expect(v_out, (prob.n_blocks, 2 * prob.k, nrhs), torch.complex64, "v_out")
+    pc = prob.c()
+    _check(library().mg_coarse_apply(ctypes.byref(pc), _ptr(X), _ptr(Y), _ptr(v_in), _ptr(v_out),
+                                     nrhs, _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# one level of the setup, buffers owned by torch
+# ---------------------------------------------------------------------------
+@dataclass
+class Level:
+    """Device buffers of one setup level (inputs, outputs and scratch)."""
+    prob: Problem
+    U: object
+    C: object
+    psi0: object
+    psi: object = None
+    Uk: object = None
+    sigma: object = None
+    flags: object = None
+    P: object = None
+    X: object = None
+    Y: object = None
+    ws_smooth: object = None
+    ws_trunc: object = None
+    coarse_tv: object = None
+    extra: dict = field(default_factory=dict)
+
+    @classmethod
+    def allocate(cls, prob: Problem, U, C, psi0, want_coarse_tv: bool = False):
+        import torch
+        dev = U.device
+        c64 = torch.complex64
+        lv = cls(prob, U, C, psi0)
+        lv.psi = torch.empty(shape_psi(prob), dtype=c64, device=dev)
+        lv.Uk = torch.empty(shape_Uk(prob), dtype=c64, device=dev)
+        lv.sigma = torch.empty(shape_sigma(prob), dtype=torch.float64, device=dev)
+        lv.flags = torch.empty((prob.n_blocks, 2), dtype=torch.int32, device=dev)
+        lv.P = torch.empty(shape_P(prob), dtype=c64, device=dev)
+        lv.X = torch.empty(shape_X(prob), dtype=c64, device=dev)
+        lv.Y = torch.empty(shape_Y(prob), dtype=c64, device=dev)
+        lv.ws_smooth = workspace(prob, MG_CALL_SMOOTH, dev)
+        lv.ws_trunc = workspace(prob, MG_CALL_TRUNCATE, dev)
+        if want_coarse_tv:
+            lv.coarse_tv = torch.empty((prob.n_blocks, 2, prob.k, prob.n_vec), dtype=c64,
+                                       device=dev)
+        return lv
+
+    def run(self, stream=None):
+        """Smoother -> chiral truncation -> prolongator -> coarse operator."""
+        p = self.prob
+        mg_smooth_testvecs(p, self.U, self.C, self.psi0, self.psi, self.ws_smooth, stream)
+        mg_chiral_truncate(p, self.psi, self.Uk, self.sigma, self.coarse_tv, self.flags,
+                           self.ws_trunc, stream)
+        mg_build_prolongator(p, self.Uk, self.P, stream)
+        mg_coarsen(p, self.U, self.C, self.P, self.X, self.Y, None, stream)
