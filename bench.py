@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of one setup level of the chiral rank-k multigrid (arXiv:2502.03091)
+on the 32^3x64 anisotropic workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one pass of the whole setup path through the C ABI on inputs that
+are already resident in HBM: MR smoother (20 iterations, m' = 64) -> chiral
+split + rank-24 truncation -> prolongator -> Galerkin coarse operator -> one
+coarse apply (8 right-hand sides).  The metric is seconds per setup level
+(lower is better).  Printed as one JSON line by rank 0.
+
+Multi-GPU: every rank builds its own level (independent replicas, no
+data-path collective); value = (max over ranks of the time per step) / N.
+
+--impl reference times the FP64 CPU oracle (the checker of this project) on
+the host cores, on a bounded sub-lattice sample of the same workload, scaled
+to the full lattice.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MG setup s/level at 32^3x64, mixed vs FP32 plain; dslash HBM GB/s; p50/p99 setup"
+UNIT = "s/level"
+
+
+def _m0_table():
+    with open(os.path.join(ROOT, "tests", "golden", "m0.json")) as fh:
+        return {k: v["m0"] for k, v in json.load(fh)["workloads"].items()}
+
+
+def workload(name: str):
+    m0 = _m0_table()
+    if name == "32^3x64":
+        return dict(workload="32^3x64 anisotropic (xi=3.5) Wilson, eps=0.2, m'=64, k=24, "
+                             "4^3x8 aggregates, 20 MR iterations, FP32 plain path",
+                    dims=[32, 32, 32, 64], block=[4, 4, 4, 8], eps=0.2, csw=0.0, xi=3.5,
+                    m=64, k=24, N=20, m0=m0["32^3x64 aniso xi=3.5 eps=0.2"], gauge_seed=20,
+                    psi_seed=21, sample_dims=[8, 8, 8, 16])
+    if name == "16^3x32":
+        return dict(workload="16^3x32 Wilson-clover c_sw=1, eps=0.25, m'=48, k=24, 4^4 "
+                             "aggregates, 20 MR iterations, FP32 plain path",
+                    dims=[16, 16, 16, 32], block=[4, 4, 4, 4], eps=0.25, csw=1.0, xi=1.0,
+                    m=48, k=24, N=20, m0=m0["16^3x32 Wilson-clover eps=0.25"], gauge_seed=10,
+                    psi_seed=11, sample_dims=[8, 8, 8, 8])
+    raise SystemExit(f"unknown workload {name}")
+
+
+def vol(d):
+    return int(d[0]) * int(d[1]) * int(d[2]) * int(d[3])
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per kernel launch (what the method must move)
+# ---------------------------------------------------------------------------
+def fused_mr_bytes(w):
+    """One MR iteration pass: read r, w, psi and write r, w, psi (6 x 96 B per
+    site and right-hand side in complex64), plus the 4 links per site (288 B)
+    and, with clover, 72 reals per site (288 B)."""
+    per_site = 6 * 96 * w["m"] + 288 + (288 if w["csw"] else 0)
+    return vol(w["dims"]) * per_site
+
+
+def dslash_bytes(w):
+    """One plain dslash: read 12 + write 12 complex64 per site and right-hand
+    side (192 B), plus links (288 B) and clover (288 B) per site."""
+    per_site = 192 * w["m"] + 288 + (288 if w["csw"] else 0)
+    return vol(w["dims"]) * per_site
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(w):
+    """Runs the FP64 oracle's whole setup level on the sample sub-lattice (same
+    m', k, N, aggregate shape); returns (seconds, scale to the full lattice,
+    threads, description).  Every stage's cost grows linearly with the volume
+    (MR: sites x m'; truncation: aggregates; coarsening: sites)."""
+    import mg_inputs as G
+    import oracle as O
+    d = w["sample_dims"]
+    U = G.gauge_field(d, w["eps"], w["gauge_seed"])
+    C = O.clover(d, U, w["csw"]) if w["csw"] else None
+    p0 = G.psi0(d, w["m"], w["psi_seed"])
+    t0 = time.perf_counter()
+    psi = O.mr(d, w["m0"], w["xi"], U, C, p0, w["N"])
+    Uk, sig = O.chiral_truncate(d, w["block"], psi, w["k"])
+    P = O.prolongator(d, w["block"], Uk)
+    X, Y = O.coarsen(d, w["block"], w["m0"], w["xi"], U, C, P)
+    v = G.coarse_vectors(X.shape[0], 2 * w["k"], 8, 1)
+    O.coarse_apply(O.coarse_dims(d, w["block"]), X, Y, v)
+    dt = time.perf_counter() - t0
+    scale = vol(w["dims"]) / vol(d)
+    threads = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    desc = (f"oracle setup level on a {'x'.join(map(str, d))} sub-lattice "
+            f"(1/{int(scale)} of the volume; same m', k, N, aggregates), time x {int(scale)}")
+    return dt, scale, threads, desc
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_sample(w)
+    times = []
+    for _ in range(args.steps):
+        dt, scale, threads, desc = oracle_sample(w)
+        times.append(dt * scale)
+    v = sum(times) / len(times)
+    cfg = config_of(w, args)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+        flush=True)
+
+
+def config_of(w, args):
+    return {"workload": w["workload"], "dims": w["dims"], "aggregate": w["block"],
+            "n_vec": w["m"], "k": w["k"], "mr_iters": w["N"], "xi": w["xi"], "eps": w["eps"],
+            "c_sw": w["csw"], "m0": w["m0"], "precision": "fp32 (complex64), fp64 small eig",
+            "global_batch": args.gpus, "parallelism": f"replicas x{args.gpus}",
+            "l2": "inputs larger than L2 (psi0 alone is "
+                  f"{vol(w['dims']) * 12 * w['m'] * 8 / 1e9:.1f} GB)"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, w):
+    import numpy as np
+    import torch
+
+    import mg_inputs as G
+    from paper_2502_03091_gb300 import build as B
+    from paper_2502_03091_gb300 import mg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    mg.library()
+
+    prob = mg.Problem(dims=w["dims"], block=w["block"], m0=w["m0"], n_vec=w["m"], k=w["k"],
+                      mr_iters=w["N"], csw=w["csw"], xi=w["xi"])
+    # inputs: links from the shared seeded generator (host), starts drawn on the
+    # device (a seeded complex Gaussian; 12.9 GB is too large to draw on the host)
+    U_host = torch.from_numpy(G.gauge_field(w["dims"], w["eps"], w["gauge_seed"])
+                              .astype(np.complex64)).pin_memory()
+    U = U_host.cuda()
+    gen = torch.Generator(device="cuda").manual_seed(w["psi_seed"])
+    psi0 = torch.complex(torch.randn(mg.shape_psi(prob), device="cuda", generator=gen),
+                         torch.randn(mg.shape_psi(prob), device="cuda", generator=gen))
+    C = None
+    if w["csw"]:
+        C = torch.empty(mg.shape_C(prob), dtype=torch.complex64, device="cuda")
+        mg.mg_clover_field(prob, U, C)
+    lv = mg.Level.allocate(prob, U, C, psi0)
+    v_in = torch.ones((prob.n_blocks, 2 * prob.k, 8), dtype=torch.complex64, device="cuda")
+    v_out = torch.empty_like(v_in)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lv.run(stream)
+        mg.mg_coarse_apply(prob, lv.X, lv.Y, v_in, v_out, stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    flags = lv.flags.cpu().numpy()
+
+    # ---- device-resident timed region ----
+    sampler = ClockSampler(local)
+    sampler.start()
+    mg.mg_timing_enable(True)
+    mg.mg_timing_read()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    kern = mg.mg_timing_read()
+    mg.mg_timing_enable(False)
+    clocks = sampler.stop()
+    ms = max_over_ranks(ms)
+
+    # ---- end to end through the public API with host buffers ----
+    psi0_host = torch.empty(psi0.shape, dtype=psi0.dtype, pin_memory=True)
+    psi0_host.copy_(psi0)
+    X_host = torch.empty(lv.X.shape, dtype=lv.X.dtype, pin_memory=True)
+    Y_host = torch.empty(lv.Y.shape, dtype=lv.Y.dtype, pin_memory=True)
+    s_host = torch.empty(lv.sigma.shape, dtype=lv.sigma.dtype, pin_memory=True)
+    h2d = U_host.numel() * 8 + psi0_host.numel() * 8
+    d2h = X_host.numel() * 8 + Y_host.numel() * 8 + s_host.numel() * 8
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        lv.U.copy_(U_host, non_blocking=True)
+        lv.psi0.copy_(psi0_host, non_blocking=True)
+        step()
+        X_host.copy_(lv.X, non_blocking=True)
+        Y_host.copy_(lv.Y, non_blocking=True)
+        s_host.copy_(lv.sigma, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ----
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            peaks = json.load(fh)
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    stages = {n: {"launches": l, "ms_per_step": t / args.steps, "ms_per_launch": t / max(l, 1)}
+              for n, (l, t) in kern.items()}
+    top = max(kern.items(), key=lambda kv: kv[1][1])[0]
+    fl, ft = kern["mr_fused_iteration"]
+    achieved = fused_mr_bytes(w) / (ft / fl * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "mr_fused_iteration_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as fh:
+            pj = json.load(fh)
+        if pj.get("source_sha1") == _kernel_sha1() and pj.get("workload") == w["workload"]:
+            traffic = pj.get("dram_bytes_per_launch")
+    dl, dt = kern["mr_neg_dslash"]
+    dslash_gbs = dslash_bytes(w) / (dt / dl * 1e-3) / 1e9
+    launches = sum(l for l, _ in kern.values())
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        dt_s, scale, threads, desc = oracle_sample(w)
+        cpu = {"value": dt_s * scale, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": desc}
+
+    out = {
+        "metric": METRIC, "value": ms / 1e3 / world, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded random SU(3) links, Gaussian starts)",
+        "config": config_of(w, args),
+        "roofline": {"kernel": "mr_fused_iteration", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": f"{peak_src} hbm_gbs", "traffic": traffic,
+                     "algorithmic_bytes_per_launch": fused_mr_bytes(w)},
+        "dslash": {"kernel": "mr_neg_dslash", "gbs": dslash_gbs, "frac": dslash_gbs / hbm,
+                   "algorithmic_bytes_per_launch": dslash_bytes(w)},
+        "top_kernel": top,
+        "stages": stages,
+        "gpu_launches": launches,
+        "blk_flags_nonzero": int((flags != 0).sum()),
+        "clocks": clocks,
+        "e2e": {"value": e2e_ms / 1e3 / world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _kernel_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    with open(os.path.join(ROOT, "paper_2502_03091_gb300", "csrc", "mg_dslash.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="32^3x64", choices=["32^3x64", "16^3x32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,23 @@ mg_status mg_coarsen(const mg_problem* prob, const void* U, const void* C, const
 mg_status mg_coarse_apply(const mg_problem* prob, const void* X, const void* Y,
                           const void* v_in, void* v_out, int32_t nrhs, void* stream);
 
+/* Per-kernel timing (measurement aid; no counterpart in the paper).  While
+ * enabled, every kernel the library launches is bracketed by two CUDA events
+ * recorded on the launching stream.  mg_timing_read waits for the recorded
+ * events, writes up to `max` entries (one per kernel kind: name, number of
+ * launches, summed milliseconds) accumulated since the previous read, resets
+ * the accumulators and returns the number of entries written (or -1 on a CUDA
+ * error).  Events come from a pool owned by the library (CUDA events, not
+ * device memory). */
+typedef struct {
+  char name[48];
+  int64_t launches;
+  double ms;
+} mg_timing_entry;
+
+mg_status mg_timing_enable(int on);
+int mg_timing_read(mg_timing_entry* out, int max);
+
 /* Message describing the calling thread's most recent failure ("" if none). */
 const char* mg_last_error(void);
 

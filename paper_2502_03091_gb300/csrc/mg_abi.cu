@@ -3,6 +3,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include "mg_common.cuh"
 
@@ -103,11 +108,108 @@ TruncWs trunc_ws_layout(const Geom& g) {
   return w;
 }
 
+// ---------------------------------------------------------------------------
+// per-kernel timing
+// ---------------------------------------------------------------------------
+namespace {
+struct TimingRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+struct TimingState {
+  std::mutex mu;
+  std::atomic<bool> on{false};
+  std::vector<std::string> kinds;
+  std::vector<int64_t> launches;
+  std::vector<double> ms;
+  std::vector<TimingRec> pending;
+  std::vector<cudaEvent_t> pool;
+};
+TimingState& timing() {
+  static TimingState* t = new TimingState();  // never destroyed: safe at exit
+  return *t;
+}
+cudaEvent_t pool_get(TimingState& t) {
+  if (!t.pool.empty()) {
+    cudaEvent_t e = t.pool.back();
+    t.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+int timing_begin(const char* name, cudaStream_t s) {
+  TimingState& t = timing();
+  if (!t.on.load(std::memory_order_relaxed)) return -1;
+  std::lock_guard<std::mutex> g(t.mu);
+  int kind = -1;
+  for (size_t i = 0; i < t.kinds.size(); ++i)
+    if (t.kinds[i] == name) kind = (int)i;
+  if (kind < 0) {
+    kind = (int)t.kinds.size();
+    t.kinds.emplace_back(name);
+    t.launches.push_back(0);
+    t.ms.push_back(0.0);
+  }
+  TimingRec r{kind, pool_get(t), pool_get(t)};
+  cudaEventRecord(r.a, s);
+  t.pending.push_back(r);
+  return (int)t.pending.size() - 1;
+}
+
+void timing_end(int token, cudaStream_t s) {
+  if (token < 0) return;
+  TimingState& t = timing();
+  std::lock_guard<std::mutex> g(t.mu);
+  if (token < (int)t.pending.size()) cudaEventRecord(t.pending[token].b, s);
+}
+
 }  // namespace mg
 
 using namespace mg;
 
 extern "C" {
+
+mg_status mg_timing_enable(int on) {
+  timing().on.store(on != 0);
+  return MG_OK;
+}
+
+int mg_timing_read(mg_timing_entry* out, int max) {
+  TimingState& t = timing();
+  std::lock_guard<std::mutex> g(t.mu);
+  bool ok = true;
+  for (const TimingRec& r : t.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+      ok = false;
+    t.ms[r.kind] += ms;
+    t.launches[r.kind] += 1;
+    t.pool.push_back(r.a);
+    t.pool.push_back(r.b);
+  }
+  t.pending.clear();
+  int n = 0;
+  for (size_t i = 0; i < t.kinds.size() && n < max; ++i) {
+    if (t.launches[i] == 0) continue;
+    if (out) {
+      std::snprintf(out[n].name, sizeof out[n].name, "%s", t.kinds[i].c_str());
+      out[n].launches = t.launches[i];
+      out[n].ms = t.ms[i];
+    }
+    ++n;
+  }
+  std::fill(t.launches.begin(), t.launches.end(), 0);
+  std::fill(t.ms.begin(), t.ms.end(), 0.0);
+  if (!ok) {
+    fail(MG_ERR_CUDA, "mg_timing_read: event query failed");
+    return -1;
+  }
+  return n;
+}
 
 const char* mg_last_error(void) { return g_err; }
 

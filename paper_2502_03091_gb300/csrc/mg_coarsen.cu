@@ -296,6 +296,7 @@ __global__ void coarse_apply_kernel(const float2* __restrict__ X, const float2* 
 }  // namespace
 
 cudaError_t launch_prolongator(const Geom& g, const float2* Uk, float2* P, cudaStream_t s) {
+  TimedScope ts("prolongator", s);
   prolongator_kernel<<<2048, 256, 0, s>>>(Uk, P, g.L[0], g.L[1], g.L[2], g.L[3], g.b[0], g.b[1],
                                            g.b[2], g.b[3], g.k);
   return cudaGetLastError();
@@ -325,6 +326,7 @@ cudaError_t launch_coarsen(const Geom& g, const float2* U, const float2* C, cons
     cudaFuncSetAttribute(coarsen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100000);
     attr_done = true;
   }
+  TimedScope ts("coarsen", s);
   coarsen_kernel<<<(int)g.nblk, kCoarsenThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -338,6 +340,7 @@ cudaError_t launch_coarse_apply(const Geom& g, const float2* X, const float2* Y,
     cudaFuncSetAttribute(coarse_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
     attr_done = true;
   }
+  TimedScope ts("coarse_apply", s);
   coarse_apply_kernel<<<(int)g.nblk, 256, smem, s>>>(X, Y, vin, vout, g.Lc[0], g.Lc[1], g.Lc[2],
                                                      g.Lc[3], n2, nrhs);
   return cudaGetLastError();

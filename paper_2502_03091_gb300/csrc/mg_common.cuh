@@ -49,6 +49,19 @@ TruncWs trunc_ws_layout(const Geom& g);
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // ---------------------------------------------------------------------------
+// optional per-kernel timing (mg_timing_enable): a scope records a CUDA event
+// pair around the launches it encloses on stream s
+// ---------------------------------------------------------------------------
+int timing_begin(const char* name, cudaStream_t s);
+void timing_end(int token, cudaStream_t s);
+struct TimedScope {
+  int tok;
+  cudaStream_t s;
+  TimedScope(const char* name, cudaStream_t st) : tok(timing_begin(name, st)), s(st) {}
+  ~TimedScope() { timing_end(tok, s); }
+};
+
+// ---------------------------------------------------------------------------
 // kernel launchers (defined in the .cu files); each returns cudaGetLastError()
 // ---------------------------------------------------------------------------
 cudaError_t launch_clover(const Geom& g, double csw, const float2* U, float2* C,

@@ -479,6 +479,9 @@ __global__ void clover_kernel(int L0, int L1, int L2, int L3, float csw,
 
 template <int PAIRS, int MODE>
 cudaError_t run_pass(const SmoothArgs& a, int grid, cudaStream_t s) {
+  static const char* names[4] = {"mr_neg_dslash", "mr_dslash_dot", "mr_fused_iteration",
+                                 "mr_last_update"};
+  TimedScope ts(names[MODE], s);
   smooth_kernel<PAIRS, MODE><<<grid, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -534,7 +537,10 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
   a.in = r[0];
   a.out = w[0];
   if ((e = run_pass<PAIRS, MODE_D_DOT>(a, G, s)) != cudaSuccess) return e;
-  finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, 0, alpha, scale);
+  {
+    TimedScope ts("mr_reduce", s);
+    finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, 0, alpha, scale);
+  }
   int cur = 0;
   for (int t = 1; t < g.niter; ++t) {
     // r_t = r_{t-1} - a w_{t-1}, w_t = D r_t, psi_t = psi_{t-1} + a r_{t-1} -> a_t
@@ -545,7 +551,10 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
     a.r_out = r[cur ^ 1];
     a.psi_out = p;
     if ((e = run_pass<PAIRS, MODE_FUSED>(a, G, s)) != cudaSuccess) return e;
+    {
+    TimedScope ts("mr_reduce", s);
     finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, 0, alpha, scale);
+  }
     cur ^= 1;
   }
   // psi_N = psi_{N-1} + a_{N-1} r_{N-1}, partial |psi_N|^2
@@ -553,9 +562,15 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
   a.psi_src = g.niter == 1 ? p0 : p;
   a.psi_out = p;
   if ((e = run_pass<PAIRS, MODE_LAST>(a, G, s)) != cudaSuccess) return e;
-  finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, 1, alpha, scale);
+  {
+    TimedScope ts("mr_reduce", s);
+    finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, 1, alpha, scale);
+  }
   const long n4 = g.V * 12L * (g.m / 2);
-  scale_kernel<<<1024, 256, 0, s>>>(p, scale, n4, g.m / 2);
+  {
+    TimedScope ts("mr_scale", s);
+    scale_kernel<<<1024, 256, 0, s>>>(p, scale, n4, g.m / 2);
+  }
   return cudaGetLastError();
 }
 
@@ -564,6 +579,7 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
 cudaError_t launch_clover(const Geom& g, double csw, const float2* U, float2* C,
                           cudaStream_t s) {
   const int V = (int)g.V;
+  TimedScope ts("clover", s);
   clover_kernel<<<(V + 127) / 128, 128, 0, s>>>(g.L[0], g.L[1], g.L[2], g.L[3], (float)csw, U, C);
   return cudaGetLastError();
 }

@@ -622,11 +622,26 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
     cudaFuncSetAttribute(form_uk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
     attr_done = true;
   }
-  gram_kernel<false><<<nbc, kThreads, sm_gram0, s>>>(psi, nullptr, G, bg);
-  chol_stage1<<<nbc, kThreads, sm_chol, s>>>(G, R1, Z1, flags, m);
-  gram_kernel<true><<<nbc, kThreads, sm_gram1, s>>>(psi, Z1, G, bg);
-  svd_stage2<<<nbc, kThreads, sm_svd, s>>>(G, R1, W2, sigma, coarse_tv, flags, m, k);
-  form_uk<<<nbc, kThreads, sm_uk, s>>>(psi, Z1, W2, Uk, bg);
+  {
+    TimedScope ts("trunc_gram", s);
+    gram_kernel<false><<<nbc, kThreads, sm_gram0, s>>>(psi, nullptr, G, bg);
+  }
+  {
+    TimedScope ts("trunc_chol64", s);
+    chol_stage1<<<nbc, kThreads, sm_chol, s>>>(G, R1, Z1, flags, m);
+  }
+  {
+    TimedScope ts("trunc_gram_q1", s);
+    gram_kernel<true><<<nbc, kThreads, sm_gram1, s>>>(psi, Z1, G, bg);
+  }
+  {
+    TimedScope ts("trunc_chol_eig64", s);
+    svd_stage2<<<nbc, kThreads, sm_svd, s>>>(G, R1, W2, sigma, coarse_tv, flags, m, k);
+  }
+  {
+    TimedScope ts("trunc_form_uk", s);
+    form_uk<<<nbc, kThreads, sm_uk, s>>>(psi, Z1, W2, Uk, bg);
+  }
   return cudaGetLastError();
 }
 

@@ -26,14 +26,18 @@ MG_CALL_SMOOTH, MG_CALL_TRUNCATE, MG_CALL_COARSEN = 0, 1, 2
 
 # every symbol include/mg.h declares
 EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_smooth_testvecs", "mg_chiral_truncate",
-           "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply", "mg_last_error",
-           "mg_version")
+           "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply", "mg_timing_enable",
+           "mg_timing_read", "mg_last_error", "mg_version")
 
 
 class MgError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
         self.status = status
+
+
+class _TimingEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
 class _Problem(ctypes.Structure):
@@ -113,6 +117,10 @@ def library(path: str = LIB_PATH):
     for f in ("mg_clover_field", "mg_smooth_testvecs", "mg_chiral_truncate",
               "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply"):
         getattr(lib, f).restype = ctypes.c_int
+    lib.mg_timing_enable.argtypes = [ctypes.c_int]
+    lib.mg_timing_enable.restype = ctypes.c_int
+    lib.mg_timing_read.argtypes = [ctypes.POINTER(_TimingEntry), ctypes.c_int]
+    lib.mg_timing_read.restype = ctypes.c_int
     lib.mg_last_error.restype = ctypes.c_char_p
     lib.mg_version.restype = ctypes.c_char_p
     _lib = lib
@@ -151,6 +159,19 @@ def _expect(t, shape, dtype, name):
 
 def version() -> str:
     return library().mg_version().decode()
+
+
+def mg_timing_enable(on: bool = True):
+    _check(library().mg_timing_enable(1 if on else 0))
+
+
+def mg_timing_read() -> dict:
+    """{kernel name: (launches, total ms)} since the previous read (then reset)."""
+    buf = (_TimingEntry * 64)()
+    n = library().mg_timing_read(buf, 64)
+    if n < 0:
+        raise MgError(4, library().mg_last_error().decode())
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(n)}
 
 
 def mg_workspace_size(prob: Problem, which: int) -> int:
