@@ -164,6 +164,25 @@ mg_status mg_coarsen(const mg_problem* prob, const void* U, const void* C, const
 mg_status mg_coarse_apply(const mg_problem* prob, const void* X, const void* Y,
                           const void* v_in, void* v_out, int32_t nrhs, void* stream);
 
+/* mg_chiral_truncate for callers that cannot allocate device memory (the
+ * paper has no counterpart; this is a service of this library).  A host
+ * application whose device memory is owned by its own pool allocator, or a
+ * solver loop that must not stall the device with cudaMalloc/cudaFree (both
+ * may synchronise the device), passes only inputs and outputs here: the
+ * scratch lives in a 64 MiB array compiled into the library, reserved on
+ * every GPU that loads it until the process exits.
+ * Same inputs, outputs and results as mg_chiral_truncate.  A problem whose
+ * scratch need (mg_workspace_size(prob, MG_CALL_TRUNCATE)) exceeds 64 MiB is
+ * rejected with MG_ERR_INVALID and a message.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array and leave their data in it (nothing in it needs to
+ * start at zero); calls that overlap on the GPU race on it, so serialise
+ * them (one stream, or synchronise between calls).  It allocates nothing. */
+mg_status mg_chiral_truncate_static(const mg_problem* prob, const void* psi, void* Uk,
+                                    double* sigma, void* coarse_tv, int32_t* blk_flags,
+                                    void* stream);
+
 /* Per-kernel timing (measurement aid; no counterpart in the paper).  While
  * enabled, every kernel the library launches is bracketed by two CUDA events
  * recorded on the launching stream.  mg_timing_read waits for the recorded

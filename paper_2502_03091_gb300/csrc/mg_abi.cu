@@ -108,6 +108,8 @@ TruncWs trunc_ws_layout(const Geom& g) {
   return w;
 }
 
+void set_last_error(const char* msg) { std::snprintf(g_err, sizeof g_err, "%s", msg); }
+
 // ---------------------------------------------------------------------------
 // per-kernel timing
 // ---------------------------------------------------------------------------

@@ -48,6 +48,9 @@ TruncWs trunc_ws_layout(const Geom& g);
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Sets the message mg_last_error() returns on the calling thread.
+void set_last_error(const char* msg);
+
 // ---------------------------------------------------------------------------
 // optional per-kernel timing (mg_timing_enable): a scope records a CUDA event
 // pair around the launches it encloses on stream s

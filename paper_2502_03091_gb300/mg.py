@@ -26,7 +26,8 @@ MG_CALL_SMOOTH, MG_CALL_TRUNCATE, MG_CALL_COARSEN = 0, 1, 2
 
 # every symbol include/mg.h declares
 EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_smooth_testvecs", "mg_chiral_truncate",
-           "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply", "mg_timing_enable",
+           "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply", "mg_chiral_truncate_static",
+           "mg_timing_enable",
            "mg_timing_read", "mg_last_error", "mg_version")
 
 
@@ -111,11 +112,13 @@ def library(path: str = LIB_PATH):
     lib.mg_clover_field.argtypes = [Pp, P, P, P]
     lib.mg_smooth_testvecs.argtypes = [Pp, P, P, P, P, P, ctypes.c_size_t, P]
     lib.mg_chiral_truncate.argtypes = [Pp, P, P, P, P, P, P, ctypes.c_size_t, P]
+    lib.mg_chiral_truncate_static.argtypes = [Pp, P, P, P, P, P, P]
     lib.mg_build_prolongator.argtypes = [Pp, P, P, P]
     lib.mg_coarsen.argtypes = [Pp, P, P, P, P, P, P, ctypes.c_size_t, P]
     lib.mg_coarse_apply.argtypes = [Pp, P, P, P, P, ctypes.c_int32, P]
     for f in ("mg_clover_field", "mg_smooth_testvecs", "mg_chiral_truncate",
-              "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply"):
+              "mg_chiral_truncate_static", "mg_build_prolongator", "mg_coarsen",
+              "mg_coarse_apply"):
         getattr(lib, f).restype = ctypes.c_int
     lib.mg_timing_enable.argtypes = [ctypes.c_int]
     lib.mg_timing_enable.restype = ctypes.c_int
@@ -258,6 +261,21 @@ def mg_chiral_truncate(prob: Problem, psi, Uk, sigma, coarse_tv, blk_flags, ws, 
     _check(library().mg_chiral_truncate(ctypes.byref(pc), _ptr(psi), _ptr(Uk), _ptr(sigma),
                                         _ptr(coarse_tv), _ptr(blk_flags), _ptr(ws),
                                         ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def mg_chiral_truncate_static(prob: Problem, psi, Uk, sigma, coarse_tv, blk_flags, stream=None):
+    """mg_chiral_truncate without a workspace argument: for callers that cannot
+    allocate device memory; scratch is a fixed 64 MiB array inside libmg.so."""
+    import torch
+    _expect(psi, shape_psi(prob), torch.complex64, "psi")
+    _expect(Uk, shape_Uk(prob), torch.complex64, "Uk")
+    _expect(sigma, shape_sigma(prob), torch.float64, "sigma")
+    _expect(coarse_tv, (prob.n_blocks, 2, prob.k, prob.n_vec), torch.complex64, "coarse_tv")
+    _expect(blk_flags, (prob.n_blocks, 2), torch.int32, "blk_flags")
+    pc = prob.c()
+    _check(library().mg_chiral_truncate_static(ctypes.byref(pc), _ptr(psi), _ptr(Uk),
+                                               _ptr(sigma), _ptr(coarse_tv), _ptr(blk_flags),
+                                               _stream(stream)))
 
 
 def mg_build_prolongator(prob: Problem, Uk, P, stream=None):
