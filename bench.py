@@ -48,6 +48,13 @@ def workload(name: str):
                     dims=[32, 32, 32, 64], block=[4, 4, 4, 8], eps=0.2, csw=0.0, xi=3.5,
                     m=64, k=24, N=20, m0=m0["32^3x64 aniso xi=3.5 eps=0.2"], gauge_seed=20,
                     psi_seed=21, sample_dims=[8, 8, 8, 16])
+    if name == "16^3x32-aniso":
+        # the 32^3x64 parameters on 1/16 of the volume: kernel-profiling case
+        w = workload("32^3x64")
+        w.update(workload="16^3x32 anisotropic (xi=3.5) Wilson, eps=0.2, m'=64, k=24, "
+                          "4^3x8 aggregates, 20 MR iterations, FP32 plain path",
+                 dims=[16, 16, 16, 32], sample_dims=[8, 8, 8, 16])
+        return w
     if name == "16^3x32":
         return dict(workload="16^3x32 Wilson-clover c_sw=1, eps=0.25, m'=48, k=24, 4^4 "
                              "aggregates, 20 MR iterations, FP32 plain path",
@@ -383,7 +390,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="32^3x64", choices=["32^3x64", "16^3x32"])
+    ap.add_argument("--workload", default="32^3x64",
+                    choices=["32^3x64", "16^3x32", "16^3x32-aniso"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     w = workload(args.workload)

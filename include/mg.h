@@ -118,6 +118,14 @@ size_t mg_workspace_size(const mg_problem* prob, int which);
  * In: U.  Out: C (layout above).  FP32 arithmetic. */
 mg_status mg_clover_field(const mg_problem* prob, const void* U, void* C, void* stream);
 
+/* The fine operator D (Sec. 1-2: the Wilson-Dirac operator whose near null
+ * space the setup exposes) applied to n_vec right-hand sides:
+ * out = D in, layouts [V][4][3][n_vec].  In: U, C (NULL for pure Wilson), in.
+ * Out: out (must not alias in).  ws: mg_workspace_size(prob, MG_CALL_SMOOTH)
+ * bytes (the same scratch as the smoother). */
+mg_status mg_apply_dirac(const mg_problem* prob, const void* U, const void* C, const void* in,
+                         void* out, void* ws, size_t ws_bytes, void* stream);
+
 /* Smoother on the homogeneous system D psi_i ~ 0 (Sec. 2, Eq. 1): minimal
  * residual with one step length per vector, mr_iters iterations, starting
  * from psi0, then every vector scaled to unit 2-norm.  In exact arithmetic:

@@ -87,7 +87,10 @@ SmoothWs smooth_ws_layout(const Geom& g) {
   w.rb = o; o = align256(o + field);
   w.wa = o; o = align256(o + field);
   w.wb = o; o = align256(o + field);
-  w.part = o; o = align256(o + sizeof(double) * 4 * (size_t)kMaxPersistentGrid * g.m);
+  w.ps = o; o = align256(o + field);
+  // partial sums: one per (right-hand side, patch of 32 sites of a timeslice)
+  const size_t npatch = ((size_t)(g.V / g.L[3]) + 31) / 32;
+  w.part = o; o = align256(o + sizeof(double) * 4 * npatch * g.m);
   w.alpha = o; o = align256(o + sizeof(float2) * g.m);
   w.scale = o; o = align256(o + sizeof(float) * g.m);
   w.bytes = o;
@@ -236,6 +239,22 @@ mg_status mg_clover_field(const mg_problem* prob, const void* U, void* C, void* 
   return cuda_status(launch_clover(g, prob->csw, static_cast<const float2*>(U),
                                    static_cast<float2*>(C), static_cast<cudaStream_t>(stream)),
                      "mg_clover_field");
+}
+
+mg_status mg_apply_dirac(const mg_problem* prob, const void* U, const void* C, const void* in,
+                         void* out, void* ws, size_t ws_bytes, void* stream) {
+  Geom g;
+  mg_status st = make_geom(prob, &g);
+  if (st != MG_OK) return st;
+  if (!U || !in || !out || !ws) return fail(MG_ERR_INVALID, "mg_apply_dirac: NULL array");
+  if (in == out) return fail(MG_ERR_INVALID, "mg_apply_dirac: out aliases in");
+  const size_t need = smooth_ws_layout(g).bytes;
+  if (ws_bytes < need)
+    return fail(MG_ERR_INVALID, "mg_apply_dirac: workspace %zu < %zu bytes", ws_bytes, need);
+  return cuda_status(launch_dirac(g, static_cast<const float2*>(U), static_cast<const float2*>(C),
+                                  static_cast<const float2*>(in), static_cast<float2*>(out),
+                                  static_cast<char*>(ws), static_cast<cudaStream_t>(stream)),
+                     "mg_apply_dirac");
 }
 
 mg_status mg_smooth_testvecs(const mg_problem* prob, const void* U, const void* C,

@@ -27,9 +27,6 @@ struct Geom {
   float diag;     // m0 + sum_mu w_mu
 };
 
-// Largest grid of the persistent smoother kernels (bounds the partial-sum
-// scratch).
-constexpr int kMaxPersistentGrid = 2048;
 constexpr int kMaxM = 64;  // largest m' this build supports
 constexpr int kMaxK = 32;  // largest k this build supports
 
@@ -37,7 +34,7 @@ constexpr int kMaxK = 32;  // largest k this build supports
 // workspace layout (byte offsets, 256-aligned), see mg_abi.cu
 // ---------------------------------------------------------------------------
 struct SmoothWs {
-  size_t ra, rb, wa, wb, part, alpha, scale, bytes;
+  size_t ra, rb, wa, wb, ps, part, alpha, scale, bytes;
 };
 struct TruncWs {
   size_t gram, r1, z1, w2, flags, bytes;
@@ -69,6 +66,9 @@ struct TimedScope {
 // ---------------------------------------------------------------------------
 cudaError_t launch_clover(const Geom& g, double csw, const float2* U, float2* C,
                           cudaStream_t s);
+
+cudaError_t launch_dirac(const Geom& g, const float2* U, const float2* C, const float2* in,
+                         float2* out, char* ws, cudaStream_t s);
 
 cudaError_t launch_smoother(const Geom& g, const float2* U, const float2* C,
                             const float2* psi0, float2* psi, char* ws, cudaStream_t s);

@@ -84,33 +84,76 @@ __device__ __forceinline__ void bdag_apply(float4 g0, float4 g1, float4& o0, flo
   if (MU == 3) { o0 = g0; o1 = g1; }
 }
 
-// Neighbour spinor component e for this thread's two right-hand sides:
-// r(y) (COMBINE = false) or r(y) - a w(y) (COMBINE = true).
-template <bool COMBINE>
-__device__ __forceinline__ float4 nb_load(const float4* __restrict__ r, const float4* __restrict__ w,
-                                          long off, float2 a0, float2 a1) {
-  const float4 v = __ldg(r + off);
-  if (!COMBINE) return v;
-  return f4sub(v, f4mul2(a0, a1, __ldg(w + off)));
+// ---------------------------------------------------------------------------
+// t-marching smoother pass.
+//
+// Internal ("slab") layout of r, w and psi: for right-hand-side slice q of
+// 2*PAIRS vectors, float4 f[((q*V + x)*12 + e)*PAIRS + p] -- every site's
+// 12 x 2*PAIRS complex numbers of one slice are contiguous.
+//
+// One CTA owns a patch of kSPC consecutive sites of a timeslice (spatial
+// lexicographic index p0 .. p0+kSPC-1) for one slice, and marches t = 0..Lt-1.
+// A ring of kRing rows of the dslash input s (s = r, or s = r - a w formed
+// when the row is staged) lives in shared memory: hops that stay in the patch
+// (x, and y when a patch spans several x-rows) and the two t-hops read the
+// ring; only hops that leave the patch go to global memory (L2).  Producer
+// warps stage row t+2 while consumer warps apply D to row t; one barrier per
+// step.  Ring slot of row r (r = -1 .. Lt+1): (r + 1) & 3.
+// ---------------------------------------------------------------------------
+constexpr int kSPC = 32;
+constexpr int kRing = 4;
+
+struct MarchArgs {
+  const float4* in;       // s source r_t (slab) or psi_0 (ABI layout)
+  const float4* win;      // w_t (slab), fused pass
+  const float4* psi_src;  // psi_t, fused pass (ABI layout for psi_0, else slab)
+  float4* out;            // D s (slab)
+  float4* r_out;          // r_{t+1} = s (slab), fused pass
+  float4* psi_out;        // psi_{t+1} (slab), fused pass
+  const float2* U;
+  const float2* C;        // clover or nullptr
+  const float2* alpha;    // [m'] step lengths
+  double* part;           // [m'][npatch][4]
+  int L[4];
+  int Vs, V, np, npatch;
+  int in_abi, psi_abi;    // layouts of `in` and `psi_src`
+  float hw[4];
+  float diag;
+};
+
+enum { MODE_NEG_D = 0, MODE_D_DOT = 1, MODE_FUSED = 2 };
+
+__device__ __forceinline__ long slab_index(int q, int V, int x, int e, int PAIRS, int p) {
+  return (((long)q * V + x) * 12 + e) * PAIRS + p;
 }
 
-template <int MU, int S, bool COMBINE>
-__device__ __forceinline__ void hop(float4 acc[12], const float4* __restrict__ r,
-                                    const float4* __restrict__ w, long nb, int np,
-                                    const float2* __restrict__ u, float hw, float2 a0, float2 a1) {
+// one hop from a neighbour whose 12 components (this thread's pair) are at
+// src[e * es]: shared memory (already combined) or global (combined here)
+template <int MU, int S, bool SHARED, bool COMBINE>
+__device__ __forceinline__ void hop2(float4 acc[12], const float4* src, const float4* wsrc, int es,
+                                     const float2* __restrict__ u, float hw, float2 a0, float2 a1) {
   float2 U[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) U[i] = __ldg(u + i);
-  // h = chi_u - S B chi_l, built one upper spin at a time:
-  // (B chi_l)_sp = coefficient * chi_{2 + lo(sp)}
   float4 h[2][3];
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     const int lo = (MU == 0 || MU == 1) ? 1 - sp : sp;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float4 up = nb_load<COMBINE>(r, w, nb + (long)(sp * 3 + c) * np, a0, a1);
-      const float4 dn = nb_load<COMBINE>(r, w, nb + (long)((2 + lo) * 3 + c) * np, a0, a1);
+      const int eu = sp * 3 + c, ed = (2 + lo) * 3 + c;
+      float4 up, dn;
+      if (SHARED) {
+        up = src[eu * es];
+        dn = src[ed * es];
+      } else {
+        up = __ldg(src + eu * es);
+        dn = __ldg(src + ed * es);
+        if (COMBINE) {
+          up = f4sub(up, f4mul2(a0, a1, __ldg(wsrc + eu * es)));
+          dn = f4sub(dn, f4mul2(a0, a1, __ldg(wsrc + ed * es)));
+        }
+      }
       const float4 bl = b_row<MU>(sp, dn);
       h[sp][c] = S > 0 ? f4sub(up, bl) : f4add(up, bl);
     }
@@ -142,94 +185,112 @@ __device__ __forceinline__ void hop(float4 acc[12], const float4* __restrict__ r
   }
 }
 
-struct SmoothArgs {
-  const float4* in;       // dslash input r (neighbours and centre)
-  const float4* win;      // w_t for the on-the-fly r_{t+1} = r_t - a_t w_t (fused pass)
-  const float4* psi_src;  // centre-only psi_t
-  float4* out;            // dslash result: -D psi_0, w_0, or w_{t+1}
-  float4* r_out;          // r_{t+1}
-  float4* psi_out;        // psi_{t+1}
-  const float2* U;
-  const float2* C;        // clover or nullptr
-  const float2* alpha;    // [m'] step lengths a_t
-  double* part;           // [m'][grid][4] partial sums
-  int L[4];
-  int V;
-  int np;                 // m'/2
-  float hw[4];
-  float diag;
-};
+// spatial hop mu (0..2) of the consumer at spatial index xyz, time t
+template <int MU, int S, int PAIRS, bool COMBINE>
+__device__ __forceinline__ void spatial_hop(float4 acc[12], const MarchArgs& a, const float4* ring_t,
+                                            int SS, int p0, int xyz, int nxyz, int t, int q, int p,
+                                            const float2* u, float2 a0, float2 a1) {
+  const int loc = nxyz - p0;
+  if (loc >= 0 && loc < kSPC && nxyz < a.Vs) {
+    hop2<MU, S, true, false>(acc, ring_t + loc * SS + p, nullptr, PAIRS, u, a.hw[MU], a0, a1);
+  } else if (a.in_abi) {
+    // the first pass reads psi_0 in the ABI layout [V][12][m'] (never combined)
+    const long o = ((long)(t * a.Vs + nxyz) * 12) * a.np + q * PAIRS + p;
+    hop2<MU, S, false, false>(acc, a.in + o, nullptr, a.np, u, a.hw[MU], a0, a1);
+  } else {
+    const long o = slab_index(q, a.V, t * a.Vs + nxyz, 0, PAIRS, p);
+    hop2<MU, S, false, COMBINE>(acc, a.in + o, COMBINE ? a.win + o : nullptr, PAIRS, u, a.hw[MU],
+                                a0, a1);
+  }
+}
 
-enum { MODE_NEG_D = 0, MODE_D_DOT = 1, MODE_FUSED = 2, MODE_LAST = 3 };
-
-// Persistent smoother pass.  The right-hand sides are processed in slices of
-// 2*PAIRS (outer loop) and the sites in chunks of 128/PAIRS (grid-stride
-// inner loop), so that at any time the whole GPU works on one slice and the
-// neighbour reads of that slice stay in L2.
-//   MODE_NEG_D: out = -D in
-//   MODE_D_DOT: out = D in; partials <out, in>, |out|^2
-//   MODE_FUSED: s = in - a win (on the fly), out = D s, r_out = s,
-//               psi_out = psi_src + a in; partials <out, s>, |out|^2
-//   MODE_LAST:  psi_out = psi_src + a in; partial |psi_out|^2
 template <int PAIRS, int MODE>
-__global__ void __launch_bounds__(128, 3) smooth_kernel(SmoothArgs a) {
-  constexpr int SPC = 128 / PAIRS;  // sites per chunk
+__global__ void __launch_bounds__(2 * kSPC * PAIRS, 1) march_kernel(MarchArgs a) {
+  constexpr int NC = kSPC * PAIRS;     // consumer threads (= producer threads)
+  constexpr int SS = 12 * PAIRS + 4;   // padded ring site stride (float4)
+  constexpr int NW = NC / 32;          // consumer warps
   constexpr bool COMBINE = MODE == MODE_FUSED;
-  const int p_loc = threadIdx.x % PAIRS;
-  const int s_loc = threadIdx.x / PAIRS;
-  const int nsl = a.np / PAIRS;
-  const long nchunk = ((long)a.V + SPC - 1) / SPC;
-  const int S1 = a.L[0], S2 = a.L[0] * a.L[1], S3 = a.L[0] * a.L[1] * a.L[2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ double red[4][PAIRS][6];
+  extern __shared__ float4 ring[];     // [kRing][kSPC][SS]
+  __shared__ double red[NW][PAIRS][6];
+  const int q = blockIdx.x / a.npatch, patch = blockIdx.x % a.npatch;
+  const int p0 = patch * kSPC;
+  const bool producer = threadIdx.x >= NC;
+  const int tid = producer ? threadIdx.x - NC : threadIdx.x;
+  const int s_loc = tid / PAIRS, p = tid % PAIRS;
+  const int gp = q * PAIRS + p;
+  const int xyz = p0 + s_loc;
+  const bool valid = xyz < a.Vs;
+  const int Lt = a.L[3];
+  float2 al0 = make_float2(0.f, 0.f), al1 = al0;
+  if (MODE == MODE_FUSED) {
+    al0 = a.alpha[2 * gp];
+    al1 = a.alpha[2 * gp + 1];
+  }
 
-  for (int q = 0; q < nsl; ++q) {
-    const int gp = q * PAIRS + p_loc;
-    float2 al0 = make_float2(0.f, 0.f), al1 = al0;
-    if (MODE == MODE_FUSED || MODE == MODE_LAST) {
-      al0 = a.alpha[2 * gp];
-      al1 = a.alpha[2 * gp + 1];
-    }
-    double pr[6] = {0, 0, 0, 0, 0, 0};  // (re<w,r>, im<w,r>, |w|^2) x 2 rhs
-    for (long c = blockIdx.x; c < nchunk; c += gridDim.x) {
-      const long xl = c * SPC + s_loc;
-      if (xl >= a.V) continue;
-      const int x = (int)xl;
-      const long base = (long)x * 12 * a.np + gp;
-      if (MODE == MODE_LAST) {
-        float s2a = 0.f, s2b = 0.f;
+  // producer: stage row r (-1 <= r <= Lt) of my site into its ring slot
+  auto stage = [&](int r) {
+    if (!valid) return;
+    const int tt = (r + Lt) % Lt;
+    const bool first = r >= 0 && r < Lt;
+    const int x = tt * a.Vs + xyz;
+    float4* dst = ring + ((r + 1) & 3) * kSPC * SS + s_loc * SS + p;
+    const long so = slab_index(q, a.V, x, 0, PAIRS, p);
+    const long ao = (long)x * 12 * a.np + gp;
 #pragma unroll
-        for (int e = 0; e < 12; ++e) {
-          const float4 rc = __ldcs(a.in + base + (long)e * a.np);
-          const float4 pc = __ldcs(a.psi_src + base + (long)e * a.np);
-          const float4 pn = f4add(pc, f4mul2(al0, al1, rc));
-          s2a += pn.x * pn.x + pn.y * pn.y;
-          s2b += pn.z * pn.z + pn.w * pn.w;
-          __stcs(a.psi_out + base + (long)e * a.np, pn);
+    for (int e = 0; e < 12; ++e) {
+      float4 v;
+      if (MODE == MODE_NEG_D && a.in_abi) v = __ldg(a.in + ao + (long)e * a.np);
+      else v = __ldg(a.in + so + e * PAIRS);
+      if (COMBINE) {
+        const float4 sv = f4sub(v, f4mul2(al0, al1, __ldg(a.win + so + e * PAIRS)));
+        dst[e * PAIRS] = sv;
+        if (first) {
+          __stcs(a.r_out + so + e * PAIRS, sv);
+          const float4 pc = a.psi_abi ? __ldcs(a.psi_src + ao + (long)e * a.np)
+                                      : __ldcs(a.psi_src + so + e * PAIRS);
+          __stcs(a.psi_out + so + e * PAIRS, f4add(pc, f4mul2(al0, al1, v)));
         }
-        pr[2] += (double)s2a;
-        pr[5] += (double)s2b;
-        continue;
+      } else {
+        dst[e * PAIRS] = v;
       }
-      int co[4];
-      {
-        int t = x;
-        co[0] = t % a.L[0]; t /= a.L[0];
-        co[1] = t % a.L[1]; t /= a.L[1];
-        co[2] = t % a.L[2]; co[3] = t / a.L[2];
-      }
-      const int st[4] = {1, S1, S2, S3};
-      int xf[4], xb[4];
+    }
+  };
+
+  int cxyz[3] = {0, 0, 0};  // spatial coordinates of my site
+  {
+    int t = xyz;
+    cxyz[0] = t % a.L[0]; t /= a.L[0];
+    cxyz[1] = t % a.L[1]; cxyz[2] = t / a.L[1];
+  }
+  const int sst[3] = {1, a.L[0], a.L[0] * a.L[1]};
+  int nf[3], nb[3];
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) {
-        xf[mu] = co[mu] < a.L[mu] - 1 ? x + st[mu] : x - (a.L[mu] - 1) * st[mu];
-        xb[mu] = co[mu] > 0 ? x - st[mu] : x + (a.L[mu] - 1) * st[mu];
-      }
-      // centre: s = r (or r - a w), z = (m0 + sum w) s + C s
+  for (int mu = 0; mu < 3; ++mu) {
+    nf[mu] = cxyz[mu] < a.L[mu] - 1 ? xyz + sst[mu] : xyz - (a.L[mu] - 1) * sst[mu];
+    nb[mu] = cxyz[mu] > 0 ? xyz - sst[mu] : xyz + (a.L[mu] - 1) * sst[mu];
+  }
+
+  double pr[6] = {0, 0, 0, 0, 0, 0};
+  if (producer) {
+    stage(-1);
+    stage(0);
+    if (Lt > 1) stage(1);
+    else stage(1);  // Lt == 1: row 1 is row 0 again (no side effects)
+  }
+  __syncthreads();
+  for (int t = 0; t < Lt; ++t) {
+    if (producer) {
+      if (t + 2 <= Lt) stage(t + 2);
+    } else if (valid) {
+      const float4* ring_t = ring + ((t + 1) & 3) * kSPC * SS;
+      const float4* ring_f = ring + ((t + 2) & 3) * kSPC * SS;
+      const float4* ring_b = ring + (t & 3) * kSPC * SS;
+      const int x = t * a.Vs + xyz;
+      const int tb = (t - 1 + Lt) % Lt;
       float4 z[12], cen[12];
 #pragma unroll
       for (int e = 0; e < 12; ++e) {
-        cen[e] = nb_load<COMBINE>(a.in, a.win, base + (long)e * a.np, al0, al1);
+        cen[e] = ring_t[s_loc * SS + e * PAIRS + p];
         z[e] = make_float4(a.diag * cen[e].x, a.diag * cen[e].y, a.diag * cen[e].z,
                            a.diag * cen[e].w);
       }
@@ -243,48 +304,45 @@ __global__ void __launch_bounds__(128, 3) smooth_kernel(SmoothArgs a) {
             for (int j = 0; j < 6; ++j)
               f4cfma(z[6 * al + i], __ldg(cl + al * 36 + i * 6 + j), cen[6 * al + j]);
       }
-      const long ps = (long)12 * a.np;
-      const float4* R = a.in;
-      const float4* W = a.win;
-      hop<0, +1, COMBINE>(z, R, W, xf[0] * ps + gp, a.np, a.U + ((long)x * 4 + 0) * 9, a.hw[0], al0, al1);
-      hop<0, -1, COMBINE>(z, R, W, xb[0] * ps + gp, a.np, a.U + ((long)xb[0] * 4 + 0) * 9, a.hw[0], al0, al1);
-      hop<1, +1, COMBINE>(z, R, W, xf[1] * ps + gp, a.np, a.U + ((long)x * 4 + 1) * 9, a.hw[1], al0, al1);
-      hop<1, -1, COMBINE>(z, R, W, xb[1] * ps + gp, a.np, a.U + ((long)xb[1] * 4 + 1) * 9, a.hw[1], al0, al1);
-      hop<2, +1, COMBINE>(z, R, W, xf[2] * ps + gp, a.np, a.U + ((long)x * 4 + 2) * 9, a.hw[2], al0, al1);
-      hop<2, -1, COMBINE>(z, R, W, xb[2] * ps + gp, a.np, a.U + ((long)xb[2] * 4 + 2) * 9, a.hw[2], al0, al1);
-      hop<3, +1, COMBINE>(z, R, W, xf[3] * ps + gp, a.np, a.U + ((long)x * 4 + 3) * 9, a.hw[3], al0, al1);
-      hop<3, -1, COMBINE>(z, R, W, xb[3] * ps + gp, a.np, a.U + ((long)xb[3] * 4 + 3) * 9, a.hw[3], al0, al1);
+      const float2* Ux = a.U + (long)x * 36;
+      spatial_hop<0, +1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nf[0], t, q, p, Ux + 0, al0, al1);
+      spatial_hop<0, -1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nb[0], t, q, p,
+                                         a.U + ((long)t * a.Vs + nb[0]) * 36 + 0, al0, al1);
+      spatial_hop<1, +1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nf[1], t, q, p, Ux + 9, al0, al1);
+      spatial_hop<1, -1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nb[1], t, q, p,
+                                         a.U + ((long)t * a.Vs + nb[1]) * 36 + 9, al0, al1);
+      spatial_hop<2, +1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nf[2], t, q, p, Ux + 18, al0, al1);
+      spatial_hop<2, -1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nb[2], t, q, p,
+                                         a.U + ((long)t * a.Vs + nb[2]) * 36 + 18, al0, al1);
+      hop2<3, +1, true, false>(z, ring_f + s_loc * SS + p, nullptr, PAIRS, Ux + 27, a.hw[3], al0, al1);
+      hop2<3, -1, true, false>(z, ring_b + s_loc * SS + p, nullptr, PAIRS,
+                               a.U + ((long)tb * a.Vs + xyz) * 36 + 27, a.hw[3], al0, al1);
+      const long so = slab_index(q, a.V, x, 0, PAIRS, p);
       if (MODE == MODE_NEG_D) {
 #pragma unroll
-        for (int e = 0; e < 12; ++e) __stcs(a.out + base + (long)e * a.np, f4neg(z[e]));
-        continue;
-      }
-      float s[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-      for (int e = 0; e < 12; ++e) {
-        const float4 w = z[e], r = cen[e];
-        s[0] += w.x * r.x + w.y * r.y;
-        s[1] += w.x * r.y - w.y * r.x;
-        s[2] += w.x * w.x + w.y * w.y;
-        s[3] += w.z * r.z + w.w * r.w;
-        s[4] += w.z * r.w - w.w * r.z;
-        s[5] += w.z * w.z + w.w * w.w;
-        __stcs(a.out + base + (long)e * a.np, w);
-      }
-      if (MODE == MODE_FUSED) {
+        for (int e = 0; e < 12; ++e) __stcs(a.out + so + e * PAIRS, f4neg(z[e]));
+      } else {
+        float s6[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int e = 0; e < 12; ++e) {
-          const float4 rc = __ldg(a.in + base + (long)e * a.np);
-          const float4 pc = __ldcs(a.psi_src + base + (long)e * a.np);
-          __stcs(a.r_out + base + (long)e * a.np, cen[e]);
-          __stcs(a.psi_out + base + (long)e * a.np, f4add(pc, f4mul2(al0, al1, rc)));
+          const float4 w = z[e], r = cen[e];
+          s6[0] += w.x * r.x + w.y * r.y;
+          s6[1] += w.x * r.y - w.y * r.x;
+          s6[2] += w.x * w.x + w.y * w.y;
+          s6[3] += w.z * r.z + w.w * r.w;
+          s6[4] += w.z * r.w - w.w * r.z;
+          s6[5] += w.z * w.z + w.w * w.w;
+          __stcs(a.out + so + e * PAIRS, w);
         }
-      }
 #pragma unroll
-      for (int i = 0; i < 6; ++i) pr[i] += (double)s[i];
+        for (int i = 0; i < 6; ++i) pr[i] += (double)s6[i];
+      }
     }
-    if (MODE != MODE_NEG_D) {
-      // lanes with the same pair index sit PAIRS apart within the warp
+    __syncthreads();
+  }
+  if (MODE != MODE_NEG_D) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (!producer) {
 #pragma unroll
       for (int off = 16; off >= PAIRS; off >>= 1)
 #pragma unroll
@@ -292,22 +350,77 @@ __global__ void __launch_bounds__(128, 3) smooth_kernel(SmoothArgs a) {
       if (lane < PAIRS)
 #pragma unroll
         for (int i = 0; i < 6; ++i) red[warp][lane][i] = pr[i];
-      __syncthreads();
-      if (threadIdx.x < PAIRS) {
-        double t[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) t[i] = red[0][threadIdx.x][i];
-        for (int w = 1; w < 4; ++w)
-#pragma unroll
-          for (int i = 0; i < 6; ++i) t[i] += red[w][threadIdx.x][i];
-        const int rhs0 = 2 * (q * PAIRS + threadIdx.x);
-        double* p0 = a.part + ((long)rhs0 * gridDim.x + blockIdx.x) * 4;
-        double* p1 = a.part + ((long)(rhs0 + 1) * gridDim.x + blockIdx.x) * 4;
-        p0[0] = t[0]; p0[1] = t[1]; p0[2] = t[2];
-        p1[0] = t[3]; p1[1] = t[4]; p1[2] = t[5];
-      }
-      __syncthreads();
     }
+    __syncthreads();
+    if (threadIdx.x < PAIRS) {
+      double tt[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) tt[i] = red[0][threadIdx.x][i];
+      for (int w = 1; w < NW; ++w)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) tt[i] += red[w][threadIdx.x][i];
+      const int rhs0 = 2 * (q * PAIRS + threadIdx.x);
+      double* q0 = a.part + ((long)rhs0 * a.npatch + patch) * 4;
+      double* q1 = a.part + ((long)(rhs0 + 1) * a.npatch + patch) * 4;
+      q0[0] = tt[0]; q0[1] = tt[1]; q0[2] = tt[2];
+      q1[0] = tt[3]; q1[1] = tt[4]; q1[2] = tt[5];
+    }
+  }
+}
+
+// psi_N = psi_{N-1} + a r_{N-1} (slab), partial |psi_N|^2 per right-hand side.
+// Grid: one CTA per (slice, patch), looping over t; thread = (site, pair).
+template <int PAIRS>
+__global__ void __launch_bounds__(kSPC * PAIRS) last_update(MarchArgs a) {
+  constexpr int NC = kSPC * PAIRS, NW = NC / 32;
+  __shared__ double red[NW][PAIRS][2];
+  const int q = blockIdx.x / a.npatch, patch = blockIdx.x % a.npatch;
+  const int s_loc = threadIdx.x / PAIRS, p = threadIdx.x % PAIRS;
+  const int gp = q * PAIRS + p;
+  const int xyz = patch * kSPC + s_loc;
+  const float2 al0 = a.alpha[2 * gp], al1 = a.alpha[2 * gp + 1];
+  double n0 = 0, n1 = 0;
+  if (xyz < a.Vs) {
+    for (int t = 0; t < a.L[3]; ++t) {
+      const int x = t * a.Vs + xyz;
+      const long so = slab_index(q, a.V, x, 0, PAIRS, p);
+      const long ao = (long)x * 12 * a.np + gp;
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int e = 0; e < 12; ++e) {
+        const float4 rc = __ldcs(a.in + so + e * PAIRS);
+        const float4 pc = a.psi_abi ? __ldcs(a.psi_src + ao + (long)e * a.np)
+                                    : __ldcs(a.psi_src + so + e * PAIRS);
+        const float4 pn = f4add(pc, f4mul2(al0, al1, rc));
+        s0 += pn.x * pn.x + pn.y * pn.y;
+        s1 += pn.z * pn.z + pn.w * pn.w;
+        __stcs(a.psi_out + so + e * PAIRS, pn);
+      }
+      n0 += (double)s0;
+      n1 += (double)s1;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = 16; off >= PAIRS; off >>= 1) {
+    n0 += __shfl_xor_sync(0xffffffffu, n0, off);
+    n1 += __shfl_xor_sync(0xffffffffu, n1, off);
+  }
+  if (lane < PAIRS) {
+    red[warp][lane][0] = n0;
+    red[warp][lane][1] = n1;
+  }
+  __syncthreads();
+  if (threadIdx.x < PAIRS) {
+    double t0 = 0, t1 = 0;
+    for (int w = 0; w < NW; ++w) {
+      t0 += red[w][threadIdx.x][0];
+      t1 += red[w][threadIdx.x][1];
+    }
+    const int rhs0 = 2 * (q * PAIRS + threadIdx.x);
+    double* q0 = a.part + ((long)rhs0 * a.npatch + patch) * 4;
+    double* q1 = a.part + ((long)(rhs0 + 1) * a.npatch + patch) * 4;
+    q0[0] = 0; q0[1] = 0; q0[2] = t0;
+    q1[0] = 0; q1[1] = 0; q1[2] = t1;
   }
 }
 
@@ -319,10 +432,10 @@ __global__ void finish_reduction(const double* __restrict__ part, int G, int m, 
   if (i >= m) return;
   double re = 0, im = 0, nn = 0;
   for (int g = 0; g < G; ++g) {
-    const double* p = part + ((long)i * G + g) * 4;
-    re += p[0];
-    im += p[1];
-    nn += p[2];
+    const double* pp = part + ((long)i * G + g) * 4;
+    re += pp[0];
+    im += pp[1];
+    nn += pp[2];
   }
   if (mode == 0) {
     alpha[i] = nn > 0 ? make_float2((float)(re / nn), (float)(im / nn)) : make_float2(0.f, 0.f);
@@ -331,15 +444,29 @@ __global__ void finish_reduction(const double* __restrict__ part, int G, int m, 
   }
 }
 
-__global__ void scale_kernel(float4* __restrict__ psi, const float* __restrict__ scale, long n,
-                             int np) {
+__global__ void fill_kernel(float* __restrict__ v, int n, float x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = x;
+}
+
+// psi (ABI layout) = scale * psi_slab
+template <int PAIRS>
+__global__ void scale_to_abi(const float4* __restrict__ src, float4* __restrict__ dst,
+                             const float* __restrict__ scale, int V, int np) {
+  const long n = (long)V * 12 * np;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x) {
-    const int p = (int)(i % np);
-    const float s0 = scale[2 * p], s1 = scale[2 * p + 1];
-    float4 v = __ldcs(psi + i);
+    // i enumerates the slab: ((q*V + x)*12 + e)*PAIRS + p
+    const int p = (int)(i % PAIRS);
+    long r = i / PAIRS;
+    const int e = (int)(r % 12);
+    r /= 12;
+    const int x = (int)(r % V);
+    const int q = (int)(r / V);
+    const int gp = q * PAIRS + p;
+    float4 v = __ldcs(src + i);
+    const float s0 = scale[2 * gp], s1 = scale[2 * gp + 1];
     v.x *= s0; v.y *= s0; v.z *= s1; v.w *= s1;
-    __stcs(psi + i, v);
+    __stcs(dst + ((long)x * 12 + e) * np + gp, v);
   }
 }
 
@@ -395,13 +522,6 @@ __global__ void clover_kernel(int L0, int L1, int L2, int L3, float csw,
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= V) return;
   const int L[4] = {L0, L1, L2, L3};
-  int co[4];
-  {
-    int t = x;
-    co[0] = t % L0; t /= L0;
-    co[1] = t % L1; t /= L1;
-    co[2] = t % L2; co[3] = t / L2;
-  }
   auto shift = [&](int s, int mu, int d) {
     int c[4];
     int t = s;
@@ -478,27 +598,19 @@ __global__ void clover_kernel(int L0, int L1, int L2, int L3, float csw,
 }
 
 template <int PAIRS, int MODE>
-cudaError_t run_pass(const SmoothArgs& a, int grid, cudaStream_t s) {
-  static const char* names[4] = {"mr_neg_dslash", "mr_dslash_dot", "mr_fused_iteration",
-                                 "mr_last_update"};
+cudaError_t run_march(const MarchArgs& a, int nsl, cudaStream_t s) {
+  static const char* names[3] = {"mr_neg_dslash", "mr_dslash_dot", "mr_fused_iteration"};
+  constexpr int SS = 12 * PAIRS + 4;
+  const size_t smem = sizeof(float4) * (size_t)kRing * kSPC * SS;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(march_kernel<PAIRS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr = true;
+  }
   TimedScope ts(names[MODE], s);
-  smooth_kernel<PAIRS, MODE><<<grid, 128, 0, s>>>(a);
+  march_kernel<PAIRS, MODE><<<nsl * a.npatch, 2 * kSPC * PAIRS, smem, s>>>(a);
   return cudaGetLastError();
-}
-
-template <int PAIRS>
-int persistent_grid() {
-  static int cached = 0;
-  if (cached) return cached;
-  int dev = 0, sms = 0, occ = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, smooth_kernel<PAIRS, MODE_FUSED>, 128, 0);
-  int g = sms * (occ > 0 ? occ : 1);
-  if (g > kMaxPersistentGrid) g = kMaxPersistentGrid;
-  if (g < 1) g = 1;
-  cached = g;
-  return g;
 }
 
 template <int PAIRS>
@@ -507,12 +619,12 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
   const SmoothWs lay = smooth_ws_layout(g);
   float4* r[2] = {reinterpret_cast<float4*>(ws + lay.ra), reinterpret_cast<float4*>(ws + lay.rb)};
   float4* w[2] = {reinterpret_cast<float4*>(ws + lay.wa), reinterpret_cast<float4*>(ws + lay.wb)};
+  float4* ps = reinterpret_cast<float4*>(ws + lay.ps);
   double* part = reinterpret_cast<double*>(ws + lay.part);
   float2* alpha = reinterpret_cast<float2*>(ws + lay.alpha);
   float* scale = reinterpret_cast<float*>(ws + lay.scale);
-  const int G = persistent_grid<PAIRS>();
 
-  SmoothArgs a{};
+  MarchArgs a{};
   a.U = U;
   a.C = C;
   a.alpha = alpha;
@@ -522,54 +634,58 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
     a.hw[i] = g.hw[i];
   }
   a.V = (int)g.V;
+  a.Vs = (int)(g.V / g.L[3]);
   a.np = g.m / 2;
+  a.npatch = (a.Vs + kSPC - 1) / kSPC;
   a.diag = g.diag;
+  const int nsl = a.np / PAIRS;
+  const int G = a.npatch;  // partial sums per right-hand side
   const float4* p0 = reinterpret_cast<const float4*>(psi0);
-  float4* p = reinterpret_cast<float4*>(psi);
   const int nred = (g.m + 63) / 64;
   cudaError_t e;
+  auto reduce = [&](int mode) {
+    TimedScope ts("mr_reduce", s);
+    finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, mode, alpha, scale);
+  };
 
-  // r_0 = -D psi_0
+  // r_0 = -D psi_0  (psi_0 in the ABI layout)
   a.in = p0;
+  a.in_abi = 1;
   a.out = r[0];
-  if ((e = run_pass<PAIRS, MODE_NEG_D>(a, G, s)) != cudaSuccess) return e;
+  if ((e = run_march<PAIRS, MODE_NEG_D>(a, nsl, s)) != cudaSuccess) return e;
   // w_0 = D r_0 -> a_0
   a.in = r[0];
+  a.in_abi = 0;
   a.out = w[0];
-  if ((e = run_pass<PAIRS, MODE_D_DOT>(a, G, s)) != cudaSuccess) return e;
-  {
-    TimedScope ts("mr_reduce", s);
-    finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, 0, alpha, scale);
-  }
+  if ((e = run_march<PAIRS, MODE_D_DOT>(a, nsl, s)) != cudaSuccess) return e;
+  reduce(0);
   int cur = 0;
   for (int t = 1; t < g.niter; ++t) {
     // r_t = r_{t-1} - a w_{t-1}, w_t = D r_t, psi_t = psi_{t-1} + a r_{t-1} -> a_t
     a.in = r[cur];
     a.win = w[cur];
-    a.psi_src = t == 1 ? p0 : p;
+    a.psi_src = t == 1 ? p0 : ps;
+    a.psi_abi = t == 1;
     a.out = w[cur ^ 1];
     a.r_out = r[cur ^ 1];
-    a.psi_out = p;
-    if ((e = run_pass<PAIRS, MODE_FUSED>(a, G, s)) != cudaSuccess) return e;
-    {
-    TimedScope ts("mr_reduce", s);
-    finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, 0, alpha, scale);
-  }
+    a.psi_out = ps;
+    if ((e = run_march<PAIRS, MODE_FUSED>(a, nsl, s)) != cudaSuccess) return e;
+    reduce(0);
     cur ^= 1;
   }
   // psi_N = psi_{N-1} + a_{N-1} r_{N-1}, partial |psi_N|^2
   a.in = r[cur];
-  a.psi_src = g.niter == 1 ? p0 : p;
-  a.psi_out = p;
-  if ((e = run_pass<PAIRS, MODE_LAST>(a, G, s)) != cudaSuccess) return e;
+  a.psi_src = g.niter == 1 ? p0 : ps;
+  a.psi_abi = g.niter == 1;
+  a.psi_out = ps;
   {
-    TimedScope ts("mr_reduce", s);
-    finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, 1, alpha, scale);
+    TimedScope ts("mr_last_update", s);
+    last_update<PAIRS><<<nsl * a.npatch, kSPC * PAIRS, 0, s>>>(a);
   }
-  const long n4 = g.V * 12L * (g.m / 2);
+  reduce(1);
   {
     TimedScope ts("mr_scale", s);
-    scale_kernel<<<1024, 256, 0, s>>>(p, scale, n4, g.m / 2);
+    scale_to_abi<PAIRS><<<2048, 256, 0, s>>>(ps, reinterpret_cast<float4*>(psi), scale, a.V, a.np);
   }
   return cudaGetLastError();
 }
@@ -582,6 +698,44 @@ cudaError_t launch_clover(const Geom& g, double csw, const float2* U, float2* C,
   TimedScope ts("clover", s);
   clover_kernel<<<(V + 127) / 128, 128, 0, s>>>(g.L[0], g.L[1], g.L[2], g.L[3], (float)csw, U, C);
   return cudaGetLastError();
+}
+
+template <int PAIRS>
+cudaError_t dirac_impl(const Geom& g, const float2* U, const float2* C, const float2* in,
+                       float2* out, char* ws, cudaStream_t s) {
+  const SmoothWs lay = smooth_ws_layout(g);
+  float4* tmp = reinterpret_cast<float4*>(ws + lay.ra);
+  float* scale = reinterpret_cast<float*>(ws + lay.scale);
+  MarchArgs a{};
+  a.U = U;
+  a.C = C;
+  for (int i = 0; i < 4; ++i) {
+    a.L[i] = g.L[i];
+    a.hw[i] = g.hw[i];
+  }
+  a.V = (int)g.V;
+  a.Vs = (int)(g.V / g.L[3]);
+  a.np = g.m / 2;
+  a.npatch = (a.Vs + kSPC - 1) / kSPC;
+  a.diag = g.diag;
+  a.in = reinterpret_cast<const float4*>(in);
+  a.in_abi = 1;
+  a.out = tmp;
+  cudaError_t e = run_march<PAIRS, MODE_NEG_D>(a, a.np / PAIRS, s);
+  if (e != cudaSuccess) return e;
+  {
+    TimedScope ts("fill", s);
+    fill_kernel<<<1, 64, 0, s>>>(scale, g.m, -1.0f);
+  }
+  TimedScope ts("mr_scale", s);
+  scale_to_abi<PAIRS><<<2048, 256, 0, s>>>(tmp, reinterpret_cast<float4*>(out), scale, a.V, a.np);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dirac(const Geom& g, const float2* U, const float2* C, const float2* in,
+                         float2* out, char* ws, cudaStream_t s) {
+  if (g.m % 8 == 0) return dirac_impl<4>(g, U, C, in, out, ws, s);
+  return dirac_impl<2>(g, U, C, in, out, ws, s);
 }
 
 cudaError_t launch_smoother(const Geom& g, const float2* U, const float2* C,

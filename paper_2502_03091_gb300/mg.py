@@ -25,7 +25,7 @@ MG_PREC_MIXED = 1
 MG_CALL_SMOOTH, MG_CALL_TRUNCATE, MG_CALL_COARSEN = 0, 1, 2
 
 # every symbol include/mg.h declares
-EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_smooth_testvecs", "mg_chiral_truncate",
+EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_apply_dirac", "mg_smooth_testvecs", "mg_chiral_truncate",
            "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply", "mg_chiral_truncate_static",
            "mg_timing_enable",
            "mg_timing_read", "mg_last_error", "mg_version")
@@ -110,13 +110,14 @@ def library(path: str = LIB_PATH):
     lib.mg_workspace_size.argtypes = [Pp, ctypes.c_int]
     lib.mg_workspace_size.restype = ctypes.c_size_t
     lib.mg_clover_field.argtypes = [Pp, P, P, P]
+    lib.mg_apply_dirac.argtypes = [Pp, P, P, P, P, P, ctypes.c_size_t, P]
     lib.mg_smooth_testvecs.argtypes = [Pp, P, P, P, P, P, ctypes.c_size_t, P]
     lib.mg_chiral_truncate.argtypes = [Pp, P, P, P, P, P, P, ctypes.c_size_t, P]
     lib.mg_chiral_truncate_static.argtypes = [Pp, P, P, P, P, P, P]
     lib.mg_build_prolongator.argtypes = [Pp, P, P, P]
     lib.mg_coarsen.argtypes = [Pp, P, P, P, P, P, P, ctypes.c_size_t, P]
     lib.mg_coarse_apply.argtypes = [Pp, P, P, P, P, ctypes.c_int32, P]
-    for f in ("mg_clover_field", "mg_smooth_testvecs", "mg_chiral_truncate",
+    for f in ("mg_clover_field", "mg_apply_dirac", "mg_smooth_testvecs", "mg_chiral_truncate",
               "mg_chiral_truncate_static", "mg_build_prolongator", "mg_coarsen",
               "mg_coarse_apply"):
         getattr(lib, f).restype = ctypes.c_int
@@ -236,6 +237,18 @@ def mg_clover_field(prob: Problem, U, C, stream=None):
     _expect(C, shape_C(prob), torch.complex64, "C")
     pc = prob.c()
     _check(library().mg_clover_field(ctypes.byref(pc), _ptr(U), _ptr(C), _stream(stream)))
+
+
+def mg_apply_dirac(prob: Problem, U, C, v_in, v_out, ws, stream=None):
+    """out = D in for n_vec right-hand sides ([V][4][3][n_vec] complex64)."""
+    import torch
+    _expect(U, shape_U(prob), torch.complex64, "U")
+    _expect(C, shape_C(prob), torch.complex64, "C")
+    _expect(v_in, shape_psi(prob), torch.complex64, "in")
+    _expect(v_out, shape_psi(prob), torch.complex64, "out")
+    pc = prob.c()
+    _check(library().mg_apply_dirac(ctypes.byref(pc), _ptr(U), _ptr(C), _ptr(v_in), _ptr(v_out),
+                                    _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def mg_smooth_testvecs(prob: Problem, U, C, psi0, psi, ws, stream=None):

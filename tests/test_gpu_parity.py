@@ -80,6 +80,23 @@ def test_clover_field(name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
+def test_dirac_apply(name):
+    """The multi-right-hand-side Wilson(-clover) operator against the oracle's."""
+    c = _case(name)
+    p = c["prob"]
+    U, C = _dev(c)
+    vin = to_dev(c["p0"])
+    out = torch.empty_like(vin)
+    mg.mg_apply_dirac(p, U, C, vin, out, mg.workspace(p, mg.MG_CALL_SMOOTH))
+    torch.cuda.synchronize()
+    ref = O.apply_D(c["dims"], c["m0"], c["xi"], c["U"], c["C"], c["p0"])
+    got = to_host(out)
+    err = np.linalg.norm((got - ref).reshape(-1, c["m"]), axis=0) / \
+        np.linalg.norm(ref.reshape(-1, c["m"]), axis=0)
+    assert err.max() <= 1e-6, err.max()
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_smoother(name):
     c = _case(name)
     p = c["prob"]
