@@ -84,9 +84,7 @@ SmoothWs smooth_ws_layout(const Geom& g) {
   const size_t field = sizeof(float2) * (size_t)g.V * 12 * g.m;
   size_t o = 0;
   w.ra = o; o = align256(o + field);
-  w.rb = o; o = align256(o + field);
   w.wa = o; o = align256(o + field);
-  w.wb = o; o = align256(o + field);
   w.ps = o; o = align256(o + field);
   // partial sums: one per (right-hand side, patch of 32 sites of a timeslice)
   const size_t npatch = ((size_t)(g.V / g.L[3]) + 31) / 32;

@@ -34,7 +34,7 @@ constexpr int kMaxK = 32;  // largest k this build supports
 // workspace layout (byte offsets, 256-aligned), see mg_abi.cu
 // ---------------------------------------------------------------------------
 struct SmoothWs {
-  size_t ra, rb, wa, wb, ps, part, alpha, scale, bytes;
+  size_t ra, wa, ps, part, alpha, scale, bytes;
 };
 struct TruncWs {
   size_t gram, r1, z1, w2, flags, bytes;

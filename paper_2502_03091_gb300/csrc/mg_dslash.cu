@@ -121,236 +121,269 @@ struct MarchArgs {
   float diag;
 };
 
-enum { MODE_NEG_D = 0, MODE_D_DOT = 1, MODE_FUSED = 2 };
+enum { MODE_NEG_D = 0, MODE_D_DOT = 1 };
 
 __device__ __forceinline__ long slab_index(int q, int V, int x, int e, int PAIRS, int p) {
   return (((long)q * V + x) * 12 + e) * PAIRS + p;
 }
 
-// one hop from a neighbour whose 12 components (this thread's pair) are at
-// src[e * es]: shared memory (already combined) or global (combined here)
-template <int MU, int S, bool SHARED, bool COMBINE>
-__device__ __forceinline__ void hop2(float4 acc[12], const float4* src, const float4* wsrc, int es,
-                                     const float2* __restrict__ u, float hw, float2 a0, float2 a1) {
+// One hop, split between two partner lanes (hf = 0, 1): lane hf forms the
+// half-spinor row h_hf = chi_hf - S (B chi_l)_hf (colour vector), multiplies
+// it by U (or U^dag) and accumulates into the two output spins it owns,
+// hf (upper) and 2 + hf (lower):
+//   upper: acc_u += hw g_hf,   lower: acc_l += -S hw (B^dag g)_hf,
+// where (B^dag g)_hf needs the partner's g for mu = x, y (one shuffle).
+//
+// load_half fetches the lane's inputs (chi_hf and the lower spin entering
+// (B chi_l)_hf) from a neighbour whose component e is at src[e * es]; src is
+// a generic pointer (shared-memory ring or global memory).
+template <int MU>
+__device__ __forceinline__ void load_half(const float4* src, int es, int hf, float4 up[3],
+                                          float4 dn[3]) {
+  const int lo = (MU == 0 || MU == 1) ? 1 - hf : hf;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    up[c] = src[(hf * 3 + c) * es];
+    dn[c] = src[((2 + lo) * 3 + c) * es];
+  }
+}
+
+template <int MU, int S>
+__device__ __forceinline__ void apply_half(float4 acc_u[3], float4 acc_l[3], int hf,
+                                           const float4 up[3], const float4 dn[3],
+                                           const float2* __restrict__ u, float hw) {
   float2 U[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) U[i] = __ldg(u + i);
-  float4 h[2][3];
+  float4 h[3];
 #pragma unroll
-  for (int sp = 0; sp < 2; ++sp) {
-    const int lo = (MU == 0 || MU == 1) ? 1 - sp : sp;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int eu = sp * 3 + c, ed = (2 + lo) * 3 + c;
-      float4 up, dn;
-      if (SHARED) {
-        up = src[eu * es];
-        dn = src[ed * es];
-      } else {
-        up = __ldg(src + eu * es);
-        dn = __ldg(src + ed * es);
-        if (COMBINE) {
-          up = f4sub(up, f4mul2(a0, a1, __ldg(wsrc + eu * es)));
-          dn = f4sub(dn, f4mul2(a0, a1, __ldg(wsrc + ed * es)));
-        }
-      }
-      const float4 bl = b_row<MU>(sp, dn);
-      h[sp][c] = S > 0 ? f4sub(up, bl) : f4add(up, bl);
-    }
+  for (int c = 0; c < 3; ++c) {
+    // (B chi_l)_hf: mu=x: -i chi_{3-hf}; mu=y: -chi_3 / +chi_2; mu=z: -i chi_2 / +i chi_3; t: chi_{2+hf}
+    float4 bl;
+    if (MU == 0) bl = f4mi(dn[c]);
+    else if (MU == 1) bl = hf == 0 ? f4neg(dn[c]) : dn[c];
+    else if (MU == 2) bl = hf == 0 ? f4mi(dn[c]) : f4i(dn[c]);
+    else bl = dn[c];
+    h[c] = S > 0 ? f4sub(up[c], bl) : f4add(up[c], bl);
   }
+  float4 g[3];
 #pragma unroll
-  for (int sp = 0; sp < 2; ++sp) {
-    float4 g[3];
+  for (int c = 0; c < 3; ++c) {
+    g[c] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      g[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (S > 0) f4cfma(g[c], U[c * 3 + d], h[sp][d]);
-        else f4cfmac(g[c], U[d * 3 + c], h[sp][d]);
-      }
+    for (int d = 0; d < 3; ++d) {
+      if (S > 0) f4cfma(g[c], U[c * 3 + d], h[d]);
+      else f4cfmac(g[c], U[d * 3 + c], h[d]);
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      h[sp][c] = g[c];
-      f4axpy(acc[sp * 3 + c], hw, g[c]);
-    }
+    f4axpy(acc_u[c], hw, g[c]);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    float4 o0, o1;
-    bdag_apply<MU>(h[0][c], h[1][c], o0, o1);
-    f4axpy(acc[6 + c], -S * hw, o0);
-    f4axpy(acc[9 + c], -S * hw, o1);
+    float4 v = g[c];
+    if (MU == 0 || MU == 1) {
+      v.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
+      v.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
+      v.z = __shfl_xor_sync(0xffffffffu, v.z, 1);
+      v.w = __shfl_xor_sync(0xffffffffu, v.w, 1);
+    }
+    // (B^dag g)_hf: x: i g_{1-hf}; y: g_1 / -g_0; z: i g_0 / -i g_1; t: g_hf
+    float4 b;
+    if (MU == 0) b = f4i(v);
+    else if (MU == 1) b = hf == 0 ? v : f4neg(v);
+    else if (MU == 2) b = hf == 0 ? f4i(v) : f4mi(v);
+    else b = v;
+    f4axpy(acc_l[c], -S * hw, b);
   }
 }
 
-// spatial hop mu (0..2) of the consumer at spatial index xyz, time t
-template <int MU, int S, int PAIRS, bool COMBINE>
-__device__ __forceinline__ void spatial_hop(float4 acc[12], const MarchArgs& a, const float4* ring_t,
-                                            int SS, int p0, int xyz, int nxyz, int t, int q, int p,
-                                            const float2* u, float2 a0, float2 a1) {
-  const int loc = nxyz - p0;
-  if (loc >= 0 && loc < kSPC && nxyz < a.Vs) {
-    hop2<MU, S, true, false>(acc, ring_t + loc * SS + p, nullptr, PAIRS, u, a.hw[MU], a0, a1);
-  } else if (a.in_abi) {
-    // the first pass reads psi_0 in the ABI layout [V][12][m'] (never combined)
-    const long o = ((long)(t * a.Vs + nxyz) * 12) * a.np + q * PAIRS + p;
-    hop2<MU, S, false, false>(acc, a.in + o, nullptr, a.np, u, a.hw[MU], a0, a1);
-  } else {
-    const long o = slab_index(q, a.V, t * a.Vs + nxyz, 0, PAIRS, p);
-    hop2<MU, S, false, COMBINE>(acc, a.in + o, COMBINE ? a.win + o : nullptr, PAIRS, u, a.hw[MU],
-                                a0, a1);
-  }
+template <int PAIRS>
+constexpr int march_threads() {
+  return 2 * kSPC * PAIRS;
 }
 
+// Dslash pass.  MODE_NEG_D: out = -D in (in = psi_0, ABI layout);
+// MODE_D_DOT: out = D in (in = r, slab) with partials <out, in>, |out|^2.
+// Each lane (site, pair, spin half hf) also stages its own 6 components of
+// ring row t+2: loads are issued before the compute of row t and stored into
+// the ring after the step's first barrier.
 template <int PAIRS, int MODE>
-__global__ void __launch_bounds__(2 * kSPC * PAIRS, 1) march_kernel(MarchArgs a) {
-  constexpr int NC = kSPC * PAIRS;     // consumer threads (= producer threads)
-  constexpr int SS = 12 * PAIRS + 4;   // padded ring site stride (float4)
-  constexpr int NW = NC / 32;          // consumer warps
-  constexpr bool COMBINE = MODE == MODE_FUSED;
-  extern __shared__ float4 ring[];     // [kRing][kSPC][SS]
+__global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchArgs a) {
+  constexpr int NC = 2 * kSPC * PAIRS;  // lanes: (site, pair, spin half)
+  constexpr int SS = 12 * PAIRS + 4;    // padded ring site stride (float4)
+  constexpr int NW = NC / 32;
+  extern __shared__ float4 ring[];      // [kRing][kSPC][SS]
   __shared__ double red[NW][PAIRS][6];
   const int q = blockIdx.x / a.npatch, patch = blockIdx.x % a.npatch;
   const int p0 = patch * kSPC;
-  const bool producer = threadIdx.x >= NC;
-  const int tid = producer ? threadIdx.x - NC : threadIdx.x;
-  const int s_loc = tid / PAIRS, p = tid % PAIRS;
+  const int Lt = a.L[3];
+  const int hf = threadIdx.x & 1;
+  const int sp_idx = threadIdx.x >> 1;
+  const int s_loc = sp_idx / PAIRS, p = sp_idx % PAIRS;
   const int gp = q * PAIRS + p;
   const int xyz = p0 + s_loc;
   const bool valid = xyz < a.Vs;
-  const int Lt = a.L[3];
-  float2 al0 = make_float2(0.f, 0.f), al1 = al0;
-  if (MODE == MODE_FUSED) {
-    al0 = a.alpha[2 * gp];
-    al1 = a.alpha[2 * gp + 1];
-  }
-
-  // producer: stage row r (-1 <= r <= Lt) of my site into its ring slot
-  auto stage = [&](int r) {
-    if (!valid) return;
-    const int tt = (r + Lt) % Lt;
-    const bool first = r >= 0 && r < Lt;
-    const int x = tt * a.Vs + xyz;
-    float4* dst = ring + ((r + 1) & 3) * kSPC * SS + s_loc * SS + p;
-    const long so = slab_index(q, a.V, x, 0, PAIRS, p);
-    const long ao = (long)x * 12 * a.np + gp;
+  const bool abi = MODE == MODE_NEG_D;  // input layout
+  const int ges = abi ? a.np : PAIRS;   // global component stride
+  int nf[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
+  {
+    int c[3];
+    int t = xyz;
+    c[0] = t % a.L[0]; t /= a.L[0];
+    c[1] = t % a.L[1]; c[2] = t / a.L[1];
+    const int sst[3] = {1, a.L[0], a.L[0] * a.L[1]};
 #pragma unroll
-    for (int e = 0; e < 12; ++e) {
-      float4 v;
-      if (MODE == MODE_NEG_D && a.in_abi) v = __ldg(a.in + ao + (long)e * a.np);
-      else v = __ldg(a.in + so + e * PAIRS);
-      if (COMBINE) {
-        const float4 sv = f4sub(v, f4mul2(al0, al1, __ldg(a.win + so + e * PAIRS)));
-        dst[e * PAIRS] = sv;
-        if (first) {
-          __stcs(a.r_out + so + e * PAIRS, sv);
-          const float4 pc = a.psi_abi ? __ldcs(a.psi_src + ao + (long)e * a.np)
-                                      : __ldcs(a.psi_src + so + e * PAIRS);
-          __stcs(a.psi_out + so + e * PAIRS, f4add(pc, f4mul2(al0, al1, v)));
-        }
-      } else {
-        dst[e * PAIRS] = v;
-      }
+    for (int mu = 0; mu < 3; ++mu) {
+      nf[mu] = c[mu] < a.L[mu] - 1 ? xyz + sst[mu] : xyz - (a.L[mu] - 1) * sst[mu];
+      nb[mu] = c[mu] > 0 ? xyz - sst[mu] : xyz + (a.L[mu] - 1) * sst[mu];
+    }
+  }
+  // global address of component 0 of site x for this lane's pair
+  auto gaddr = [&](int x) -> const float4* {
+    return abi ? a.in + (long)x * 12 * a.np + gp : a.in + slab_index(q, a.V, x, 0, PAIRS, p);
+  };
+  // staging of this lane's 6 components of row r (-1 <= r <= Lt)
+  auto stage_load = [&](int r, float4 sv[6]) {
+    if (!valid) return;
+    const float4* src = gaddr(((r + Lt) % Lt) * a.Vs + xyz);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
+      sv[k] = __ldg(src + e * ges);
+    }
+  };
+  auto stage_store = [&](int r, const float4 sv[6]) {
+    if (!valid) return;
+    float4* dst = ring + ((r + 1) & 3) * kSPC * SS + s_loc * SS + p;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
+      dst[e * PAIRS] = sv[k];
     }
   };
 
-  int cxyz[3] = {0, 0, 0};  // spatial coordinates of my site
-  {
-    int t = xyz;
-    cxyz[0] = t % a.L[0]; t /= a.L[0];
-    cxyz[1] = t % a.L[1]; cxyz[2] = t / a.L[1];
-  }
-  const int sst[3] = {1, a.L[0], a.L[0] * a.L[1]};
-  int nf[3], nb[3];
-#pragma unroll
-  for (int mu = 0; mu < 3; ++mu) {
-    nf[mu] = cxyz[mu] < a.L[mu] - 1 ? xyz + sst[mu] : xyz - (a.L[mu] - 1) * sst[mu];
-    nb[mu] = cxyz[mu] > 0 ? xyz - sst[mu] : xyz + (a.L[mu] - 1) * sst[mu];
-  }
-
   double pr[6] = {0, 0, 0, 0, 0, 0};
-  if (producer) {
-    stage(-1);
-    stage(0);
-    if (Lt > 1) stage(1);
-    else stage(1);  // Lt == 1: row 1 is row 0 again (no side effects)
+  {
+    float4 sv[6];
+    for (int r = -1; r <= 1; ++r) {
+      stage_load(r, sv);
+      stage_store(r, sv);
+    }
   }
   __syncthreads();
   for (int t = 0; t < Lt; ++t) {
-    if (producer) {
-      if (t + 2 <= Lt) stage(t + 2);
-    } else if (valid) {
+    float4 sv[6];
+    const bool do_stage = t + 2 <= Lt;
+    if (do_stage) stage_load(t + 2, sv);
+    {
+      // every lane takes part in the shuffles; lanes of an invalid site
+      // compute on site p0 and discard the result
+      const int xyzc = valid ? xyz : p0;
       const float4* ring_t = ring + ((t + 1) & 3) * kSPC * SS;
       const float4* ring_f = ring + ((t + 2) & 3) * kSPC * SS;
       const float4* ring_b = ring + (t & 3) * kSPC * SS;
-      const int x = t * a.Vs + xyz;
+      const int sl = xyzc - p0;
+      const int x = t * a.Vs + xyzc;
       const int tb = (t - 1 + Lt) % Lt;
-      float4 z[12], cen[12];
+      const float4* cen = ring_t + sl * SS + p;  // component e at cen[e * PAIRS]
+      float4 zu[3], zl[3];
 #pragma unroll
-      for (int e = 0; e < 12; ++e) {
-        cen[e] = ring_t[s_loc * SS + e * PAIRS + p];
-        z[e] = make_float4(a.diag * cen[e].x, a.diag * cen[e].y, a.diag * cen[e].z,
-                           a.diag * cen[e].w);
+      for (int c = 0; c < 3; ++c) {
+        const float4 cu = cen[(hf * 3 + c) * PAIRS], cl4 = cen[((2 + hf) * 3 + c) * PAIRS];
+        zu[c] = make_float4(a.diag * cu.x, a.diag * cu.y, a.diag * cu.z, a.diag * cu.w);
+        zl[c] = make_float4(a.diag * cl4.x, a.diag * cl4.y, a.diag * cl4.z, a.diag * cl4.w);
       }
       if (a.C) {
+        // row (alpha, spin hf, colour c) of the chirality-alpha 6x6 block
         const float2* cl = a.C + (long)x * 72;
 #pragma unroll
-        for (int al = 0; al < 2; ++al)
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = 0; j < 6; ++j)
-              f4cfma(z[6 * al + i], __ldg(cl + al * 36 + i * 6 + j), cen[6 * al + j]);
+          for (int j = 0; j < 6; ++j) {
+            f4cfma(zu[c], __ldg(cl + (hf * 3 + c) * 6 + j), cen[j * PAIRS]);
+            f4cfma(zl[c], __ldg(cl + 36 + (hf * 3 + c) * 6 + j), cen[(6 + j) * PAIRS]);
+          }
       }
       const float2* Ux = a.U + (long)x * 36;
-      spatial_hop<0, +1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nf[0], t, q, p, Ux + 0, al0, al1);
-      spatial_hop<0, -1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nb[0], t, q, p,
-                                         a.U + ((long)t * a.Vs + nb[0]) * 36 + 0, al0, al1);
-      spatial_hop<1, +1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nf[1], t, q, p, Ux + 9, al0, al1);
-      spatial_hop<1, -1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nb[1], t, q, p,
-                                         a.U + ((long)t * a.Vs + nb[1]) * 36 + 9, al0, al1);
-      spatial_hop<2, +1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nf[2], t, q, p, Ux + 18, al0, al1);
-      spatial_hop<2, -1, PAIRS, COMBINE>(z, a, ring_t, SS, p0, xyz, nb[2], t, q, p,
-                                         a.U + ((long)t * a.Vs + nb[2]) * 36 + 18, al0, al1);
-      hop2<3, +1, true, false>(z, ring_f + s_loc * SS + p, nullptr, PAIRS, Ux + 27, a.hw[3], al0, al1);
-      hop2<3, -1, true, false>(z, ring_b + s_loc * SS + p, nullptr, PAIRS,
-                               a.U + ((long)tb * a.Vs + xyz) * 36 + 27, a.hw[3], al0, al1);
-      const long so = slab_index(q, a.V, x, 0, PAIRS, p);
-      if (MODE == MODE_NEG_D) {
+      const long tV = (long)t * a.Vs;
 #pragma unroll
-        for (int e = 0; e < 12; ++e) __stcs(a.out + so + e * PAIRS, f4neg(z[e]));
-      } else {
-        float s6[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-        for (int e = 0; e < 12; ++e) {
-          const float4 w = z[e], r = cen[e];
-          s6[0] += w.x * r.x + w.y * r.y;
-          s6[1] += w.x * r.y - w.y * r.x;
-          s6[2] += w.x * w.x + w.y * w.y;
-          s6[3] += w.z * r.z + w.w * r.w;
-          s6[4] += w.z * r.w - w.w * r.z;
-          s6[5] += w.z * w.z + w.w * w.w;
-          __stcs(a.out + so + e * PAIRS, w);
+      for (int mu = 0; mu < 3; ++mu) {
+        // forward and backward neighbours: ring if inside the patch, else global
+        const int f = valid ? nf[mu] : p0, b = valid ? nb[mu] : p0;
+        const int lf = f - p0, lb = b - p0;
+        const bool rf = lf >= 0 && lf < kSPC && f < a.Vs, rb = lb >= 0 && lb < kSPC && b < a.Vs;
+        const float4* pf = rf ? ring_t + lf * SS + p : gaddr(t * a.Vs + f);
+        const float4* pb = rb ? ring_t + lb * SS + p : gaddr(t * a.Vs + b);
+        const int esf = rf ? PAIRS : ges, esb = rb ? PAIRS : ges;
+        float4 uf[3], df[3], ub[3], db[3];
+        if (mu == 0) {
+          load_half<0>(pf, esf, hf, uf, df);
+          load_half<0>(pb, esb, hf, ub, db);
+          apply_half<0, +1>(zu, zl, hf, uf, df, Ux + 0, a.hw[0]);
+          apply_half<0, -1>(zu, zl, hf, ub, db, a.U + (tV + b) * 36 + 0, a.hw[0]);
+        } else if (mu == 1) {
+          load_half<1>(pf, esf, hf, uf, df);
+          load_half<1>(pb, esb, hf, ub, db);
+          apply_half<1, +1>(zu, zl, hf, uf, df, Ux + 9, a.hw[1]);
+          apply_half<1, -1>(zu, zl, hf, ub, db, a.U + (tV + b) * 36 + 9, a.hw[1]);
+        } else {
+          load_half<2>(pf, esf, hf, uf, df);
+          load_half<2>(pb, esb, hf, ub, db);
+          apply_half<2, +1>(zu, zl, hf, uf, df, Ux + 18, a.hw[2]);
+          apply_half<2, -1>(zu, zl, hf, ub, db, a.U + (tV + b) * 36 + 18, a.hw[2]);
         }
+      }
+      {
+        float4 uf[3], df[3], ub[3], db[3];
+        load_half<3>(ring_f + sl * SS + p, PAIRS, hf, uf, df);
+        load_half<3>(ring_b + sl * SS + p, PAIRS, hf, ub, db);
+        apply_half<3, +1>(zu, zl, hf, uf, df, Ux + 27, a.hw[3]);
+        apply_half<3, -1>(zu, zl, hf, ub, db, a.U + ((long)tb * a.Vs + xyzc) * 36 + 27, a.hw[3]);
+      }
+      if (valid) {
+        const long so = slab_index(q, a.V, x, 0, PAIRS, p);
+        const int eu = hf * 3, el = (2 + hf) * 3;
+        if (MODE == MODE_NEG_D) {
 #pragma unroll
-        for (int i = 0; i < 6; ++i) pr[i] += (double)s6[i];
+          for (int c = 0; c < 3; ++c) {
+            __stcs(a.out + so + (eu + c) * PAIRS, f4neg(zu[c]));
+            __stcs(a.out + so + (el + c) * PAIRS, f4neg(zl[c]));
+          }
+        } else {
+          float s6[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            const int e = k < 3 ? eu + k : el + k - 3;
+            const float4 w = k < 3 ? zu[k] : zl[k - 3], r = cen[e * PAIRS];
+            s6[0] += w.x * r.x + w.y * r.y;
+            s6[1] += w.x * r.y - w.y * r.x;
+            s6[2] += w.x * w.x + w.y * w.y;
+            s6[3] += w.z * r.z + w.w * r.w;
+            s6[4] += w.z * r.w - w.w * r.z;
+            s6[5] += w.z * w.z + w.w * w.w;
+            __stcs(a.out + so + e * PAIRS, w);
+          }
+#pragma unroll
+          for (int i = 0; i < 6; ++i) pr[i] += (double)s6[i];
+        }
       }
     }
+    // row t+2 goes into the slot of row t-2 (free once every lane is past step t)
+    __syncthreads();
+    if (do_stage) stage_store(t + 2, sv);
     __syncthreads();
   }
   if (MODE != MODE_NEG_D) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (!producer) {
+    // lane = 2 * (s * PAIRS + p) + hf: sum over hf and s, keep p
 #pragma unroll
-      for (int off = 16; off >= PAIRS; off >>= 1)
+    for (int i = 0; i < 6; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], 1);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], off);
-      if (lane < PAIRS)
+    for (int off = 16; off >= 2 * PAIRS; off >>= 1)
 #pragma unroll
-        for (int i = 0; i < 6; ++i) red[warp][lane][i] = pr[i];
-    }
+      for (int i = 0; i < 6; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], off);
+    if (lane < 2 * PAIRS && (lane & 1) == 0)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) red[warp][lane >> 1][i] = pr[i];
     __syncthreads();
     if (threadIdx.x < PAIRS) {
       double tt[6];
@@ -365,6 +398,31 @@ __global__ void __launch_bounds__(2 * kSPC * PAIRS, 1) march_kernel(MarchArgs a)
       q0[0] = tt[0]; q0[1] = tt[1]; q0[2] = tt[2];
       q1[0] = tt[3]; q1[1] = tt[4]; q1[2] = tt[5];
     }
+  }
+}
+
+// MR update between two dslash passes (streaming, slab layout):
+//   r <- r - a w  (r_{t+1}),   psi_out <- psi_src + a r_t   (psi_src in the ABI
+// layout for psi_0).  One float4 (two right-hand sides) per thread.
+template <int PAIRS>
+__global__ void mr_update(float4* __restrict__ r, const float4* __restrict__ w,
+                          const float4* __restrict__ psi_src, float4* __restrict__ psi_out,
+                          const float2* __restrict__ alpha, int V, int np, int psi_abi) {
+  const long n = (long)V * 12 * np;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    const int p = (int)(i % PAIRS);
+    long rr = i / PAIRS;
+    const int e = (int)(rr % 12);
+    rr /= 12;
+    const int x = (int)(rr % V);
+    const int q = (int)(rr / V);
+    const int gp = q * PAIRS + p;
+    const float2 a0 = alpha[2 * gp], a1 = alpha[2 * gp + 1];
+    const float4 rv = __ldcs(r + i), wv = __ldcs(w + i);
+    const float4 pv = psi_abi ? __ldcs(psi_src + ((long)x * 12 + e) * np + gp) : __ldcs(psi_src + i);
+    __stcs(r + i, f4sub(rv, f4mul2(a0, a1, wv)));
+    __stcs(psi_out + i, f4add(pv, f4mul2(a0, a1, rv)));
   }
 }
 
@@ -599,7 +657,7 @@ __global__ void clover_kernel(int L0, int L1, int L2, int L3, float csw,
 
 template <int PAIRS, int MODE>
 cudaError_t run_march(const MarchArgs& a, int nsl, cudaStream_t s) {
-  static const char* names[3] = {"mr_neg_dslash", "mr_dslash_dot", "mr_fused_iteration"};
+  static const char* names[2] = {"mr_neg_dslash", "mr_dslash_dot"};
   constexpr int SS = 12 * PAIRS + 4;
   const size_t smem = sizeof(float4) * (size_t)kRing * kSPC * SS;
   static bool attr = false;
@@ -609,7 +667,7 @@ cudaError_t run_march(const MarchArgs& a, int nsl, cudaStream_t s) {
     attr = true;
   }
   TimedScope ts(names[MODE], s);
-  march_kernel<PAIRS, MODE><<<nsl * a.npatch, 2 * kSPC * PAIRS, smem, s>>>(a);
+  march_kernel<PAIRS, MODE><<<nsl * a.npatch, march_threads<PAIRS>(), smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -617,8 +675,8 @@ template <int PAIRS>
 cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const float2* psi0,
                           float2* psi, char* ws, cudaStream_t s) {
   const SmoothWs lay = smooth_ws_layout(g);
-  float4* r[2] = {reinterpret_cast<float4*>(ws + lay.ra), reinterpret_cast<float4*>(ws + lay.rb)};
-  float4* w[2] = {reinterpret_cast<float4*>(ws + lay.wa), reinterpret_cast<float4*>(ws + lay.wb)};
+  float4* r = reinterpret_cast<float4*>(ws + lay.ra);
+  float4* w = reinterpret_cast<float4*>(ws + lay.wa);
   float4* ps = reinterpret_cast<float4*>(ws + lay.ps);
   double* part = reinterpret_cast<double*>(ws + lay.part);
   float2* alpha = reinterpret_cast<float2*>(ws + lay.alpha);
@@ -650,31 +708,25 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
 
   // r_0 = -D psi_0  (psi_0 in the ABI layout)
   a.in = p0;
-  a.in_abi = 1;
-  a.out = r[0];
+  a.out = r;
   if ((e = run_march<PAIRS, MODE_NEG_D>(a, nsl, s)) != cudaSuccess) return e;
   // w_0 = D r_0 -> a_0
-  a.in = r[0];
-  a.in_abi = 0;
-  a.out = w[0];
+  a.in = r;
+  a.out = w;
   if ((e = run_march<PAIRS, MODE_D_DOT>(a, nsl, s)) != cudaSuccess) return e;
   reduce(0);
-  int cur = 0;
   for (int t = 1; t < g.niter; ++t) {
-    // r_t = r_{t-1} - a w_{t-1}, w_t = D r_t, psi_t = psi_{t-1} + a r_{t-1} -> a_t
-    a.in = r[cur];
-    a.win = w[cur];
-    a.psi_src = t == 1 ? p0 : ps;
-    a.psi_abi = t == 1;
-    a.out = w[cur ^ 1];
-    a.r_out = r[cur ^ 1];
-    a.psi_out = ps;
-    if ((e = run_march<PAIRS, MODE_FUSED>(a, nsl, s)) != cudaSuccess) return e;
+    // r_t = r_{t-1} - a w_{t-1}, psi_t = psi_{t-1} + a r_{t-1}; w_t = D r_t -> a_t
+    {
+      TimedScope ts("mr_update", s);
+      mr_update<PAIRS><<<4096, 256, 0, s>>>(r, w, t == 1 ? p0 : ps, ps, alpha, a.V, a.np,
+                                            t == 1 ? 1 : 0);
+    }
+    if ((e = run_march<PAIRS, MODE_D_DOT>(a, nsl, s)) != cudaSuccess) return e;
     reduce(0);
-    cur ^= 1;
   }
   // psi_N = psi_{N-1} + a_{N-1} r_{N-1}, partial |psi_N|^2
-  a.in = r[cur];
+  a.in = r;
   a.psi_src = g.niter == 1 ? p0 : ps;
   a.psi_abi = g.niter == 1;
   a.psi_out = ps;
@@ -687,16 +739,6 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
     TimedScope ts("mr_scale", s);
     scale_to_abi<PAIRS><<<2048, 256, 0, s>>>(ps, reinterpret_cast<float4*>(psi), scale, a.V, a.np);
   }
-  return cudaGetLastError();
-}
-
-}  // namespace
-
-cudaError_t launch_clover(const Geom& g, double csw, const float2* U, float2* C,
-                          cudaStream_t s) {
-  const int V = (int)g.V;
-  TimedScope ts("clover", s);
-  clover_kernel<<<(V + 127) / 128, 128, 0, s>>>(g.L[0], g.L[1], g.L[2], g.L[3], (float)csw, U, C);
   return cudaGetLastError();
 }
 
@@ -729,6 +771,16 @@ cudaError_t dirac_impl(const Geom& g, const float2* U, const float2* C, const fl
   }
   TimedScope ts("mr_scale", s);
   scale_to_abi<PAIRS><<<2048, 256, 0, s>>>(tmp, reinterpret_cast<float4*>(out), scale, a.V, a.np);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_clover(const Geom& g, double csw, const float2* U, float2* C,
+                          cudaStream_t s) {
+  const int V = (int)g.V;
+  TimedScope ts("clover", s);
+  clover_kernel<<<(V + 127) / 128, 128, 0, s>>>(g.L[0], g.L[1], g.L[2], g.L[3], (float)csw, U, C);
   return cudaGetLastError();
 }
 
