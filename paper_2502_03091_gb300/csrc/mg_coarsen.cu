@@ -15,8 +15,6 @@
 namespace mg {
 namespace {
 
-constexpr int kCoarsenThreads = 256;
-constexpr int kSitesPerStage = 4;
 
 __global__ void prolongator_kernel(const float2* __restrict__ Uk, float2* __restrict__ P, int L0,
                                    int L1, int L2, int L3, int b0, int b1, int b2, int b3,
@@ -79,134 +77,144 @@ __device__ __forceinline__ float2 bent(int mu, int s, int t) {
   return s == t ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
 }
 
-// One CTA per block j.  Each active thread owns a 4x4 tile of the 2k x 2k
-// coarse matrices (NP = 2k rounded up to 4).  Per stage, kSitesPerStage sites
-// are staged: for every site the depth-6 left factor Pi(x) and right factor
-// W(x) = hw U_mu(x) Pi(x+mu) go to shared memory (depth 12 for the
-// diagonal/clover term, with W = 1/2 M(x) P(x)).
-__global__ void __launch_bounds__(kCoarsenThreads) coarsen_kernel(CoarsenArgs a) {
-  extern __shared__ float2 sm[];
-  const int k = a.k, n2 = 2 * k, NP = (n2 + 3) & ~3, TT = NP / 4;
-  float2* Ls = sm;                          // [kSitesPerStage][12][NP]
-  float2* Rs = Ls + kSitesPerStage * 12 * NP;  // [kSitesPerStage][12][NP]
-  float2* Ts = Rs + kSitesPerStage * 12 * NP;  // [NP][NP] transpose scratch
-  __shared__ int s_face[kSitesPerStage];
-  const int j = blockIdx.x;
-  const int tid = threadIdx.x;
-  const bool active = tid < TT * TT;
-  const int ti = tid / TT, tj = tid % TT;
-  float2 A[4][4];  // X half: 1/2 M-term + interior hops
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) A[p][q] = make_float2(0.f, 0.f);
+// Coarsening as register-tiled complex GEMMs.  One CTA (16 x 16 threads) per
+// block j.  Thread (ti, tj) owns the T x T output entries
+// (a*16 + ti, b*16 + tj), a, b < T, of every 2k x 2k matrix (2k <= 16 T).
+// For each pass the block's sites are processed in chunks of kChunk sites; the
+// chunk's depth-6 left factor L (6 x 2k per site) and right factor R go to
+// shared memory, then every thread accumulates conj(L)^T R into its tile:
+//   passes 0, 1 (chirality alpha): L = P_alpha(x), R = 1/2 (m0 + sum w + C_alpha(x)) P_alpha(x)
+//     (columns of the other chirality are zero);
+//   passes 2..5 (mu = 0..3):       L = Pi_mu(x), R = hw_mu U_mu(x) Pi_mu(x + mu),
+//     added to the interior sum S or, for sites on the block's +mu face, to Y_{+mu}.
+// At the end X = S + sigma_3 S^dag sigma_3 (the 1/2 on the diagonal term makes
+// its two halves add up), and Y_{-mu}(j + mu) = sigma_3 Y_{+mu}(j)^dag sigma_3.
+constexpr int kChunk = 16;
 
-  // pass -1: diagonal + clover, pass mu = 0..3: hops
-  for (int pass = -1; pass < 4; ++pass) {
-    const int depth = pass < 0 ? 12 : 6;
-    float2 Yacc[4][4];
+// Each row sp of B_mu has a single non-zero B_mu[sp][t]; Pi_mu uses -B_mu, so
+// the lower-chirality columns of Pi_mu(z) are g * P_1(z)[t] with g = -B_mu[sp][t].
+__device__ __forceinline__ void pi_entry(int mu, int sp, int& t, float2& g) {
+  if (mu == 0) { t = 1 - sp; g = make_float2(0.f, 1.f); }                          // -(-i)
+  else if (mu == 1) { t = 1 - sp; g = make_float2(sp == 0 ? 1.f : -1.f, 0.f); }    // -(-1), -(+1)
+  else if (mu == 2) { t = sp; g = make_float2(0.f, sp == 0 ? 1.f : -1.f); }        // -(-i), -(+i)
+  else { t = sp; g = make_float2(-1.f, 0.f); }
+}
+
+template <int T>
+__global__ void __launch_bounds__(256, 2) coarsen_kernel(CoarsenArgs a) {
+  constexpr int NP = 16 * T;  // padded 2k
+  extern __shared__ float2 sm[];
+  float2* Lf = sm;                        // [kChunk][6][NP]
+  float2* Rf = Lf + kChunk * 6 * NP;      // [kChunk][6][NP]
+  float2* Tr = Rf + kChunk * 6 * NP;      // [NP][NP + 1] transpose scratch
+  __shared__ int s_face[kChunk], s_site[kChunk], s_nbr[kChunk];
+  const int k = a.k, n2 = 2 * k;
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  float2 S[T][T];
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < T; ++p)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) Yacc[p][q] = make_float2(0.f, 0.f);
-    for (int s0 = 0; s0 < a.nb; s0 += kSitesPerStage) {
+    for (int q = 0; q < T; ++q) S[p][q] = make_float2(0.f, 0.f);
+
+  for (int pass = 0; pass < 6; ++pass) {
+    const int mu = pass - 2;
+    float2 Yc[T][T];
+#pragma unroll
+    for (int p = 0; p < T; ++p)
+#pragma unroll
+      for (int q = 0; q < T; ++q) Yc[p][q] = make_float2(0.f, 0.f);
+    for (int s0 = 0; s0 < a.nb; s0 += kChunk) {
       __syncthreads();
-      // build the factors
-      for (int idx = tid; idx < kSitesPerStage * depth * NP; idx += blockDim.x) {
-        const int ls = idx / (depth * NP), rem = idx % (depth * NP);
+      if (tid < kChunk) {
+        const int loc = s0 + tid;
+        int xo[4];
+        const int x = loc < a.nb ? site_of(a, j, loc, xo) : -1;
+        s_site[tid] = x;
+        s_face[tid] = (x >= 0 && mu >= 0) ? (xo[mu] % a.b[mu]) == a.b[mu] - 1 : 0;
+        if (x >= 0 && mu >= 0) {
+          xo[mu] = (xo[mu] + 1) % a.L[mu];
+          s_nbr[tid] = xo[0] + a.L[0] * (xo[1] + a.L[1] * (xo[2] + a.L[2] * xo[3]));
+        } else {
+          s_nbr[tid] = x;
+        }
+      }
+      __syncthreads();
+      // stage L and R for the chunk
+      for (int idx = tid; idx < kChunk * 6 * NP; idx += 256) {
+        const int ls = idx / (6 * NP), rem = idx % (6 * NP);
         const int e = rem / NP, col = rem % NP;
-        const int loc = s0 + ls;
+        const int x = s_site[ls];
         float2 lv = make_float2(0.f, 0.f), rv = lv;
-        if (loc < a.nb && col < n2) {
-          int xo[4];
-          const int x = site_of(a, j, loc, xo);
+        if (x >= 0 && col < n2) {
           const int al = col / k, i = col % k;
           const float2* Px = a.P + (long)x * 12 * k;  // [2][6][k]
-          if (pass < 0) {
-            // rows e = (alpha_r, spin, colour) of the 12 x 2k chirality-sparse P(x)
-            const int ar = e / 6, er = e % 6;
-            lv = ar == al ? Px[(al * 6 + er) * k + i] : make_float2(0.f, 0.f);
-            if (ar == al) {
-              float2 s = cscale(Px[(al * 6 + er) * k + i], 0.5f * a.diag);
+          if (mu < 0) {
+            const int ar = pass;  // chirality of this pass
+            if (al == ar) {
+              lv = __ldg(Px + (ar * 6 + e) * k + i);
+              float2 sacc = cscale(lv, 0.5f * a.diag);
               if (a.C) {
-                const float2* cl = a.C + (long)x * 72 + al * 36 + er * 6;
-                for (int f = 0; f < 6; ++f) cfma(s, cscale(cl[f], 0.5f), Px[(al * 6 + f) * k + i]);
+                const float2* cl = a.C + (long)x * 72 + ar * 36 + e * 6;
+#pragma unroll
+                for (int f = 0; f < 6; ++f)
+                  cfma(sacc, cscale(__ldg(cl + f), 0.5f), __ldg(Px + (ar * 6 + f) * k + i));
               }
-              rv = s;
+              rv = sacc;
             }
-            if (idx % (depth * NP) == 0) s_face[ls] = 0;
           } else {
-            const int mu = pass;
             const int sp = e / 3, c = e % 3;
-            // Pi(x)[sp][c][col]
-            if (al == 0) {
-              lv = Px[(0 * 6 + sp * 3 + c) * k + i];
-            } else {
-              float2 s = make_float2(0.f, 0.f);
-              for (int t = 0; t < 2; ++t) cfma(s, bent(mu, sp, t), Px[(6 + t * 3 + c) * k + i]);
-              lv = make_float2(-s.x, -s.y);
-            }
-            // W(x) = hw U_mu(x) Pi(x+mu)
-            int y[4] = {xo[0], xo[1], xo[2], xo[3]};
-            y[mu] = (y[mu] + 1) % a.L[mu];
-            const int xy = y[0] + a.L[0] * (y[1] + a.L[1] * (y[2] + a.L[2] * y[3]));
-            const float2* Py = a.P + (long)xy * 12 * k;
+            int tt;
+            float2 gph;
+            pi_entry(mu, sp, tt, gph);
+            // Pi_mu(z)[sp][d][col]: offset of the P entry and its phase
+            const int off = al == 0 ? (sp * 3) * k + i : (6 + tt * 3) * k + i;
+            const float2 ph = al == 0 ? make_float2(1.f, 0.f) : gph;
+            lv = cmul(ph, __ldg(Px + off + c * k));
+            const float2* Py = a.P + (long)s_nbr[ls] * 12 * k + off;
             const float2* u = a.U + ((long)x * 4 + mu) * 9 + c * 3;
-            float2 s = make_float2(0.f, 0.f);
-            for (int d = 0; d < 3; ++d) {
-              float2 pid;
-              if (al == 0) {
-                pid = Py[(sp * 3 + d) * k + i];
-              } else {
-                float2 q = make_float2(0.f, 0.f);
-                for (int t = 0; t < 2; ++t) cfma(q, bent(mu, sp, t), Py[(6 + t * 3 + d) * k + i]);
-                pid = make_float2(-q.x, -q.y);
-              }
-              cfma(s, u[d], pid);
-            }
-            rv = cscale(s, a.hw[mu]);
-            if (idx % (depth * NP) == 0) s_face[ls] = (xo[mu] % a.b[mu]) == a.b[mu] - 1;
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cfma(acc, __ldg(u + d), __ldg(Py + d * k));
+            rv = cscale(cmul(ph, acc), a.hw[mu]);
           }
         }
-        Ls[(ls * 12 + e) * NP + col] = lv;
-        Rs[(ls * 12 + e) * NP + col] = rv;
+        Lf[idx] = lv;
+        Rf[idx] = rv;
       }
       __syncthreads();
-      if (active) {
-        for (int ls = 0; ls < kSitesPerStage && s0 + ls < a.nb; ++ls) {
-          const bool face = pass >= 0 && s_face[ls];
-          float2 t[4][4];
+      // accumulate conj(L)^T R into the tile
+      for (int ls = 0; ls < kChunk; ++ls) {
+        if (s_site[ls] < 0) break;
+        const bool face = s_face[ls];
+        float2 t[T][T];
 #pragma unroll
-          for (int p = 0; p < 4; ++p)
+        for (int p = 0; p < T; ++p)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) t[p][q] = make_float2(0.f, 0.f);
-          for (int e = 0; e < depth; ++e) {
-            const float2* lr = Ls + (ls * 12 + e) * NP;
-            const float2* rr = Rs + (ls * 12 + e) * NP;
-            float2 lv[4], rv[4];
+          for (int q = 0; q < T; ++q) t[p][q] = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              lv[p] = lr[4 * ti + p];
-              rv[p] = rr[4 * tj + p];
-            }
+        for (int e = 0; e < 6; ++e) {
+          float2 lv[T], rv[T];
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
+          for (int p = 0; p < T; ++p) lv[p] = Lf[(ls * 6 + e) * NP + p * 16 + ti];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) cfmac(t[p][q], lv[p], rv[q]);
-          }
+          for (int q = 0; q < T; ++q) rv[q] = Rf[(ls * 6 + e) * NP + q * 16 + tj];
 #pragma unroll
-          for (int p = 0; p < 4; ++p)
+          for (int p = 0; p < T; ++p)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              if (face) Yacc[p][q] = cadd(Yacc[p][q], t[p][q]);
-              else A[p][q] = cadd(A[p][q], t[p][q]);
-            }
+            for (int q = 0; q < T; ++q) cfmac(t[p][q], lv[p], rv[q]);
         }
+#pragma unroll
+        for (int p = 0; p < T; ++p)
+#pragma unroll
+          for (int q = 0; q < T; ++q) {
+            if (face) Yc[p][q] = cadd(Yc[p][q], t[p][q]);
+            else S[p][q] = cadd(S[p][q], t[p][q]);
+          }
       }
     }
-    if (pass >= 0) {
+    if (mu >= 0) {
       // Y_{+mu}(j) and Y_{-mu}(j + mu) = sigma_3 Y_{+mu}(j)^dag sigma_3
-      const int mu = pass;
       int jc[4];
       {
         int t = j;
@@ -217,39 +225,35 @@ __global__ void __launch_bounds__(kCoarsenThreads) coarsen_kernel(CoarsenArgs a)
       jc[mu] = (jc[mu] + 1) % a.Lc[mu];
       const int jn = jc[0] + a.Lc[0] * (jc[1] + a.Lc[1] * (jc[2] + a.Lc[2] * jc[3]));
       __syncthreads();
-      if (active) {
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < T; ++p)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int r = 4 * ti + p, c = 4 * tj + q;
-            Ts[r * NP + c] = Yacc[p][q];
-            if (r < n2 && c < n2) a.Y[(((long)j * 8 + mu) * n2 + r) * n2 + c] = Yacc[p][q];
-          }
-      }
+        for (int q = 0; q < T; ++q) {
+          const int r = p * 16 + ti, c = q * 16 + tj;
+          Tr[r * (NP + 1) + c] = Yc[p][q];
+          if (r < n2 && c < n2) a.Y[(((long)j * 8 + mu) * n2 + r) * n2 + c] = Yc[p][q];
+        }
       __syncthreads();
-      for (int idx = tid; idx < n2 * n2; idx += blockDim.x) {
+      for (int idx = tid; idx < n2 * n2; idx += 256) {
         const int r = idx / n2, c = idx % n2;
-        float2 v = cconj(Ts[c * NP + r]);
+        float2 v = cconj(Tr[c * (NP + 1) + r]);
         if ((r < k) != (c < k)) v = make_float2(-v.x, -v.y);
         a.Y[(((long)jn * 8 + 4 + mu) * n2 + r) * n2 + c] = v;
       }
     }
   }
-  // X = A + sigma_3 A^dag sigma_3
+  // X = S + sigma_3 S^dag sigma_3
   __syncthreads();
-  if (active) {
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < T; ++p)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) Ts[(4 * ti + p) * NP + 4 * tj + q] = A[p][q];
-  }
+    for (int q = 0; q < T; ++q) Tr[(p * 16 + ti) * (NP + 1) + q * 16 + tj] = S[p][q];
   __syncthreads();
-  for (int idx = tid; idx < n2 * n2; idx += blockDim.x) {
+  for (int idx = tid; idx < n2 * n2; idx += 256) {
     const int r = idx / n2, c = idx % n2;
-    float2 v = cconj(Ts[c * NP + r]);
+    float2 v = cconj(Tr[c * (NP + 1) + r]);
     if ((r < k) != (c < k)) v = make_float2(-v.x, -v.y);
-    a.X[((long)j * n2 + r) * n2 + c] = cadd(Ts[r * NP + c], v);
+    a.X[((long)j * n2 + r) * n2 + c] = cadd(Tr[r * (NP + 1) + c], v);
   }
 }
 
@@ -302,6 +306,21 @@ cudaError_t launch_prolongator(const Geom& g, const float2* Uk, float2* P, cudaS
   return cudaGetLastError();
 }
 
+template <int T>
+cudaError_t coarsen_t(const CoarsenArgs& a, int nblk, cudaStream_t s) {
+  constexpr int NP = 16 * T;
+  const size_t smem = sizeof(float2) * (size_t)(2 * kChunk * 6 * NP + NP * (NP + 1));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(coarsen_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr = true;
+  }
+  TimedScope ts("coarsen", s);
+  coarsen_kernel<T><<<nblk, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_coarsen(const Geom& g, const float2* U, const float2* C, const float2* P,
                            float2* X, float2* Y, cudaStream_t s) {
   CoarsenArgs a;
@@ -319,16 +338,12 @@ cudaError_t launch_coarsen(const Geom& g, const float2* U, const float2* C, cons
   a.nb = g.nb;
   a.k = g.k;
   a.diag = g.diag;
-  const int NP = (2 * g.k + 3) & ~3;
-  const size_t smem = sizeof(float2) * (size_t)(2 * kSitesPerStage * 12 * NP + NP * NP);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(coarsen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100000);
-    attr_done = true;
-  }
-  TimedScope ts("coarsen", s);
-  coarsen_kernel<<<(int)g.nblk, kCoarsenThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  const int n2 = 2 * g.k;
+  const int nblk = (int)g.nblk;
+  if (n2 <= 16) return coarsen_t<1>(a, nblk, s);
+  if (n2 <= 32) return coarsen_t<2>(a, nblk, s);
+  if (n2 <= 48) return coarsen_t<3>(a, nblk, s);
+  return coarsen_t<4>(a, nblk, s);
 }
 
 cudaError_t launch_coarse_apply(const Geom& g, const float2* X, const float2* Y,
