@@ -104,6 +104,7 @@ TruncWs trunc_ws_layout(const Geom& g) {
   w.r1 = o; o = align256(o + sizeof(double2) * nbc * mm);
   w.z1 = o; o = align256(o + sizeof(float2) * nbc * mm);
   w.w2 = o; o = align256(o + sizeof(float2) * nbc * g.m * g.k);
+  w.hm = o; o = align256(o + sizeof(double2) * nbc * mm);
   w.flags = o; o = align256(o + sizeof(int32_t) * nbc);
   w.bytes = o;
   return w;

@@ -37,7 +37,7 @@ struct SmoothWs {
   size_t ra, wa, ps, part, alpha, scale, bytes;
 };
 struct TruncWs {
-  size_t gram, r1, z1, w2, flags, bytes;
+  size_t gram, r1, z1, w2, hm, flags, bytes;
 };
 
 SmoothWs smooth_ws_layout(const Geom& g);

@@ -164,97 +164,9 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const float2* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// FP64 dense helpers on shared memory (one CTA, m <= 64)
-// ---------------------------------------------------------------------------
-
-// In-place upper Cholesky G = R^dag R on the upper triangle of Gs (m x m),
-// with `shift` added to the diagonal.  Returns false on a pivot <= tol.
-__device__ bool chol_upper(double2* Gs, int m, double tol, int* s_fail) {
-  if (threadIdx.x == 0) *s_fail = 0;
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = Gs[j * m + j].x;
-      if (!(d > tol)) *s_fail = 1;
-      Gs[j * m + j] = make_double2(d > tol ? sqrt(d) : 1.0, 0.0);
-    }
-    __syncthreads();
-    const double inv = 1.0 / Gs[j * m + j].x;
-    for (int l = j + 1 + threadIdx.x; l < m; l += blockDim.x)
-      Gs[j * m + l] = zscale(Gs[j * m + l], inv);
-    __syncthreads();
-    const int n = m - j - 1;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int a = j + 1 + idx / n, b = j + 1 + idx % n;
-      if (b >= a) Gs[a * m + b] = zsub(Gs[a * m + b], zmulc(Gs[j * m + a], Gs[j * m + b]));
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x)
-    if (idx / m > idx % m) Gs[idx] = make_double2(0.0, 0.0);
-  __syncthreads();
-  return *s_fail == 0;
-}
-
-// Zs = Rs^{-1} for upper-triangular Rs (column c solved by thread c).
-__device__ void tri_inverse_upper(const double2* Rs, double2* Zs, int m) {
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Zs[idx] = make_double2(0.0, 0.0);
-  __syncthreads();
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    for (int i = c; i >= 0; --i) {
-      double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
-      for (int l = i + 1; l <= c; ++l) s = zsub(s, zmul(Rs[i * m + l], Zs[l * m + c]));
-      Zs[i * m + c] = zscale(s, 1.0 / Rs[i * m + i].x);
-    }
-  }
-  __syncthreads();
-}
-
-// Stage 1: R1 = chol(G1) (with a diagonal shift if a pivot fails), store R1
-// (FP64) and Z1 = R1^{-1} (FP32).
-__global__ void __launch_bounds__(kThreads) chol_stage1(const double2* __restrict__ G,
-                                                        double2* __restrict__ R1,
-                                                        float2* __restrict__ Z1,
-                                                        int32_t* __restrict__ flags, int m) {
-  extern __shared__ double2 dsm[];
-  double2* Gs = dsm;
-  double2* Zs = dsm + m * m;
-  __shared__ int s_fail;
-  __shared__ double s_maxd;
-  const int bc = blockIdx.x;
-  const double2* Gb = G + (long)bc * m * m;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) Gs[i] = Gb[i];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double mx = 0;
-    for (int i = 0; i < m; ++i) mx = fmax(mx, Gs[i * m + i].x);
-    s_maxd = mx;
-  }
-  __syncthreads();
-  const double maxd = s_maxd;
-  int32_t flag = 0;
-  if (!chol_upper(Gs, m, 1e-13 * maxd, &s_fail)) {
-    flag |= 1;
-    for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-      Gs[i] = Gb[i];
-      if (i / m == i % m) Gs[i].x += 1e-5 * maxd;
-    }
-    __syncthreads();
-    if (!chol_upper(Gs, m, 1e-13 * maxd, &s_fail)) flag |= 2;
-  }
-  tri_inverse_upper(Gs, Zs, m);
-  double2* Rb = R1 + (long)bc * m * m;
-  float2* Zb = Z1 + (long)bc * m * m;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    Rb[i] = Gs[i];
-    Zb[i] = make_float2((float)Zs[i].x, (float)Zs[i].y);
-  }
-  if (threadIdx.x == 0) flags[bc] = flag;
-}
-
-// ---------------------------------------------------------------------------
-// FP64 top-k eigenpairs of a Hermitian m x m matrix in shared memory:
-// Householder tridiagonalisation, Sturm bisection, inverse iteration.
+// FP64 dense helpers on shared memory (one CTA, m <= 64).  Matrices use the
+// leading dimension ld = m + 1: the padding keeps column accesses free of
+// bank conflicts.
 // ---------------------------------------------------------------------------
 
 __device__ double block_sum(double v, double* red) {
@@ -268,17 +180,122 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-// Hs: Hermitian (full). On exit: d[0..m), e[0..m-1) complex subdiagonal
-// T[j+1][j], reflector j stored in column j of Hs rows j+1.. (u_j), tau[j].
-// H = Q T Q^dag with Q = H_0 H_1 ... H_{m-3}, H_j = I - tau_j u_j u_j^dag.
-__device__ void tridiagonalise(double2* Hs, int m, double* d, double2* e, double* tau,
-                               double2* p, double* red) {
+// In-place upper Cholesky G = R^dag R on the upper triangle of Gs (m x m,
+// leading dimension ld).  Returns false if a pivot is <= tol; the lower
+// triangle is zeroed on exit.
+__device__ bool chol_upper(double2* Gs, int m, int ld, double tol, int* s_fail) {
+  if (threadIdx.x == 0) *s_fail = 0;
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = Gs[j * ld + j].x;
+      if (!(d > tol)) *s_fail = 1;
+      Gs[j * ld + j] = make_double2(d > tol ? sqrt(d) : 1.0, 0.0);
+    }
+    __syncthreads();
+    const double inv = 1.0 / Gs[j * ld + j].x;
+    for (int l = j + 1 + threadIdx.x; l < m; l += blockDim.x)
+      Gs[j * ld + l] = zscale(Gs[j * ld + l], inv);
+    __syncthreads();
+    const int n = m - j - 1;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int r = j + 1 + idx / n, c = j + 1 + idx % n;
+      if (c >= r) Gs[r * ld + c] = zsub(Gs[r * ld + c], zmulc(Gs[j * ld + r], Gs[j * ld + c]));
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x)
+    if (idx / m > idx % m) Gs[(idx / m) * ld + idx % m] = make_double2(0.0, 0.0);
+  __syncthreads();
+  return *s_fail == 0;
+}
+
+// Stage 1: R1 = chol(G1) (with a diagonal shift if a pivot fails), store R1
+// (FP64) and Z1 = R1^{-1} (FP32).  The inverse is formed row by row from the
+// bottom: z_ic = (delta_ic - sum_{i<l<=c} R_il z_lc) / R_ii, four threads per
+// column sharing the sum.
+__global__ void __launch_bounds__(kThreads, 2) chol_stage1(const double2* __restrict__ G,
+                                                           double2* __restrict__ R1,
+                                                           float2* __restrict__ Z1,
+                                                           int32_t* __restrict__ flags, int m) {
+  extern __shared__ double2 dsm[];
+  const int ld = m + 1;
+  double2* Gs = dsm;                                    // [m][ld] FP64
+  float2* Zs = reinterpret_cast<float2*>(Gs + m * ld);  // [m][m] FP32
+  __shared__ int s_fail;
+  __shared__ double red[32];
+  const int bc = blockIdx.x;
+  const double2* Gb = G + (long)bc * m * m;
+  double mx = 0;
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+    const double2 v = Gb[i];
+    Gs[(i / m) * ld + i % m] = v;
+    if (i / m == i % m) mx = fmax(mx, v.x);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  double maxd = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) maxd = fmax(maxd, red[i]);
+  int32_t flag = 0;
+  if (!chol_upper(Gs, m, ld, 1e-13 * maxd, &s_fail)) {
+    flag |= 1;
+    for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+      double2 v = Gb[i];
+      if (i / m == i % m) v.x += 1e-5 * maxd;
+      Gs[(i / m) * ld + i % m] = v;
+    }
+    __syncthreads();
+    if (!chol_upper(Gs, m, ld, 1e-13 * maxd, &s_fail)) flag |= 2;
+  }
+  double2* Rb = R1 + (long)bc * m * m;
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+    Rb[i] = Gs[(i / m) * ld + i % m];
+    Zs[i] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // Z1 is an FP32 output and R1 is well conditioned: the substitution runs in
+  // FP32 arithmetic on the FP64 factor rounded to FP32
+  const int c = threadIdx.x >> 2, part = threadIdx.x & 3;
+  for (int i = m - 1; i >= 0; --i) {
+    float2 acc = make_float2(0.f, 0.f);
+    if (c < m && c >= i)
+      for (int l = i + 1 + part; l <= c; l += 4) {
+        const double2 r = Gs[i * ld + l];
+        cfma(acc, make_float2((float)r.x, (float)r.y), Zs[l * m + c]);
+      }
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+    if (c < m && c >= i && part == 0) {
+      const float inv = (float)(1.0 / Gs[i * ld + i].x);
+      Zs[i * m + c] = make_float2(((i == c ? 1.f : 0.f) - acc.x) * inv, -acc.y * inv);
+    }
+    __syncthreads();
+  }
+  float2* Zb = Z1 + (long)bc * m * m;
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) Zb[i] = Zs[i];
+  if (threadIdx.x == 0) flags[bc] = flag;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 top-k eigenpairs of a Hermitian m x m matrix in shared memory:
+// Householder tridiagonalisation, Sturm multisection, inverse iteration.
+// ---------------------------------------------------------------------------
+
+// Hs: Hermitian (full, leading dimension ld).  On exit: d[0..m), e[0..m-1)
+// complex subdiagonal T[j+1][j], reflector j stored in column j of Hs rows
+// j+1.. (u_j), tau[j].  H = Q T Q^dag with Q = H_0 H_1 ... H_{m-3},
+// H_j = I - tau_j u_j u_j^dag.
+__device__ void tridiagonalise(double2* Hs, int m, int ld, double* d, double2* e, double* tau,
+                               double2* uv, double2* pv, double* red) {
   for (int j = 0; j + 2 < m; ++j) {
     const int n = m - j - 1;  // length of x = H[j+1.., j]
     double tail = 0;
-    for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) tail += zabs2(Hs[i * m + j]);
+    for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) tail += zabs2(Hs[i * ld + j]);
     tail = block_sum(tail, red);
-    const double2 x0 = Hs[(j + 1) * m + j];
+    const double2 x0 = Hs[(j + 1) * ld + j];
     double t = 0.0;
     double2 beta = x0;
     if (tail > 0.0) {
@@ -288,40 +305,37 @@ __device__ void tridiagonalise(double2* Hs, int m, double* d, double2* e, double
       beta = zscale(ph, -nx);
       const double2 u0 = zsub(x0, beta);
       t = 2.0 / (zabs2(u0) + tail);
+      // u (contiguous copy) and its column copy for the back-transform
+      for (int a = threadIdx.x; a < n; a += blockDim.x) uv[a] = a == 0 ? u0 : Hs[(j + 1 + a) * ld + j];
       __syncthreads();
-      if (threadIdx.x == 0) Hs[(j + 1) * m + j] = u0;
-      __syncthreads();
-      // p = t A u over the trailing block A = H[j+1.., j+1..]
+      if (threadIdx.x == 0) Hs[(j + 1) * ld + j] = u0;
+      // p = t A u over the trailing block A = H[j+1.., j+1..], one warp per row
       const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
       for (int a = w; a < n; a += nw) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int b = lane; b < n; b += 32)
-          s = zadd(s, zmul(Hs[(j + 1 + a) * m + j + 1 + b], Hs[(j + 1 + b) * m + j]));
+        double2 sacc = make_double2(0.0, 0.0);
+        const double2* row = Hs + (j + 1 + a) * ld + j + 1;
+        for (int b = lane; b < n; b += 32) sacc = zadd(sacc, zmul(row[b], uv[b]));
         for (int o = 16; o > 0; o >>= 1) {
-          s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-          s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+          sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+          sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
         }
-        if (lane == 0) p[a] = zscale(s, t);
+        if (lane == 0) pv[a] = zscale(sacc, t);
       }
       __syncthreads();
       // K = t/2 u^dag p (real); w = p - K u (stored over p)
       double kr = 0;
-      for (int a = threadIdx.x; a < n; a += blockDim.x) kr += zmulc(Hs[(j + 1 + a) * m + j], p[a]).x;
+      for (int a = threadIdx.x; a < n; a += blockDim.x) kr += zmulc(uv[a], pv[a]).x;
       kr = 0.5 * t * block_sum(kr, red);
-      __syncthreads();
-      for (int a = threadIdx.x; a < n; a += blockDim.x)
-        p[a] = zsub(p[a], zscale(Hs[(j + 1 + a) * m + j], kr));
+      for (int a = threadIdx.x; a < n; a += blockDim.x) pv[a] = zsub(pv[a], zscale(uv[a], kr));
       __syncthreads();
       // A -= u w^dag + w u^dag
       for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int a = idx / n, b = idx % n;
-        const double2 ua = Hs[(j + 1 + a) * m + j], ub = Hs[(j + 1 + b) * m + j];
-        double2 v = Hs[(j + 1 + a) * m + j + 1 + b];
-        v = zsub(v, zmul(ua, zconj(p[b])));
-        v = zsub(v, zmul(p[a], zconj(ub)));
-        Hs[(j + 1 + a) * m + j + 1 + b] = v;
+        const int ra = idx / n, cb = idx % n;
+        double2 v = Hs[(j + 1 + ra) * ld + j + 1 + cb];
+        v = zsub(v, zmul(uv[ra], zconj(pv[cb])));
+        v = zsub(v, zmul(pv[ra], zconj(uv[cb])));
+        Hs[(j + 1 + ra) * ld + j + 1 + cb] = v;
       }
-      __syncthreads();
     }
     if (threadIdx.x == 0) {
       e[j] = beta;
@@ -331,127 +345,226 @@ __device__ void tridiagonalise(double2* Hs, int m, double* d, double2* e, double
   }
   if (threadIdx.x == 0) {
     if (m >= 2) {
-      e[m - 2] = Hs[(m - 1) * m + m - 2];
+      e[m - 2] = Hs[(m - 1) * ld + m - 2];
       tau[m - 2] = 0.0;
     }
-    for (int i = 0; i < m; ++i) d[i] = Hs[i * m + i].x;
   }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = Hs[i * ld + i].x;
   __syncthreads();
 }
 
-// number of eigenvalues of the real symmetric tridiagonal (d, f) below x
-__device__ int sturm_count(const double* d, const double* f2, int n, double x, double tiny) {
-  double q = d[0] - x;
-  int c = q < 0;
+// number of eigenvalues of the real symmetric tridiagonal (d, f) below x, in
+// FP32 (locates eigenvalues to ~1e-7 |T|; they are refined in FP64 later)
+__device__ int sturm_count32(const float* d, const float* f2, int n, float x, float tiny) {
+  float q = d[0] - x;
+  int c = q < 0.f;
   for (int i = 1; i < n; ++i) {
-    if (fabs(q) < tiny) q = q < 0 ? -tiny : tiny;
-    q = d[i] - x - f2[i - 1] / q;
-    c += q < 0;
+    if (fabsf(q) < tiny) q = q < 0.f ? -tiny : tiny;
+    q = d[i] - x - __fdividef(f2[i - 1], q);
+    c += q < 0.f;
   }
   return c;
 }
 
-// one step of inverse iteration: z <- (T - lam)^{-1} z, LU with partial pivoting
-__device__ void tri_solve(const double* d, const double* f, int n, double lam, double tiny,
-                          double* z) {
+// LU factorisation with partial pivoting of the tridiagonal T - lam (diagonal
+// d, off-diagonal f): U has diagonals a, c, c2; L has multipliers l and the
+// row swaps in the bit mask piv
+struct TriLU {
   double a[kMaxM], c[kMaxM], c2[kMaxM], l[kMaxM];
-  bool piv[kMaxM];
+  unsigned long long piv;
+};
+
+__device__ void tri_factor(const double* d, const double* f, int n, double lam, double tiny,
+                           TriLU& F) {
+  F.piv = 0ull;
   for (int i = 0; i < n; ++i) {
-    a[i] = d[i] - lam;
-    c[i] = i + 1 < n ? f[i] : 0.0;
-    c2[i] = 0.0;
+    F.a[i] = d[i] - lam;
+    F.c[i] = i + 1 < n ? f[i] : 0.0;
+    F.c2[i] = 0.0;
   }
   for (int i = 0; i + 1 < n; ++i) {
     const double bsub = f[i];
-    if (fabs(a[i]) >= fabs(bsub)) {
-      piv[i] = false;
-      if (a[i] == 0.0) a[i] = tiny;
-      l[i] = bsub / a[i];
-      a[i + 1] -= l[i] * c[i];
+    if (fabs(F.a[i]) >= fabs(bsub)) {
+      if (F.a[i] == 0.0) F.a[i] = tiny;
+      F.l[i] = bsub / F.a[i];
+      F.a[i + 1] -= F.l[i] * F.c[i];
     } else {
-      piv[i] = true;
-      l[i] = a[i] / bsub;
-      a[i] = bsub;
-      const double tmp = a[i + 1];
-      a[i + 1] = c[i] - l[i] * tmp;
+      F.piv |= 1ull << i;
+      F.l[i] = F.a[i] / bsub;
+      F.a[i] = bsub;
+      const double tmp = F.a[i + 1];
+      F.a[i + 1] = F.c[i] - F.l[i] * tmp;
       if (i + 2 < n) {
-        c2[i] = c[i + 1];
-        c[i + 1] = -l[i] * c2[i];
+        F.c2[i] = F.c[i + 1];
+        F.c[i + 1] = -F.l[i] * F.c2[i];
       }
-      c[i] = tmp;
+      F.c[i] = tmp;
     }
   }
+  for (int i = 0; i < n; ++i)
+    if (fabs(F.a[i]) < tiny) F.a[i] = F.a[i] < 0 ? -tiny : tiny;
+}
+
+// one step of inverse iteration: z <- (T - lam)^{-1} z with the factors F
+__device__ void tri_solve(const TriLU& F, int n, double* z) {
   for (int i = 0; i + 1 < n; ++i) {
-    if (piv[i]) {
+    if ((F.piv >> i) & 1ull) {
       const double t = z[i];
       z[i] = z[i + 1];
-      z[i + 1] = t - l[i] * z[i + 1];
+      z[i + 1] = t - F.l[i] * z[i + 1];
     } else {
-      z[i + 1] -= l[i] * z[i];
+      z[i + 1] -= F.l[i] * z[i];
     }
   }
   for (int i = n - 1; i >= 0; --i) {
-    double s = z[i];
-    if (i + 1 < n) s -= c[i] * z[i + 1];
-    if (i + 2 < n) s -= c2[i] * z[i + 2];
-    const double p = fabs(a[i]) < tiny ? (a[i] < 0 ? -tiny : tiny) : a[i];
-    z[i] = s / p;
+    double sacc = z[i];
+    if (i + 1 < n) sacc -= F.c[i] * z[i + 1];
+    if (i + 2 < n) sacc -= F.c2[i] * z[i + 2];
+    z[i] = sacc / F.a[i];
   }
 }
 
 // Stage 2: R2 = chol(G2), R = R2 R1, H = R R^dag, top-k eigenpairs of H,
 // sigma = sqrt(lambda), W2 = R2^{-1} U~_k (FP32), optional Sigma_k V_k^dag = U~_k^dag R.
-__global__ void __launch_bounds__(kThreads) svd_stage2(
-    const double2* __restrict__ G2, const double2* __restrict__ R1, float2* __restrict__ W2,
-    double* __restrict__ sigma, float2* __restrict__ ctv, int32_t* __restrict__ flags, int m,
-    int k) {
+// Global scratch per block-chirality: G (in: G2, out: R2), R1 (in: R1,
+// out: R), Hg (H).
+constexpr int kBisect = 10;  // points per multisection step
+
+__global__ void __launch_bounds__(kThreads, 2) svd_stage2(
+    double2* __restrict__ G2, double2* __restrict__ R1, double2* __restrict__ Hg,
+    float2* __restrict__ W2, double* __restrict__ sigma, float2* __restrict__ ctv,
+    int32_t* __restrict__ flags, int m, int k) {
   extern __shared__ double2 dsm[];
-  double2* As = dsm;              // R2
-  double2* Bs = As + m * m;       // R, later U~_k (m x k) and tridiagonal eigvecs
-  double2* Hs = Bs + m * m;       // H, then reflectors
-  __shared__ double d[kMaxM], tau[kMaxM], fo[kMaxM], f2[kMaxM], lam[kMaxK];
-  __shared__ double2 e[kMaxM], delta[kMaxM], pv[kMaxM];
+  const int ld = m + 1;
+  double2* M = dsm;            // [m][ld]
+  double2* Uk = M + m * ld;    // [m][k]
+  __shared__ double d[kMaxM], tau[kMaxM], fo[kMaxM];
+  __shared__ float d32[kMaxM], f232[kMaxM];
+  __shared__ double s_dmax;
+  __shared__ double2 e[kMaxM], delta[kMaxM], uv[kMaxM], pv[kMaxM], rowbuf[kMaxM];
   __shared__ double red[32];
+  __shared__ double lo[kMaxK], hi[kMaxK], lam[kMaxK];
+  __shared__ int cnt[kMaxK][kBisect];
   __shared__ int s_fail;
   __shared__ int leader[kMaxK];
   const int bc = blockIdx.x;
-  // R2
-  const double2* Gb = G2 + (long)bc * m * m;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) As[i] = Gb[i];
+  double2* Gb = G2 + (long)bc * m * m;
+  double2* Rg = R1 + (long)bc * m * m;
+  double2* Hb = Hg + (long)bc * m * m;
+  // R2 = chol(G2), kept in global for W2
+  double mx = 0;
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+    const double2 v = Gb[i];
+    M[(i / m) * ld + i % m] = v;
+    if (i / m == i % m) mx = fmax(mx, v.x);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   double maxd = 0;
-  for (int i = 0; i < m; ++i) maxd = fmax(maxd, As[i * m + i].x);
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) maxd = fmax(maxd, red[i]);
   int32_t flag = 0;
-  if (!chol_upper(As, m, 1e-13 * maxd, &s_fail)) flag |= 4;
-  // R = R2 R1 (upper)
-  const double2* R1b = R1 + (long)bc * m * m;
+  if (!chol_upper(M, m, ld, 1e-13 * maxd, &s_fail)) flag |= 4;
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) Gb[i] = M[(i / m) * ld + i % m];
+  __syncthreads();
+  // R = R2 R1 = R1 + (R2 - 1) R1.  After CholeskyQR2's first pass R2 = 1 + D
+  // with D small, so the correction D R1 is formed in FP32 and added to R1 in
+  // FP64: its error u_fp32 |D| |R1| is below the FP32 rounding of the input
+  // vectors by the factor |D| < 1e-3.  A larger D takes the FP64 product.
+  // Column c of R1 is read in chunks of 16 rows; each thread keeps 16 rows of
+  // one column.  R -> Hb.
+  {
+    double dm = 0;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int i = idx / m, c = idx % m;
+      const double2 v = M[i * ld + c];
+      dm = fmax(dm, fabs(v.x - (i == c ? 1.0 : 0.0)) + fabs(v.y));
+    }
+    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmax(t, red[i]);
+      s_dmax = t;
+    }
+    __syncthreads();
+    const bool small = s_dmax < 1e-3;
+    const int c = threadIdx.x % 64, r0 = threadIdx.x / 64;  // rows r0, r0+4, ...
+    if (c < m) {
+      if (small) {
+        float2 acc[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) acc[r] = make_float2(0.f, 0.f);
+        for (int l0 = 0; l0 < m; l0 += 16) {
+          float2 col[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int l = l0 + q;
+            const double2 v = l < m ? Rg[l * m + c] : make_double2(0.0, 0.0);
+            col[q] = make_float2((float)v.x, (float)v.y);
+          }
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            const int i = r0 + 4 * r;
+            if (i >= m) continue;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const int l = l0 + q;
+              if (l < m && l >= i) {
+                const double2 dv = M[i * ld + l];
+                cfma(acc[r], make_float2((float)(dv.x - (l == i ? 1.0 : 0.0)), (float)dv.y), col[q]);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int i = r0 + 4 * r;
+          if (i < m) {
+            const double2 base = c >= i ? Rg[i * m + c] : make_double2(0.0, 0.0);
+            Hb[i * m + c] = c >= i ? make_double2(base.x + acc[r].x, base.y + acc[r].y)
+                                   : make_double2(0.0, 0.0);
+          }
+        }
+      } else {
+        for (int i = r0; i < m; i += 4) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int l = i; l <= c; ++l) acc = zadd(acc, zmul(M[i * ld + l], Rg[l * m + c]));
+          Hb[i * m + c] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+      const double2 v = Hb[i];
+      M[(i / m) * ld + i % m] = v;
+      Rg[i] = v;
+    }
+    __syncthreads();
+  }
+  // H = R R^dag (upper triangle computed, mirrored) -> global, then back into M
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    const int i = idx / m, c = idx % m;
-    double2 s = make_double2(0.0, 0.0);
-    for (int l = i; l <= c; ++l) s = zadd(s, zmul(As[i * m + l], R1b[l * m + c]));
-    Bs[idx] = s;
+    const int i = idx / m, jj = idx % m;
+    if (jj < i) continue;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = jj; l < m; ++l) acc = zadd(acc, zmul(M[i * ld + l], zconj(M[jj * ld + l])));
+    Hb[i * m + jj] = acc;
+    Hb[jj * m + i] = zconj(acc);
   }
   __syncthreads();
-  // H = R R^dag
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    const int i = idx / m, c = idx % m;
-    const int l0 = i > c ? i : c;
-    double2 s = make_double2(0.0, 0.0);
-    for (int l = l0; l < m; ++l) s = zadd(s, zmul(Bs[i * m + l], zconj(Bs[c * m + l])));
-    Hs[idx] = s;
-  }
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) M[(i / m) * ld + i % m] = Hb[i];
   __syncthreads();
-  // coarse test vectors need R; they are formed after U~_k, so keep R in
-  // global scratch only when requested: recompute from As and R1 below.
-  tridiagonalise(Hs, m, d, e, tau, pv, red);
+  tridiagonalise(M, m, ld, d, e, tau, uv, pv, red);
   if (threadIdx.x == 0) {
     delta[0] = make_double2(1.0, 0.0);
     for (int j = 0; j + 1 < m; ++j) {
       const double ae = sqrt(zabs2(e[j]));
       fo[j] = ae;
-      f2[j] = ae * ae;
+      f232[j] = (float)(ae * ae);
       delta[j + 1] = ae > 0 ? zmul(delta[j], zscale(e[j], 1.0 / ae)) : delta[j];
     }
+    for (int j = 0; j < m; ++j) d32[j] = (float)d[j];
   }
   __syncthreads();
   double tnorm = 0;
@@ -460,34 +573,59 @@ __global__ void __launch_bounds__(kThreads) svd_stage2(
     tnorm = fmax(tnorm, r);
   }
   const double tiny = 1e-300 + 1e-15 * tnorm;
-  // eigenvalue i (i-th largest) by bisection, one thread each
+  // multisection: kBisect threads per eigenvalue (the i-th largest)
   if (threadIdx.x < k) {
-    const int target = m - 1 - threadIdx.x;  // index among ascending eigenvalues
-    double lo = -tnorm, hi = tnorm;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if (sturm_count(d, f2, m, mid, 1e-300) > target) hi = mid;
-      else lo = mid;
-    }
-    lam[threadIdx.x] = 0.5 * (lo + hi);
+    lo[threadIdx.x] = -tnorm;
+    hi[threadIdx.x] = tnorm;
   }
   __syncthreads();
-  // clusters (eigenvalues closer than 1e-10 |T|) are handled by their first member
+  {
+    const int ei = threadIdx.x / kBisect, sp = threadIdx.x % kBisect;
+    const float tiny32 = 1e-30f + 1e-20f * (float)tnorm;
+    for (int it = 0; it < 9; ++it) {
+      if (ei < k) {
+        const double l0 = lo[ei], h0 = hi[ei];
+        const double x = l0 + (h0 - l0) * (double)(sp + 1) / (double)(kBisect + 1);
+        cnt[ei][sp] = sturm_count32(d32, f232, m, (float)x, tiny32);
+      }
+      __syncthreads();
+      if (ei < k && sp == 0) {
+        const int target = m - 1 - ei;  // index among ascending eigenvalues
+        const double l0 = lo[ei], h0 = hi[ei];
+        double nl = l0, nh = h0;
+        for (int q = 0; q < kBisect; ++q) {
+          const double x = l0 + (h0 - l0) * (double)(q + 1) / (double)(kBisect + 1);
+          if (cnt[ei][q] > target) {
+            nh = x;
+            break;
+          }
+          nl = x;
+        }
+        lo[ei] = nl;
+        hi[ei] = nh;
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x < k) lam[threadIdx.x] = 0.5 * (lo[threadIdx.x] + hi[threadIdx.x]);
+  __syncthreads();
+  // clusters (eigenvalues closer than 1e-6 |T|, above the FP32 resolution of
+  // the multisection) are handled by their first member
   if (threadIdx.x < k) {
     const int i = threadIdx.x;
-    leader[i] = (i == 0 || fabs(lam[i - 1] - lam[i]) > 1e-10 * tnorm) ? 1 : 0;
+    leader[i] = (i == 0 || fabs(lam[i - 1] - lam[i]) > 1e-6 * tnorm) ? 1 : 0;
   }
   __syncthreads();
-  // inverse iteration; the real eigenvector z_i of T' goes to Bs column i (.x)
-  double2* Uk = Bs;  // m x k, row-major
+  // inverse iteration; the real eigenvector z_i of T' goes to Uk column i (.x)
   if (threadIdx.x < k && leader[threadIdx.x]) {
     int i = threadIdx.x;
     do {
       double z[kMaxM];
+      TriLU F;
+      tri_factor(d, fo, m, lam[i], tiny, F);
       for (int r = 0; r < m; ++r) z[r] = 1.0 + 0.01 * r + 0.001 * i;
-      for (int it = 0; it < 4; ++it) {
-        tri_solve(d, fo, m, lam[i], tiny, z);
+      for (int it = 0; it < 3; ++it) {
+        tri_solve(F, m, z);
         for (int pj = threadIdx.x; pj < i; ++pj) {  // previous members of this cluster
           double dot = 0;
           for (int r = 0; r < m; ++r) dot += Uk[r * k + pj].x * z[r];
@@ -498,60 +636,82 @@ __global__ void __launch_bounds__(kThreads) svd_stage2(
         nrm = 1.0 / sqrt(nrm);
         for (int r = 0; r < m; ++r) z[r] *= nrm;
       }
+      // FP64 Rayleigh quotient z^T T z refines the FP32 multisection value
+      double rq = 0;
+      for (int r = 0; r < m; ++r) rq += d[r] * z[r] * z[r];
+      for (int r = 0; r + 1 < m; ++r) rq += 2.0 * fo[r] * z[r] * z[r + 1];
+      lam[i] = rq;
       for (int r = 0; r < m; ++r) Uk[r * k + i] = make_double2(z[r], 0.0);
       ++i;
     } while (i < k && !leader[i]);
   }
   __syncthreads();
-  // back-transform: y = Q (delta .* z), one warp per vector
+  // back-transform: y = Q (delta .* z); reflector j copied to uv first
+  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x)
+    Uk[idx] = zscale(delta[idx / k], Uk[idx].x);
+  __syncthreads();
   {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = w; i < k; i += nw) {
-      for (int r = lane; r < m; r += 32) Uk[r * k + i] = zscale(delta[r], Uk[r * k + i].x);
-      __syncwarp();
-      for (int j = m - 3; j >= 0; --j) {
-        if (tau[j] == 0.0) continue;
-        double2 s = make_double2(0.0, 0.0);
-        for (int r = j + 1 + lane; r < m; r += 32) s = zadd(s, zmulc(Hs[r * m + j], Uk[r * k + i]));
+    for (int j = m - 3; j >= 0; --j) {
+      if (tau[j] == 0.0) continue;
+      const int n = m - j - 1;
+      for (int a = threadIdx.x; a < n; a += blockDim.x) uv[a] = M[(j + 1 + a) * ld + j];
+      __syncthreads();
+      for (int i = w; i < k; i += nw) {
+        double2 sacc = make_double2(0.0, 0.0);
+        for (int a = lane; a < n; a += 32) sacc = zadd(sacc, zmulc(uv[a], Uk[(j + 1 + a) * k + i]));
         for (int o = 16; o > 0; o >>= 1) {
-          s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-          s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+          sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+          sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
         }
-        s = zscale(s, tau[j]);
-        for (int r = j + 1 + lane; r < m; r += 32)
-          Uk[r * k + i] = zsub(Uk[r * k + i], zmul(s, Hs[r * m + j]));
-        __syncwarp();
+        sacc = zscale(sacc, tau[j]);
+        for (int a = lane; a < n; a += 32)
+          Uk[(j + 1 + a) * k + i] = zsub(Uk[(j + 1 + a) * k + i], zmul(sacc, uv[a]));
       }
+      __syncthreads();
     }
   }
-  __syncthreads();
   if (threadIdx.x < k) sigma[(long)bc * k + threadIdx.x] = sqrt(fmax(lam[threadIdx.x], 0.0));
-  // W2 = R2^{-1} U~_k, column i by thread i (back substitution, R2 upper)
-  float2* Wb = W2 + (long)bc * m * k;
-  if (threadIdx.x < k) {
-    const int i = threadIdx.x;
-    double2 y[kMaxM];
-    for (int r = m - 1; r >= 0; --r) {
-      double2 s = Uk[r * k + i];
-      for (int l = r + 1; l < m; ++l) s = zsub(s, zmul(As[r * m + l], y[l]));
-      y[r] = zscale(s, 1.0 / As[r * m + r].x);
-    }
-    for (int r = 0; r < m; ++r) Wb[r * k + i] = make_float2((float)y[r].x, (float)y[r].y);
-  }
   if (ctv) {
-    // Sigma_k V_k^dag = U~_k^dag R,  R = R2 R1 recomputed entry by entry
+    // Sigma_k V_k^dag = U~_k^dag R  (R from global)
     float2* cb = ctv + (long)bc * k * m;
     for (int idx = threadIdx.x; idx < k * m; idx += blockDim.x) {
       const int i = idx / m, c = idx % m;
-      double2 s = make_double2(0.0, 0.0);
-      for (int l = 0; l <= c; ++l) {
-        double2 rl = make_double2(0.0, 0.0);
-        for (int q = l; q <= c; ++q) rl = zadd(rl, zmul(As[l * m + q], R1b[q * m + c]));
-        s = zadd(s, zmulc(Uk[l * k + i], rl));
+      double2 acc = make_double2(0.0, 0.0);
+      for (int l = 0; l <= c; ++l) acc = zadd(acc, zmulc(Uk[l * k + i], Rg[l * m + c]));
+      cb[idx] = make_float2((float)acc.x, (float)acc.y);
+    }
+    __syncthreads();
+  }
+  // W2 = R2^{-1} U~_k (an FP32 output; R2 is close to 1): FP32 substitution
+  // from the bottom, eight threads per column, R2 staged into M
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) M[(i / m) * ld + i % m] = Gb[i];
+  __syncthreads();
+  {
+    const int c = threadIdx.x >> 3, part = threadIdx.x & 7;
+    for (int i = m - 1; i >= 0; --i) {
+      float2 acc = make_float2(0.f, 0.f);
+      if (c < k)
+        for (int l = i + 1 + part; l < m; l += 8) {
+          const double2 r = M[i * ld + l], u = Uk[l * k + c];
+          cfma(acc, make_float2((float)r.x, (float)r.y), make_float2((float)u.x, (float)u.y));
+        }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
       }
-      cb[idx] = make_float2((float)s.x, (float)s.y);
+      if (c < k && part == 0) {
+        const float inv = (float)(1.0 / M[i * ld + i].x);
+        const double2 u = Uk[i * k + c];
+        Uk[i * k + c] = make_double2(((float)u.x - acc.x) * inv, ((float)u.y - acc.y) * inv);
+      }
+      __syncthreads();
     }
   }
+  float2* Wb = W2 + (long)bc * m * k;
+  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x)
+    Wb[idx] = make_float2((float)Uk[idx].x, (float)Uk[idx].y);
   if (threadIdx.x == 0) flags[bc] |= flag;
 }
 
@@ -597,6 +757,7 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
   double2* R1 = reinterpret_cast<double2*>(ws + lay.r1);
   float2* Z1 = reinterpret_cast<float2*>(ws + lay.z1);
   float2* W2 = reinterpret_cast<float2*>(ws + lay.w2);
+  double2* Hm = reinterpret_cast<double2*>(ws + lay.hm);
   BlockGeom bg;
   for (int i = 0; i < 4; ++i) {
     bg.L[i] = g.L[i];
@@ -610,8 +771,8 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
   const int m = g.m, k = g.k;
   const size_t sm_gram0 = sizeof(float2) * (size_t)(2 * kChunkRows * m);
   const size_t sm_gram1 = sm_gram0 + sizeof(float2) * (size_t)m * m;
-  const size_t sm_chol = sizeof(double2) * (size_t)2 * m * m;
-  const size_t sm_svd = sizeof(double2) * (size_t)3 * m * m;
+  const size_t sm_chol = sizeof(double2) * (size_t)m * (m + 1) + sizeof(float2) * (size_t)m * m;
+  const size_t sm_svd = sizeof(double2) * ((size_t)m * (m + 1) + (size_t)m * k);
   const size_t sm_uk = sm_gram1 + sizeof(float2) * (size_t)m * k;
   static bool attr_done = false;
   if (!attr_done) {
@@ -636,7 +797,7 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
   }
   {
     TimedScope ts("trunc_chol_eig64", s);
-    svd_stage2<<<nbc, kThreads, sm_svd, s>>>(G, R1, W2, sigma, coarse_tv, flags, m, k);
+    svd_stage2<<<nbc, kThreads, sm_svd, s>>>(G, R1, Hm, W2, sigma, coarse_tv, flags, m, k);
   }
   {
     TimedScope ts("trunc_form_uk", s);
