@@ -208,6 +208,16 @@ typedef struct {
 mg_status mg_timing_enable(int on);
 int mg_timing_read(mg_timing_entry* out, int max);
 
+/* Device status of the work enqueued so far on `stream` (not in the paper;
+ * the failure-detection side of the library).  Waits for the stream, then
+ * reads and clears the library's device status word.  Returns MG_OK, or
+ * MG_ERR_TIMEOUT if a smoother or operator pass since the previous call gave
+ * up waiting (after a bounded number of polls, about a second) for input it
+ * had staged into shared memory: that pass stopped early and its outputs are
+ * not valid.  MG_ERR_CUDA if the stream reports a CUDA error.  The status
+ * word is shared by every stream of the process on the current device. */
+mg_status mg_sync_status(void* stream);
+
 /* Message describing the calling thread's most recent failure ("" if none). */
 const char* mg_last_error(void);
 

@@ -215,6 +215,17 @@ int mg_timing_read(mg_timing_entry* out, int max) {
   return n;
 }
 
+mg_status mg_sync_status(void* stream) {
+  int st = 0;
+  const cudaError_t e = read_device_status(&st, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(MG_ERR_CUDA, "mg_sync_status: %s", cudaGetErrorString(e));
+  if (st & 1)
+    return fail(MG_ERR_TIMEOUT,
+                "a smoother or operator pass gave up waiting for its staged input; its "
+                "outputs are not valid");
+  return MG_OK;
+}
+
 const char* mg_last_error(void) { return g_err; }
 
 const char* mg_version(void) { return "chiral-mg-gb300 0.1 (sm_103a)"; }

@@ -73,6 +73,10 @@ cudaError_t launch_dirac(const Geom& g, const float2* U, const float2* C, const 
 cudaError_t launch_smoother(const Geom& g, const float2* U, const float2* C,
                             const float2* psi0, float2* psi, char* ws, cudaStream_t s);
 
+// Synchronises s, then reads and clears the device status word (bit 0: a
+// smoother pass gave up waiting for its staged input).
+cudaError_t read_device_status(int* out, cudaStream_t s);
+
 cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double* sigma,
                             float2* coarse_tv, int32_t* flags, char* ws, cudaStream_t s);
 

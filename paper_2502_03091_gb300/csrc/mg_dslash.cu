@@ -2,228 +2,292 @@
 // minimal-residual smoother of the setup (paper Sec. 2, Eq. 1: m' random
 // starts relaxed on D psi = 0), plus the clover-field preparation.
 //
-// Layout of every spinor field: float4 f[(site*12 + spin*3 + colour)*(m'/2) + pair],
-// i.e. complex64 [V][4][3][m'] read two right-hand sides at a time.
-//
 // Smoother (per right-hand side, a = step length), the textbook MR order:
 //   r_0 = -D psi_0,  w_0 = D r_0,  a_t = <w_t, r_t> / <w_t, w_t>
-//   psi_{t+1} = psi_t + a_t r_t,  r_{t+1} = r_t - a_t w_t,  w_{t+1} = D r_{t+1}.
-// Each iteration is ONE pass: the pass for t+1 reads r_t and w_t at the site
-// and its 8 neighbours, forms r_{t+1} = r_t - a_t w_t on the fly wherever it
-// is needed (bitwise the same value at every use), applies D to it, and
-// writes r_{t+1}, w_{t+1} and psi_{t+1} together with the partial inner
-// products of a_{t+1}.  The last iteration only updates psi; a final pass
-// scales each vector to unit norm.
+//   psi_{t+1} = psi_t + a_t r_t,  r_{t+1} = r_t - a_t w_t,  w_{t+1} = D r_{t+1},
+// and finally psi_i / |psi_i|.  Each iteration is two passes: a streaming
+// update of r and psi, then the dslash w = D r with the partial inner
+// products of a_{t+1}.
+//
+// Internal "slab" layout of r, w and psi: the right-hand sides are cut into
+// slabs of 2P (P pairs); float4 f[((q*V + x)*12 + e)*P + p] holds component
+// e = spin*3 + colour of site x for the pair (2(qP+p), 2(qP+p)+1) as
+// (re_0, re_1, im_0, im_1).  The real parts and the imaginary parts of a
+// pair are packed FP32 pairs, the operands of the f32x2 instructions, and the
+// 12 x 2P numbers of one site and slab are contiguous (768 bytes for P = 4).
+#include <cstdint>
+
 #include "mg_common.cuh"
 
 namespace mg {
 namespace {
 
+// device status word: bit 0 = a pass gave up waiting for its staged input
+__device__ int g_status;
+
 // ---------------------------------------------------------------------------
-// two-right-hand-side complex arithmetic on float4 = (re0, im0, re1, im1)
+// packed FP32 pairs: component .x belongs to the first right-hand side of a
+// pair, .y to the second
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
-  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+__device__ __forceinline__ unsigned long long pk(float2 a) {
+  unsigned long long u;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(a.x), "f"(a.y));
+  return u;
 }
-__device__ __forceinline__ float4 f4sub(float4 a, float4 b) {
-  return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+__device__ __forceinline__ float2 upk(unsigned long long u) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(u));
+  return a;
 }
-__device__ __forceinline__ float4 f4neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
-__device__ __forceinline__ float4 f4i(float4 a) { return make_float4(-a.y, a.x, -a.w, a.z); }
-__device__ __forceinline__ float4 f4mi(float4 a) { return make_float4(a.y, -a.x, a.w, -a.z); }
-// acc += s * a (real s)
-__device__ __forceinline__ void f4axpy(float4& acc, float s, float4 a) {
-  acc.x = fmaf(s, a.x, acc.x);
-  acc.y = fmaf(s, a.y, acc.y);
-  acc.z = fmaf(s, a.z, acc.z);
-  acc.w = fmaf(s, a.w, acc.w);
+// a * b + c, lane-wise
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+  return upk(d);
 }
-// acc += u * a (complex u, same for both right-hand sides)
-__device__ __forceinline__ void f4cfma(float4& acc, float2 u, float4 a) {
-  acc.x = fmaf(u.x, a.x, fmaf(-u.y, a.y, acc.x));
-  acc.y = fmaf(u.x, a.y, fmaf(u.y, a.x, acc.y));
-  acc.z = fmaf(u.x, a.z, fmaf(-u.y, a.w, acc.z));
-  acc.w = fmaf(u.x, a.w, fmaf(u.y, a.z, acc.w));
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+  return upk(d);
 }
-// acc += conj(u) * a
-__device__ __forceinline__ void f4cfmac(float4& acc, float2 u, float4 a) {
-  acc.x = fmaf(u.x, a.x, fmaf(u.y, a.y, acc.x));
-  acc.y = fmaf(u.x, a.y, fmaf(-u.y, a.x, acc.y));
-  acc.z = fmaf(u.x, a.z, fmaf(u.y, a.w, acc.z));
-  acc.w = fmaf(u.x, a.w, fmaf(-u.y, a.z, acc.w));
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+
+// one complex component of two right-hand sides
+struct CP {
+  float2 re, im;
+};
+__device__ __forceinline__ CP cp_ld(const float4* p) {
+  const float4 v = *p;
+  return CP{make_float2(v.x, v.y), make_float2(v.z, v.w)};
 }
-// per-right-hand-side complex scale: (a0 * v.xy, a1 * v.zw)
-__device__ __forceinline__ float4 f4mul2(float2 a0, float2 a1, float4 v) {
-  return make_float4(a0.x * v.x - a0.y * v.y, a0.x * v.y + a0.y * v.x,
-                     a1.x * v.z - a1.y * v.w, a1.x * v.w + a1.y * v.z);
+__device__ __forceinline__ float4 cp_f4(CP a) { return make_float4(a.re.x, a.re.y, a.im.x, a.im.y); }
+
+// acc += u h for a link entry u shared by both right-hand sides; nim = -Im h
+__device__ __forceinline__ void lmul(CP& acc, float2 u, const CP& h, float2 nim) {
+  const float2 ur = dup(u.x), ui = dup(u.y);
+  acc.re = pfma(ur, h.re, acc.re);
+  acc.re = pfma(ui, nim, acc.re);
+  acc.im = pfma(ur, h.im, acc.im);
+  acc.im = pfma(ui, h.re, acc.im);
+}
+// acc += conj(u) h; nre = -Re h
+__device__ __forceinline__ void lmulc(CP& acc, float2 u, const CP& h, float2 nre) {
+  const float2 ur = dup(u.x), ui = dup(u.y);
+  acc.re = pfma(ur, h.re, acc.re);
+  acc.re = pfma(ui, h.im, acc.re);
+  acc.im = pfma(ur, h.im, acc.im);
+  acc.im = pfma(ui, nre, acc.im);
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier and bulk-copy (TMA engine) primitives
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// waits for the phase with the given parity; gives up after a bounded number
+// of polls (each poll suspends the thread for a hardware-defined time)
+constexpr int kMaxPolls = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+  for (int i = 0; i < kMaxPolls; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// global -> shared bulk copy completing on bar (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ long slab_index(int q, int V, int x, int e, int PAIRS, int p) {
+  return (((long)q * V + x) * 12 + e) * PAIRS + p;
 }
 
 // ---------------------------------------------------------------------------
 // one hop of the Wilson operator, spin-projected:
-//   S = +1: acc += hw (1 - gamma_mu) U_mu(x) psi(x + mu)
-//   S = -1: acc += hw (1 + gamma_mu) U_mu(x - mu)^dag psi(x - mu)
-// With psi = (psi_u, psi_l) in the chiral basis, (1 - S gamma) chi =
-// (h, -S B^dag h) with h = chi_u - S B chi_l, so only the half spinor h
+//   S = +1: acc += hw (1 - gamma_mu) U_mu(x) chi(x + mu)
+//   S = -1: acc += hw (1 + gamma_mu) U_mu(x - mu)^dag chi(x - mu)
+// With chi = (chi_u, chi_l) in the chiral basis, (1 - S gamma_mu) chi =
+// (h, -S B_mu^dag h) with h = chi_u - S B_mu chi_l, so only the half spinor h
 // (2 spins x 3 colours) is multiplied by the link.
 // B_x = -i sigma_1, B_y = -i sigma_2, B_z = -i sigma_3, B_t = 1.
+//
+// The hop is split between two partner lanes (hf = 0, 1): lane hf forms row
+// hf of h, multiplies it by the link and accumulates the output spins hf
+// (upper: + hw g) and 2 + hf (lower: -S hw (B^dag g)_hf); for mu = x, y the
+// lower part needs the partner's g (one shuffle).  src points at component 0
+// of the neighbour's pair (component e at src[e * PAIRS], shared ring or
+// global slab); u at the 9 entries of the link.
 // ---------------------------------------------------------------------------
-// (B_mu chi_l)_sp given the one lower spin component it depends on
-template <int MU>
-__device__ __forceinline__ float4 b_row(int sp, float4 v) {
-  if (MU == 0) return f4mi(v);                     // -i chi_{3-sp}
-  if (MU == 1) return sp == 0 ? f4neg(v) : v;      // -chi_3, +chi_2
-  if (MU == 2) return sp == 0 ? f4mi(v) : f4i(v);  // -i chi_2, +i chi_3
-  return v;                                        // chi_{2+sp}
+template <int MU, int S, int PAIRS>
+__device__ __forceinline__ void hop(CP zu[3], CP zl[3], int hf, const float4* src,
+                                    const float2* __restrict__ u, float hw) {
+  // (B chi_l)_hf uses lower spin 2 + lo
+  const int lo = (MU == 0 || MU == 1) ? 1 - hf : hf;
+  CP h[3];
+  float2 nh[3];
+  {
+    // h.re = up.re + cr A, h.im = up.im + ci B with (A, B) = (dn.im, dn.re) for
+    // x, z and (dn.re, dn.im) for y, t:
+    //   x: B chi_l = -i chi_{3-hf};  y: -chi_3 / +chi_2;  z: -i chi_2 / +i chi_3;  t: chi_{2+hf}
+    float cr, ci;
+    if (MU == 0) {
+      cr = -S;
+      ci = S;
+    } else if (MU == 1) {
+      const float s1 = hf ? 1.f : -1.f;
+      cr = ci = -S * s1;
+    } else if (MU == 2) {
+      const float s2 = hf ? -1.f : 1.f;
+      cr = -S * s2;
+      ci = S * s2;
+    } else {
+      cr = ci = -S;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const CP up = cp_ld(src + (hf * 3 + c) * PAIRS);
+      const CP dn = cp_ld(src + ((2 + lo) * 3 + c) * PAIRS);
+      const float2 A = (MU == 0 || MU == 2) ? dn.im : dn.re;
+      const float2 B = (MU == 0 || MU == 2) ? dn.re : dn.im;
+      h[c].re = pfma(dup(cr), A, up.re);
+      h[c].im = pfma(dup(ci), B, up.im);
+      nh[c] = pmul(dup(-1.f), S > 0 ? h[c].im : h[c].re);
+    }
+  }
+  // lower-spin coefficients: acc_l.re += kr X, acc_l.im += ki Y
+  //   x: i g_{1-hf};  y: g_1 / -g_0;  z: i g_0 / -i g_1;  t: g_hf
+  float kr, ki;
+  if (MU == 0) {
+    kr = S * hw;
+    ki = -S * hw;
+  } else if (MU == 1) {
+    const float t1 = hf ? -1.f : 1.f;
+    kr = ki = -S * hw * t1;
+  } else if (MU == 2) {
+    const float t2 = hf ? -1.f : 1.f;
+    kr = S * hw * t2;
+    ki = -S * hw * t2;
+  } else {
+    kr = ki = -S * hw;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    CP g{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (S > 0) lmul(g, __ldg(u + c * 3 + d), h[d], nh[d]);
+      else lmulc(g, __ldg(u + d * 3 + c), h[d], nh[d]);
+    }
+    zu[c].re = pfma(dup(hw), g.re, zu[c].re);
+    zu[c].im = pfma(dup(hw), g.im, zu[c].im);
+    if (MU == 0 || MU == 1) {
+      g.re.x = __shfl_xor_sync(0xffffffffu, g.re.x, 1);
+      g.re.y = __shfl_xor_sync(0xffffffffu, g.re.y, 1);
+      g.im.x = __shfl_xor_sync(0xffffffffu, g.im.x, 1);
+      g.im.y = __shfl_xor_sync(0xffffffffu, g.im.y, 1);
+    }
+    const float2 X = (MU == 0 || MU == 2) ? g.im : g.re;
+    const float2 Y = (MU == 0 || MU == 2) ? g.re : g.im;
+    zl[c].re = pfma(dup(kr), X, zl[c].re);
+    zl[c].im = pfma(dup(ki), Y, zl[c].im);
+  }
 }
-template <int MU>
-__device__ __forceinline__ void bdag_apply(float4 g0, float4 g1, float4& o0, float4& o1) {
-  // (o0, o1) = B_mu^dag (g0, g1)
-  if (MU == 0) { o0 = f4i(g1); o1 = f4i(g0); }
-  if (MU == 1) { o0 = g1; o1 = f4neg(g0); }
-  if (MU == 2) { o0 = f4i(g0); o1 = f4mi(g1); }
-  if (MU == 3) { o0 = g0; o1 = g1; }
+
+// acc += c v for a complex number c shared by both right-hand sides
+__device__ __forceinline__ void cmul_acc(CP& acc, float2 c, const CP& v) {
+  acc.re = pfma(dup(c.x), v.re, acc.re);
+  acc.re = pfma(dup(-c.y), v.im, acc.re);
+  acc.im = pfma(dup(c.x), v.im, acc.im);
+  acc.im = pfma(dup(c.y), v.re, acc.im);
 }
 
 // ---------------------------------------------------------------------------
-// t-marching smoother pass.
-//
-// Internal ("slab") layout of r, w and psi: for right-hand-side slice q of
-// 2*PAIRS vectors, float4 f[((q*V + x)*12 + e)*PAIRS + p] -- every site's
-// 12 x 2*PAIRS complex numbers of one slice are contiguous.
+// t-marching dslash pass.
 //
 // One CTA owns a patch of kSPC consecutive sites of a timeslice (spatial
-// lexicographic index p0 .. p0+kSPC-1) for one slice, and marches t = 0..Lt-1.
-// A ring of kRing rows of the dslash input s (s = r, or s = r - a w formed
-// when the row is staged) lives in shared memory: hops that stay in the patch
-// (x, and y when a patch spans several x-rows) and the two t-hops read the
-// ring; only hops that leave the patch go to global memory (L2).  Producer
-// warps stage row t+2 while consumer warps apply D to row t; one barrier per
-// step.  Ring slot of row r (r = -1 .. Lt+1): (r + 1) & 3.
+// lexicographic index p0 .. p0+kSPC-1) for one slab, and marches t = 0..Lt-1.
+// A ring of kRing rows of the input lives in shared memory: hops that stay in
+// the patch (x, and y when a patch spans several x-rows) and both t-hops read
+// the ring; the other hops read global memory (L2).  A ring row is one bulk
+// copy of the patch's contiguous slab row (24.6 KB for P = 4) that completes
+// on the slot's mbarrier: at step t thread 0 issues row t+2 into the slot of row t-2
+// (free since the previous step's barrier) and every thread waits for row
+// t+1, so each row has a whole step to arrive.  Row r (-1 <= r <= Lt) uses
+// slot (r+1) & 3 for the ((r+1)/4)-th time: phase parity ((r+1)/4) & 1.
+//
+// MODE_NEG_D: out = -D in.  MODE_D_DOT: out = D in, plus per-patch partial
+// sums <out, in> and |out|^2 per right-hand side.
+// Lanes: threadIdx = (site * P + pair) * 2 + hf.
 // ---------------------------------------------------------------------------
 constexpr int kSPC = 32;
 constexpr int kRing = 4;
 
 struct MarchArgs {
-  const float4* in;       // s source r_t (slab) or psi_0 (ABI layout)
-  const float4* win;      // w_t (slab), fused pass
-  const float4* psi_src;  // psi_t, fused pass (ABI layout for psi_0, else slab)
-  float4* out;            // D s (slab)
-  float4* r_out;          // r_{t+1} = s (slab), fused pass
-  float4* psi_out;        // psi_{t+1} (slab), fused pass
-  const float2* U;
-  const float2* C;        // clover or nullptr
-  const float2* alpha;    // [m'] step lengths
-  double* part;           // [m'][npatch][4]
+  const float4* in;   // input s (slab)
+  float4* out;        // D s or -D s (slab)
+  const float2* U;    // links [V][4][3][3]
+  const float2* C;    // clover [V][2][6][6] or nullptr
+  double* part;       // [m'][npatch][4]
+  int* status;        // device status word
   int L[4];
   int Vs, V, np, npatch;
-  int in_abi, psi_abi;    // layouts of `in` and `psi_src`
   float hw[4];
   float diag;
 };
 
 enum { MODE_NEG_D = 0, MODE_D_DOT = 1 };
 
-__device__ __forceinline__ long slab_index(int q, int V, int x, int e, int PAIRS, int p) {
-  return (((long)q * V + x) * 12 + e) * PAIRS + p;
-}
-
-// One hop, split between two partner lanes (hf = 0, 1): lane hf forms the
-// half-spinor row h_hf = chi_hf - S (B chi_l)_hf (colour vector), multiplies
-// it by U (or U^dag) and accumulates into the two output spins it owns,
-// hf (upper) and 2 + hf (lower):
-//   upper: acc_u += hw g_hf,   lower: acc_l += -S hw (B^dag g)_hf,
-// where (B^dag g)_hf needs the partner's g for mu = x, y (one shuffle).
-//
-// load_half fetches the lane's inputs (chi_hf and the lower spin entering
-// (B chi_l)_hf) from a neighbour whose component e is at src[e * es]; src is
-// a generic pointer (shared-memory ring or global memory).
-template <int MU>
-__device__ __forceinline__ void load_half(const float4* src, int es, int hf, float4 up[3],
-                                          float4 dn[3]) {
-  const int lo = (MU == 0 || MU == 1) ? 1 - hf : hf;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    up[c] = src[(hf * 3 + c) * es];
-    dn[c] = src[((2 + lo) * 3 + c) * es];
-  }
-}
-
-template <int MU, int S>
-__device__ __forceinline__ void apply_half(float4 acc_u[3], float4 acc_l[3], int hf,
-                                           const float4 up[3], const float4 dn[3],
-                                           const float2* __restrict__ u, float hw) {
-  float2 U[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) U[i] = __ldg(u + i);
-  float4 h[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    // (B chi_l)_hf: mu=x: -i chi_{3-hf}; mu=y: -chi_3 / +chi_2; mu=z: -i chi_2 / +i chi_3; t: chi_{2+hf}
-    float4 bl;
-    if (MU == 0) bl = f4mi(dn[c]);
-    else if (MU == 1) bl = hf == 0 ? f4neg(dn[c]) : dn[c];
-    else if (MU == 2) bl = hf == 0 ? f4mi(dn[c]) : f4i(dn[c]);
-    else bl = dn[c];
-    h[c] = S > 0 ? f4sub(up[c], bl) : f4add(up[c], bl);
-  }
-  float4 g[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    g[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (S > 0) f4cfma(g[c], U[c * 3 + d], h[d]);
-      else f4cfmac(g[c], U[d * 3 + c], h[d]);
-    }
-    f4axpy(acc_u[c], hw, g[c]);
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    float4 v = g[c];
-    if (MU == 0 || MU == 1) {
-      v.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
-      v.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
-      v.z = __shfl_xor_sync(0xffffffffu, v.z, 1);
-      v.w = __shfl_xor_sync(0xffffffffu, v.w, 1);
-    }
-    // (B^dag g)_hf: x: i g_{1-hf}; y: g_1 / -g_0; z: i g_0 / -i g_1; t: g_hf
-    float4 b;
-    if (MU == 0) b = f4i(v);
-    else if (MU == 1) b = hf == 0 ? v : f4neg(v);
-    else if (MU == 2) b = hf == 0 ? f4i(v) : f4mi(v);
-    else b = v;
-    f4axpy(acc_l[c], -S * hw, b);
-  }
-}
-
 template <int PAIRS>
 constexpr int march_threads() {
   return 2 * kSPC * PAIRS;
 }
 
-// Dslash pass.  MODE_NEG_D: out = -D in (in = psi_0, ABI layout);
-// MODE_D_DOT: out = D in (in = r, slab) with partials <out, in>, |out|^2.
-// Each lane (site, pair, spin half hf) also stages its own 6 components of
-// ring row t+2: loads are issued before the compute of row t and stored into
-// the ring after the step's first barrier.
 template <int PAIRS, int MODE>
 __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchArgs a) {
-  constexpr int NC = 2 * kSPC * PAIRS;  // lanes: (site, pair, spin half)
-  constexpr int SS = 12 * PAIRS + 4;    // padded ring site stride (float4)
+  constexpr int NC = 2 * kSPC * PAIRS;
+  constexpr int SS = 12 * PAIRS;  // ring site stride (float4): a row is a copy of the slab row
   constexpr int NW = NC / 32;
-  extern __shared__ float4 ring[];      // [kRing][kSPC][SS]
+  constexpr uint32_t kSiteBytes = 12 * PAIRS * sizeof(float4);
+  extern __shared__ __align__(128) float4 ring[];  // [kRing][kSPC][SS]
+  __shared__ __align__(8) unsigned long long bar[kRing];
   __shared__ double red[NW][PAIRS][6];
+  __shared__ int s_abort;
   const int q = blockIdx.x / a.npatch, patch = blockIdx.x % a.npatch;
   const int p0 = patch * kSPC;
   const int Lt = a.L[3];
+  const int nvalid = min(kSPC, a.Vs - p0);
   const int hf = threadIdx.x & 1;
   const int sp_idx = threadIdx.x >> 1;
   const int s_loc = sp_idx / PAIRS, p = sp_idx % PAIRS;
-  const int gp = q * PAIRS + p;
   const int xyz = p0 + s_loc;
   const bool valid = xyz < a.Vs;
-  const bool abi = MODE == MODE_NEG_D;  // input layout
-  const int ges = abi ? a.np : PAIRS;   // global component stride
   int nf[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
   {
     int c[3];
@@ -237,140 +301,133 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
       nb[mu] = c[mu] > 0 ? xyz - sst[mu] : xyz + (a.L[mu] - 1) * sst[mu];
     }
   }
-  // global address of component 0 of site x for this lane's pair
-  auto gaddr = [&](int x) -> const float4* {
-    return abi ? a.in + (long)x * 12 * a.np + gp : a.in + slab_index(q, a.V, x, 0, PAIRS, p);
-  };
-  // staging of this lane's 6 components of row r (-1 <= r <= Lt)
-  auto stage_load = [&](int r, float4 sv[6]) {
-    if (!valid) return;
-    const float4* src = gaddr(((r + Lt) % Lt) * a.Vs + xyz);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
-      sv[k] = __ldg(src + e * ges);
-    }
-  };
-  auto stage_store = [&](int r, const float4 sv[6]) {
-    if (!valid) return;
-    float4* dst = ring + ((r + 1) & 3) * kSPC * SS + s_loc * SS + p;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
-      dst[e * PAIRS] = sv[k];
-    }
-  };
-
-  double pr[6] = {0, 0, 0, 0, 0, 0};
-  {
-    float4 sv[6];
-    for (int r = -1; r <= 1; ++r) {
-      stage_load(r, sv);
-      stage_store(r, sv);
-    }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kRing; ++i) mbar_init(&bar[i], 1);
+    mbar_fence_init();
+    s_abort = 0;
   }
   __syncthreads();
+  // thread 0: one bulk copy of ring row r (the patch's sites are contiguous in the slab)
+  auto issue = [&](int r) {
+    const int slot = (r + 1) & 3;
+    const uint32_t bytes = (uint32_t)nvalid * kSiteBytes;
+    mbar_expect_tx(&bar[slot], bytes);
+    const int x = ((r + Lt) % Lt) * a.Vs + p0;
+    bulk_g2s(ring + slot * kSPC * SS, a.in + slab_index(q, a.V, x, 0, PAIRS, 0), bytes, &bar[slot]);
+  };
+  auto wait_row = [&](int r) -> bool {
+    return mbar_wait(&bar[(r + 1) & 3], (uint32_t)(((r + 1) >> 2) & 1));
+  };
+  auto give_up = [&]() {
+    s_abort = 1;
+    atomicOr(a.status, 1);
+  };
+  if (threadIdx.x == 0) {
+    issue(-1);
+    issue(0);
+    issue(1);
+  }
+  if (!wait_row(-1) || !wait_row(0)) give_up();
+
+  double pr[6] = {0, 0, 0, 0, 0, 0};
+  int last_issued = 1;
   for (int t = 0; t < Lt; ++t) {
-    float4 sv[6];
-    const bool do_stage = t + 2 <= Lt;
-    if (do_stage) stage_load(t + 2, sv);
+    if (t + 2 <= Lt) {
+      if (threadIdx.x == 0) issue(t + 2);
+      last_issued = t + 2;
+    }
+    if (!wait_row(t + 1)) give_up();
     {
-      // every lane takes part in the shuffles; lanes of an invalid site
-      // compute on site p0 and discard the result
+      // lanes of a site beyond the lattice compute on site p0 and discard it
       const int xyzc = valid ? xyz : p0;
+      const int sl = xyzc - p0;
       const float4* ring_t = ring + ((t + 1) & 3) * kSPC * SS;
       const float4* ring_f = ring + ((t + 2) & 3) * kSPC * SS;
       const float4* ring_b = ring + (t & 3) * kSPC * SS;
-      const int sl = xyzc - p0;
       const int x = t * a.Vs + xyzc;
       const int tb = (t - 1 + Lt) % Lt;
-      const float4* cen = ring_t + sl * SS + p;  // component e at cen[e * PAIRS]
-      float4 zu[3], zl[3];
+      const float4* cen = ring_t + sl * SS + p;
+      CP zu[3], zl[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float4 cu = cen[(hf * 3 + c) * PAIRS], cl4 = cen[((2 + hf) * 3 + c) * PAIRS];
-        zu[c] = make_float4(a.diag * cu.x, a.diag * cu.y, a.diag * cu.z, a.diag * cu.w);
-        zl[c] = make_float4(a.diag * cl4.x, a.diag * cl4.y, a.diag * cl4.z, a.diag * cl4.w);
+        const CP u = cp_ld(cen + (hf * 3 + c) * PAIRS), l = cp_ld(cen + ((2 + hf) * 3 + c) * PAIRS);
+        zu[c] = CP{pmul(dup(a.diag), u.re), pmul(dup(a.diag), u.im)};
+        zl[c] = CP{pmul(dup(a.diag), l.re), pmul(dup(a.diag), l.im)};
       }
       if (a.C) {
-        // row (alpha, spin hf, colour c) of the chirality-alpha 6x6 block
+        // row (spin hf, colour c) of each chirality's 6x6 block
         const float2* cl = a.C + (long)x * 72;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int j = 0; j < 6; ++j) {
-            f4cfma(zu[c], __ldg(cl + (hf * 3 + c) * 6 + j), cen[j * PAIRS]);
-            f4cfma(zl[c], __ldg(cl + 36 + (hf * 3 + c) * 6 + j), cen[(6 + j) * PAIRS]);
+            cmul_acc(zu[c], __ldg(cl + (hf * 3 + c) * 6 + j), cp_ld(cen + j * PAIRS));
+            cmul_acc(zl[c], __ldg(cl + 36 + (hf * 3 + c) * 6 + j), cp_ld(cen + (6 + j) * PAIRS));
           }
       }
       const float2* Ux = a.U + (long)x * 36;
       const long tV = (long)t * a.Vs;
 #pragma unroll
       for (int mu = 0; mu < 3; ++mu) {
-        // forward and backward neighbours: ring if inside the patch, else global
+        // neighbours: ring if inside the patch, else global (same component stride)
         const int f = valid ? nf[mu] : p0, b = valid ? nb[mu] : p0;
         const int lf = f - p0, lb = b - p0;
         const bool rf = lf >= 0 && lf < kSPC && f < a.Vs, rb = lb >= 0 && lb < kSPC && b < a.Vs;
-        const float4* pf = rf ? ring_t + lf * SS + p : gaddr(t * a.Vs + f);
-        const float4* pb = rb ? ring_t + lb * SS + p : gaddr(t * a.Vs + b);
-        const int esf = rf ? PAIRS : ges, esb = rb ? PAIRS : ges;
-        float4 uf[3], df[3], ub[3], db[3];
+        const float4* pf = rf ? ring_t + lf * SS + p : a.in + slab_index(q, a.V, tV + f, 0, PAIRS, p);
+        const float4* pb = rb ? ring_t + lb * SS + p : a.in + slab_index(q, a.V, tV + b, 0, PAIRS, p);
+        const float2* ub = a.U + (tV + b) * 36 + mu * 9;
         if (mu == 0) {
-          load_half<0>(pf, esf, hf, uf, df);
-          load_half<0>(pb, esb, hf, ub, db);
-          apply_half<0, +1>(zu, zl, hf, uf, df, Ux + 0, a.hw[0]);
-          apply_half<0, -1>(zu, zl, hf, ub, db, a.U + (tV + b) * 36 + 0, a.hw[0]);
+          hop<0, +1, PAIRS>(zu, zl, hf, pf, Ux, a.hw[0]);
+          hop<0, -1, PAIRS>(zu, zl, hf, pb, ub, a.hw[0]);
         } else if (mu == 1) {
-          load_half<1>(pf, esf, hf, uf, df);
-          load_half<1>(pb, esb, hf, ub, db);
-          apply_half<1, +1>(zu, zl, hf, uf, df, Ux + 9, a.hw[1]);
-          apply_half<1, -1>(zu, zl, hf, ub, db, a.U + (tV + b) * 36 + 9, a.hw[1]);
+          hop<1, +1, PAIRS>(zu, zl, hf, pf, Ux + 9, a.hw[1]);
+          hop<1, -1, PAIRS>(zu, zl, hf, pb, ub, a.hw[1]);
         } else {
-          load_half<2>(pf, esf, hf, uf, df);
-          load_half<2>(pb, esb, hf, ub, db);
-          apply_half<2, +1>(zu, zl, hf, uf, df, Ux + 18, a.hw[2]);
-          apply_half<2, -1>(zu, zl, hf, ub, db, a.U + (tV + b) * 36 + 18, a.hw[2]);
+          hop<2, +1, PAIRS>(zu, zl, hf, pf, Ux + 18, a.hw[2]);
+          hop<2, -1, PAIRS>(zu, zl, hf, pb, ub, a.hw[2]);
         }
       }
-      {
-        float4 uf[3], df[3], ub[3], db[3];
-        load_half<3>(ring_f + sl * SS + p, PAIRS, hf, uf, df);
-        load_half<3>(ring_b + sl * SS + p, PAIRS, hf, ub, db);
-        apply_half<3, +1>(zu, zl, hf, uf, df, Ux + 27, a.hw[3]);
-        apply_half<3, -1>(zu, zl, hf, ub, db, a.U + ((long)tb * a.Vs + xyzc) * 36 + 27, a.hw[3]);
-      }
+      hop<3, +1, PAIRS>(zu, zl, hf, ring_f + sl * SS + p, Ux + 27, a.hw[3]);
+      hop<3, -1, PAIRS>(zu, zl, hf, ring_b + sl * SS + p,
+                        a.U + ((long)tb * a.Vs + xyzc) * 36 + 27, a.hw[3]);
       if (valid) {
         const long so = slab_index(q, a.V, x, 0, PAIRS, p);
-        const int eu = hf * 3, el = (2 + hf) * 3;
         if (MODE == MODE_NEG_D) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            __stcs(a.out + so + (eu + c) * PAIRS, f4neg(zu[c]));
-            __stcs(a.out + so + (el + c) * PAIRS, f4neg(zl[c]));
+          for (int k = 0; k < 6; ++k) {
+            const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
+            const CP w = k < 3 ? zu[k] : zl[k - 3];
+            __stcs(a.out + so + e * PAIRS, make_float4(-w.re.x, -w.re.y, -w.im.x, -w.im.y));
           }
         } else {
-          float s6[6] = {0, 0, 0, 0, 0, 0};
+          float2 sre = make_float2(0.f, 0.f), sim = sre, snn = sre;
 #pragma unroll
           for (int k = 0; k < 6; ++k) {
-            const int e = k < 3 ? eu + k : el + k - 3;
-            const float4 w = k < 3 ? zu[k] : zl[k - 3], r = cen[e * PAIRS];
-            s6[0] += w.x * r.x + w.y * r.y;
-            s6[1] += w.x * r.y - w.y * r.x;
-            s6[2] += w.x * w.x + w.y * w.y;
-            s6[3] += w.z * r.z + w.w * r.w;
-            s6[4] += w.z * r.w - w.w * r.z;
-            s6[5] += w.z * w.z + w.w * w.w;
-            __stcs(a.out + so + e * PAIRS, w);
+            const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
+            const CP w = k < 3 ? zu[k] : zl[k - 3];
+            const CP r = cp_ld(cen + e * PAIRS);
+            // <w, r> = sum conj(w) r
+            sre = pfma(w.re, r.re, sre);
+            sre = pfma(w.im, r.im, sre);
+            sim = pfma(w.re, r.im, sim);
+            sim = pfma(pmul(dup(-1.f), w.im), r.re, sim);
+            snn = pfma(w.re, w.re, snn);
+            snn = pfma(w.im, w.im, snn);
+            __stcs(a.out + so + e * PAIRS, cp_f4(w));
           }
-#pragma unroll
-          for (int i = 0; i < 6; ++i) pr[i] += (double)s6[i];
+          pr[0] += (double)sre.x; pr[1] += (double)sim.x; pr[2] += (double)snn.x;
+          pr[3] += (double)sre.y; pr[4] += (double)sim.y; pr[5] += (double)snn.y;
         }
       }
     }
-    // row t+2 goes into the slot of row t-2 (free once every lane is past step t)
+    // the slot of row t-1 is refilled at the next step
     __syncthreads();
-    if (do_stage) stage_store(t + 2, sv);
-    __syncthreads();
+    if (s_abort) break;
+  }
+  if (s_abort) {
+    // let the copies still in flight land before the CTA's shared memory is released
+    if (last_issued >= 1) (void)wait_row(last_issued);
+    return;
   }
   if (MODE != MODE_NEG_D) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -401,63 +458,92 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
   }
 }
 
-// MR update between two dslash passes (streaming, slab layout):
-//   r <- r - a w  (r_{t+1}),   psi_out <- psi_src + a r_t   (psi_src in the ABI
-// layout for psi_0).  One float4 (two right-hand sides) per thread.
+// ---------------------------------------------------------------------------
+// streaming kernels over the slab layout
+// ---------------------------------------------------------------------------
+// decomposes a slab float4 index into (slab q, site x, component e, pair p)
 template <int PAIRS>
-__global__ void mr_update(float4* __restrict__ r, const float4* __restrict__ w,
-                          const float4* __restrict__ psi_src, float4* __restrict__ psi_out,
-                          const float2* __restrict__ alpha, int V, int np, int psi_abi) {
+__device__ __forceinline__ void slab_coords(long i, int V, int& q, int& x, int& e, int& p) {
+  p = (int)(i % PAIRS);
+  long r = i / PAIRS;
+  e = (int)(r % 12);
+  r /= 12;
+  x = (int)(r % V);
+  q = (int)(r / V);
+}
+
+// psi_0 (ABI layout [V][12][m'] complex) -> slab layout
+template <int PAIRS>
+__global__ void to_slab(const float4* __restrict__ src, float4* __restrict__ dst, int V, int np) {
   const long n = (long)V * 12 * np;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x) {
-    const int p = (int)(i % PAIRS);
-    long rr = i / PAIRS;
-    const int e = (int)(rr % 12);
-    rr /= 12;
-    const int x = (int)(rr % V);
-    const int q = (int)(rr / V);
-    const int gp = q * PAIRS + p;
-    const float2 a0 = alpha[2 * gp], a1 = alpha[2 * gp + 1];
-    const float4 rv = __ldcs(r + i), wv = __ldcs(w + i);
-    const float4 pv = psi_abi ? __ldcs(psi_src + ((long)x * 12 + e) * np + gp) : __ldcs(psi_src + i);
-    __stcs(r + i, f4sub(rv, f4mul2(a0, a1, wv)));
-    __stcs(psi_out + i, f4add(pv, f4mul2(a0, a1, rv)));
+    int q, x, e, p;
+    slab_coords<PAIRS>(i, V, q, x, e, p);
+    const float4 v = __ldcs(src + ((long)x * 12 + e) * np + q * PAIRS + p);
+    __stcs(dst + i, make_float4(v.x, v.z, v.y, v.w));
   }
 }
 
-// psi_N = psi_{N-1} + a r_{N-1} (slab), partial |psi_N|^2 per right-hand side.
-// Grid: one CTA per (slice, patch), looping over t; thread = (site, pair).
+// MR update between two dslash passes: r <- r - a w (r_{t+1}),
+// psi <- psi + a r_t.  One float4 (a pair of right-hand sides) per thread.
 template <int PAIRS>
-__global__ void __launch_bounds__(kSPC * PAIRS) last_update(MarchArgs a) {
-  constexpr int NC = kSPC * PAIRS, NW = NC / 32;
-  __shared__ double red[NW][PAIRS][2];
-  const int q = blockIdx.x / a.npatch, patch = blockIdx.x % a.npatch;
-  const int s_loc = threadIdx.x / PAIRS, p = threadIdx.x % PAIRS;
-  const int gp = q * PAIRS + p;
-  const int xyz = patch * kSPC + s_loc;
-  const float2 al0 = a.alpha[2 * gp], al1 = a.alpha[2 * gp + 1];
-  double n0 = 0, n1 = 0;
-  if (xyz < a.Vs) {
-    for (int t = 0; t < a.L[3]; ++t) {
-      const int x = t * a.Vs + xyz;
-      const long so = slab_index(q, a.V, x, 0, PAIRS, p);
-      const long ao = (long)x * 12 * a.np + gp;
-      float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-      for (int e = 0; e < 12; ++e) {
-        const float4 rc = __ldcs(a.in + so + e * PAIRS);
-        const float4 pc = a.psi_abi ? __ldcs(a.psi_src + ao + (long)e * a.np)
-                                    : __ldcs(a.psi_src + so + e * PAIRS);
-        const float4 pn = f4add(pc, f4mul2(al0, al1, rc));
-        s0 += pn.x * pn.x + pn.y * pn.y;
-        s1 += pn.z * pn.z + pn.w * pn.w;
-        __stcs(a.psi_out + so + e * PAIRS, pn);
-      }
-      n0 += (double)s0;
-      n1 += (double)s1;
-    }
+__global__ void mr_update(float4* __restrict__ r, const float4* __restrict__ w,
+                          float4* __restrict__ psi, const float2* __restrict__ alpha, int V,
+                          int np) {
+  const long n = (long)V * 12 * np;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    int q, x, e, p;
+    slab_coords<PAIRS>(i, V, q, x, e, p);
+    const int gp = q * PAIRS + p;
+    const float2 a0 = alpha[2 * gp], a1 = alpha[2 * gp + 1];
+    const float2 ar = make_float2(a0.x, a1.x), ai = make_float2(a0.y, a1.y);
+    const float4 rv = __ldcs(r + i), wv = __ldcs(w + i), pv = __ldcs(psi + i);
+    // a w and a r per right-hand side
+    const float2 wr = make_float2(wv.x, wv.y), wi = make_float2(wv.z, wv.w);
+    const float2 rr = make_float2(rv.x, rv.y), ri = make_float2(rv.z, rv.w);
+    const float awr0 = ar.x * wr.x - ai.x * wi.x, awr1 = ar.y * wr.y - ai.y * wi.y;
+    const float awi0 = ar.x * wi.x + ai.x * wr.x, awi1 = ar.y * wi.y + ai.y * wr.y;
+    const float arr0 = ar.x * rr.x - ai.x * ri.x, arr1 = ar.y * rr.y - ai.y * ri.y;
+    const float ari0 = ar.x * ri.x + ai.x * rr.x, ari1 = ar.y * ri.y + ai.y * rr.y;
+    __stcs(r + i, make_float4(rv.x - awr0, rv.y - awr1, rv.z - awi0, rv.w - awi1));
+    __stcs(psi + i, make_float4(pv.x + arr0, pv.y + arr1, pv.z + ari0, pv.w + ari1));
   }
+}
+
+// psi_N = psi_{N-1} + a r_{N-1} in place, partial |psi_N|^2 per right-hand side.
+// Streaming: CTA (slab q, chunk g) covers the contiguous sites
+// [g*cs, (g+1)*cs) of slab q; thread i handles float4s i, i + 256, ... of that
+// range, all of one pair (256 is a multiple of P).  Partials go to
+// part[(rhs * nchunk + g) * 4 + 2].
+template <int PAIRS>
+__global__ void __launch_bounds__(256) last_update(const float4* __restrict__ r,
+                                                   float4* __restrict__ psi,
+                                                   const float2* __restrict__ alpha,
+                                                   double* __restrict__ part, int V, int cs,
+                                                   int nchunk) {
+  constexpr int NW = 256 / 32;
+  __shared__ double red[NW][PAIRS][2];
+  const int q = blockIdx.x / nchunk, g = blockIdx.x % nchunk;
+  const int p = threadIdx.x % PAIRS;
+  const int gp = q * PAIRS + p;
+  const float2 a0 = alpha[2 * gp], a1 = alpha[2 * gp + 1];
+  const long x0 = (long)g * cs, x1 = min((long)V, x0 + cs);
+  const long i0 = slab_index(q, V, (int)x0, 0, PAIRS, 0), i1 = slab_index(q, V, (int)x1, 0, PAIRS, 0);
+  float s0 = 0.f, s1 = 0.f;
+  for (long i = i0 + threadIdx.x; i < i1; i += 256) {
+    const float4 rc = __ldcs(r + i);
+    const float4 pc = __ldcs(psi + i);
+    const float4 pn = make_float4(pc.x + a0.x * rc.x - a0.y * rc.z,
+                                  pc.y + a1.x * rc.y - a1.y * rc.w,
+                                  pc.z + a0.x * rc.z + a0.y * rc.x,
+                                  pc.w + a1.x * rc.w + a1.y * rc.y);
+    s0 += pn.x * pn.x + pn.z * pn.z;
+    s1 += pn.y * pn.y + pn.w * pn.w;
+    __stcs(psi + i, pn);
+  }
+  double n0 = s0, n1 = s1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int off = 16; off >= PAIRS; off >>= 1) {
     n0 += __shfl_xor_sync(0xffffffffu, n0, off);
@@ -475,8 +561,8 @@ __global__ void __launch_bounds__(kSPC * PAIRS) last_update(MarchArgs a) {
       t1 += red[w][threadIdx.x][1];
     }
     const int rhs0 = 2 * (q * PAIRS + threadIdx.x);
-    double* q0 = a.part + ((long)rhs0 * a.npatch + patch) * 4;
-    double* q1 = a.part + ((long)(rhs0 + 1) * a.npatch + patch) * 4;
+    double* q0 = part + ((long)rhs0 * nchunk + g) * 4;
+    double* q1 = part + ((long)(rhs0 + 1) * nchunk + g) * 4;
     q0[0] = 0; q0[1] = 0; q0[2] = t0;
     q1[0] = 0; q1[1] = 0; q1[2] = t1;
   }
@@ -513,18 +599,12 @@ __global__ void scale_to_abi(const float4* __restrict__ src, float4* __restrict_
   const long n = (long)V * 12 * np;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x) {
-    // i enumerates the slab: ((q*V + x)*12 + e)*PAIRS + p
-    const int p = (int)(i % PAIRS);
-    long r = i / PAIRS;
-    const int e = (int)(r % 12);
-    r /= 12;
-    const int x = (int)(r % V);
-    const int q = (int)(r / V);
+    int q, x, e, p;
+    slab_coords<PAIRS>(i, V, q, x, e, p);
     const int gp = q * PAIRS + p;
-    float4 v = __ldcs(src + i);
+    const float4 v = __ldcs(src + i);
     const float s0 = scale[2 * gp], s1 = scale[2 * gp + 1];
-    v.x *= s0; v.y *= s0; v.z *= s1; v.w *= s1;
-    __stcs(dst + ((long)x * 12 + e) * np + gp, v);
+    __stcs(dst + ((long)x * 12 + e) * np + gp, make_float4(v.x * s0, v.z * s0, v.y * s1, v.w * s1));
   }
 }
 
@@ -658,9 +738,9 @@ __global__ void clover_kernel(int L0, int L1, int L2, int L3, float csw,
 template <int PAIRS, int MODE>
 cudaError_t run_march(const MarchArgs& a, int nsl, cudaStream_t s) {
   static const char* names[2] = {"mr_neg_dslash", "mr_dslash_dot"};
-  constexpr int SS = 12 * PAIRS + 4;
+  constexpr int SS = 12 * PAIRS;
   const size_t smem = sizeof(float4) * (size_t)kRing * kSPC * SS;
-  static bool attr = false;
+  static bool attr = false;  // (SS as in the kernel)
   if (!attr) {
     cudaFuncSetAttribute(march_kernel<PAIRS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
@@ -668,6 +748,41 @@ cudaError_t run_march(const MarchArgs& a, int nsl, cudaStream_t s) {
   }
   TimedScope ts(names[MODE], s);
   march_kernel<PAIRS, MODE><<<nsl * a.npatch, march_threads<PAIRS>(), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+int* status_word() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+  return static_cast<int*>(p);
+}
+
+// common part of the smoother and the operator apply: the slab copy of the
+// input (into ps) and the march arguments
+template <int PAIRS>
+cudaError_t march_setup(const Geom& g, const float2* U, const float2* C, const float2* in,
+                        char* ws, MarchArgs& a, cudaStream_t s) {
+  const SmoothWs lay = smooth_ws_layout(g);
+  float4* ps = reinterpret_cast<float4*>(ws + lay.ps);
+  a = MarchArgs{};
+  a.U = U;
+  a.C = C;
+  a.part = reinterpret_cast<double*>(ws + lay.part);
+  a.status = status_word();
+  if (!a.status) return cudaErrorInvalidSymbol;
+  for (int i = 0; i < 4; ++i) {
+    a.L[i] = g.L[i];
+    a.hw[i] = g.hw[i];
+  }
+  a.V = (int)g.V;
+  a.Vs = (int)(g.V / g.L[3]);
+  a.np = g.m / 2;
+  a.npatch = (a.Vs + kSPC - 1) / kSPC;
+  a.diag = g.diag;
+  {
+    TimedScope ts("mr_to_slab", s);
+    to_slab<PAIRS><<<4096, 256, 0, s>>>(reinterpret_cast<const float4*>(in), ps, a.V, a.np);
+  }
   return cudaGetLastError();
 }
 
@@ -681,33 +796,19 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
   double* part = reinterpret_cast<double*>(ws + lay.part);
   float2* alpha = reinterpret_cast<float2*>(ws + lay.alpha);
   float* scale = reinterpret_cast<float*>(ws + lay.scale);
-
-  MarchArgs a{};
-  a.U = U;
-  a.C = C;
-  a.alpha = alpha;
-  a.part = part;
-  for (int i = 0; i < 4; ++i) {
-    a.L[i] = g.L[i];
-    a.hw[i] = g.hw[i];
-  }
-  a.V = (int)g.V;
-  a.Vs = (int)(g.V / g.L[3]);
-  a.np = g.m / 2;
-  a.npatch = (a.Vs + kSPC - 1) / kSPC;
-  a.diag = g.diag;
+  MarchArgs a;
+  cudaError_t e = march_setup<PAIRS>(g, U, C, psi0, ws, a, s);
+  if (e != cudaSuccess) return e;
   const int nsl = a.np / PAIRS;
   const int G = a.npatch;  // partial sums per right-hand side
-  const float4* p0 = reinterpret_cast<const float4*>(psi0);
   const int nred = (g.m + 63) / 64;
-  cudaError_t e;
   auto reduce = [&](int mode) {
     TimedScope ts("mr_reduce", s);
     finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, mode, alpha, scale);
   };
 
-  // r_0 = -D psi_0  (psi_0 in the ABI layout)
-  a.in = p0;
+  // r_0 = -D psi_0
+  a.in = ps;
   a.out = r;
   if ((e = run_march<PAIRS, MODE_NEG_D>(a, nsl, s)) != cudaSuccess) return e;
   // w_0 = D r_0 -> a_0
@@ -719,20 +820,18 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
     // r_t = r_{t-1} - a w_{t-1}, psi_t = psi_{t-1} + a r_{t-1}; w_t = D r_t -> a_t
     {
       TimedScope ts("mr_update", s);
-      mr_update<PAIRS><<<4096, 256, 0, s>>>(r, w, t == 1 ? p0 : ps, ps, alpha, a.V, a.np,
-                                            t == 1 ? 1 : 0);
+      mr_update<PAIRS><<<4096, 256, 0, s>>>(r, w, ps, alpha, a.V, a.np);
     }
     if ((e = run_march<PAIRS, MODE_D_DOT>(a, nsl, s)) != cudaSuccess) return e;
     reduce(0);
   }
   // psi_N = psi_{N-1} + a_{N-1} r_{N-1}, partial |psi_N|^2
-  a.in = r;
-  a.psi_src = g.niter == 1 ? p0 : ps;
-  a.psi_abi = g.niter == 1;
-  a.psi_out = ps;
+  // |psi_N|^2 partials over npatch chunks of the slab (the partial-sum array
+  // holds npatch entries per right-hand side)
   {
+    const int cs = (a.V + G - 1) / G;
     TimedScope ts("mr_last_update", s);
-    last_update<PAIRS><<<nsl * a.npatch, kSPC * PAIRS, 0, s>>>(a);
+    last_update<PAIRS><<<nsl * G, 256, 0, s>>>(r, ps, alpha, part, a.V, cs, G);
   }
   reduce(1);
   {
@@ -746,31 +845,21 @@ template <int PAIRS>
 cudaError_t dirac_impl(const Geom& g, const float2* U, const float2* C, const float2* in,
                        float2* out, char* ws, cudaStream_t s) {
   const SmoothWs lay = smooth_ws_layout(g);
-  float4* tmp = reinterpret_cast<float4*>(ws + lay.ra);
+  float4* r = reinterpret_cast<float4*>(ws + lay.ra);
+  float4* ps = reinterpret_cast<float4*>(ws + lay.ps);
   float* scale = reinterpret_cast<float*>(ws + lay.scale);
-  MarchArgs a{};
-  a.U = U;
-  a.C = C;
-  for (int i = 0; i < 4; ++i) {
-    a.L[i] = g.L[i];
-    a.hw[i] = g.hw[i];
-  }
-  a.V = (int)g.V;
-  a.Vs = (int)(g.V / g.L[3]);
-  a.np = g.m / 2;
-  a.npatch = (a.Vs + kSPC - 1) / kSPC;
-  a.diag = g.diag;
-  a.in = reinterpret_cast<const float4*>(in);
-  a.in_abi = 1;
-  a.out = tmp;
-  cudaError_t e = run_march<PAIRS, MODE_NEG_D>(a, a.np / PAIRS, s);
+  MarchArgs a;
+  cudaError_t e = march_setup<PAIRS>(g, U, C, in, ws, a, s);
   if (e != cudaSuccess) return e;
+  a.in = ps;
+  a.out = r;
+  if ((e = run_march<PAIRS, MODE_NEG_D>(a, a.np / PAIRS, s)) != cudaSuccess) return e;
   {
     TimedScope ts("fill", s);
     fill_kernel<<<1, 64, 0, s>>>(scale, g.m, -1.0f);
   }
   TimedScope ts("mr_scale", s);
-  scale_to_abi<PAIRS><<<2048, 256, 0, s>>>(tmp, reinterpret_cast<float4*>(out), scale, a.V, a.np);
+  scale_to_abi<PAIRS><<<2048, 256, 0, s>>>(r, reinterpret_cast<float4*>(out), scale, a.V, a.np);
   return cudaGetLastError();
 }
 
@@ -794,6 +883,17 @@ cudaError_t launch_smoother(const Geom& g, const float2* U, const float2* C,
                             const float2* psi0, float2* psi, char* ws, cudaStream_t s) {
   if (g.m % 8 == 0) return smoother_impl<4>(g, U, C, psi0, psi, ws, s);
   return smoother_impl<2>(g, U, C, psi0, psi, ws, s);
+}
+
+cudaError_t read_device_status(int* out, cudaStream_t s) {
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  int v = 0;
+  if ((e = cudaMemcpyFromSymbol(&v, g_status, sizeof(int))) != cudaSuccess) return e;
+  const int zero = 0;
+  if ((e = cudaMemcpyToSymbol(g_status, &zero, sizeof(int))) != cudaSuccess) return e;
+  *out = v;
+  return cudaSuccess;
 }
 
 }  // namespace mg

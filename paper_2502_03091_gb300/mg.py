@@ -28,7 +28,7 @@ MG_CALL_SMOOTH, MG_CALL_TRUNCATE, MG_CALL_COARSEN = 0, 1, 2
 EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_apply_dirac", "mg_smooth_testvecs", "mg_chiral_truncate",
            "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply", "mg_chiral_truncate_static",
            "mg_timing_enable",
-           "mg_timing_read", "mg_last_error", "mg_version")
+           "mg_timing_read", "mg_sync_status", "mg_last_error", "mg_version")
 
 
 class MgError(RuntimeError):
@@ -125,6 +125,8 @@ def library(path: str = LIB_PATH):
     lib.mg_timing_enable.restype = ctypes.c_int
     lib.mg_timing_read.argtypes = [ctypes.POINTER(_TimingEntry), ctypes.c_int]
     lib.mg_timing_read.restype = ctypes.c_int
+    lib.mg_sync_status.argtypes = [P]
+    lib.mg_sync_status.restype = ctypes.c_int
     lib.mg_last_error.restype = ctypes.c_char_p
     lib.mg_version.restype = ctypes.c_char_p
     _lib = lib
@@ -176,6 +178,13 @@ def mg_timing_read() -> dict:
     if n < 0:
         raise MgError(4, library().mg_last_error().decode())
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(n)}
+
+
+def mg_sync_status(stream=None):
+    """Waits for the stream; raises MgError (MG_ERR_TIMEOUT) if a smoother or
+    operator pass enqueued since the previous call gave up waiting for its
+    staged input."""
+    _check(library().mg_sync_status(_stream(stream)))
 
 
 def mg_workspace_size(prob: Problem, which: int) -> int:
