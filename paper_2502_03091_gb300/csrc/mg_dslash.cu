@@ -145,9 +145,37 @@ __device__ __forceinline__ long slab_index(int q, int V, int x, int e, int PAIRS
 // of the neighbour's pair (component e at src[e * PAIRS], shared ring or
 // global slab); u at the 9 entries of the link.
 // ---------------------------------------------------------------------------
+// the 9 entries of one link at u (u is 8-byte aligned; u16 says whether u
+// itself is 16-byte aligned): four 16-byte loads and one 8-byte load
+__device__ __forceinline__ void load_link(const float2* __restrict__ u, bool u16, float2 L[9]) {
+  // the 16-byte aligned run of 8 entries starts at u or at u + 1
+  const float4* a4 = reinterpret_cast<const float4*>(u16 ? u : u + 1);
+  float4 v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __ldg(a4 + i);
+  const float2 last = __ldg(u16 ? u + 8 : u);
+  if (u16) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      L[2 * i] = make_float2(v[i].x, v[i].y);
+      L[2 * i + 1] = make_float2(v[i].z, v[i].w);
+    }
+    L[8] = last;
+  } else {
+    L[0] = last;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      L[2 * i + 1] = make_float2(v[i].x, v[i].y);
+      L[2 * i + 2] = make_float2(v[i].z, v[i].w);
+    }
+  }
+}
+
 template <int MU, int S, int PAIRS>
 __device__ __forceinline__ void hop(CP zu[3], CP zl[3], int hf, const float4* src,
                                     const float2* __restrict__ u, float hw) {
+  float2 L[9];
+  load_link(u, (reinterpret_cast<uintptr_t>(u) & 15) == 0, L);
   // (B chi_l)_hf uses lower spin 2 + lo
   const int lo = (MU == 0 || MU == 1) ? 1 - hf : hf;
   CP h[3];
@@ -202,8 +230,8 @@ __device__ __forceinline__ void hop(CP zu[3], CP zl[3], int hf, const float4* sr
     CP g{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      if (S > 0) lmul(g, __ldg(u + c * 3 + d), h[d], nh[d]);
-      else lmulc(g, __ldg(u + d * 3 + c), h[d], nh[d]);
+      if (S > 0) lmul(g, L[c * 3 + d], h[d], nh[d]);
+      else lmulc(g, L[d * 3 + c], h[d], nh[d]);
     }
     zu[c].re = pfma(dup(hw), g.re, zu[c].re);
     zu[c].im = pfma(dup(hw), g.im, zu[c].im);
@@ -278,6 +306,7 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
   extern __shared__ __align__(128) float4 ring[];  // [kRing][kSPC][SS]
   __shared__ __align__(8) unsigned long long bar[kRing];
   __shared__ double red[NW][PAIRS][6];
+  __shared__ double pr_s[MODE == MODE_D_DOT ? NC : 1][6];  // per-lane FP64 partial sums
   __shared__ int s_abort;
   const int q = blockIdx.x / a.npatch, patch = blockIdx.x % a.npatch;
   const int p0 = patch * kSPC;
@@ -329,7 +358,12 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
   }
   if (!wait_row(-1) || !wait_row(0)) give_up();
 
-  double pr[6] = {0, 0, 0, 0, 0, 0};
+  // partial sums: FP32 pairs in registers over 8 steps, then added into the
+  // lane's FP64 slots in shared memory (keeps registers for the hops)
+  float2 sre = make_float2(0.f, 0.f), sim = sre, snn = sre;
+  if (MODE == MODE_D_DOT)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) pr_s[threadIdx.x][i] = 0.0;
   int last_issued = 1;
   for (int t = 0; t < Lt; ++t) {
     if (t + 2 <= Lt) {
@@ -400,7 +434,6 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
             __stcs(a.out + so + e * PAIRS, make_float4(-w.re.x, -w.re.y, -w.im.x, -w.im.y));
           }
         } else {
-          float2 sre = make_float2(0.f, 0.f), sim = sre, snn = sre;
 #pragma unroll
           for (int k = 0; k < 6; ++k) {
             const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
@@ -415,9 +448,13 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
             snn = pfma(w.im, w.im, snn);
             __stcs(a.out + so + e * PAIRS, cp_f4(w));
           }
-          pr[0] += (double)sre.x; pr[1] += (double)sim.x; pr[2] += (double)snn.x;
-          pr[3] += (double)sre.y; pr[4] += (double)sim.y; pr[5] += (double)snn.y;
         }
+      }
+      if (MODE == MODE_D_DOT && ((t & 7) == 7 || t == Lt - 1)) {
+        double* ps_ = pr_s[threadIdx.x];
+        ps_[0] += (double)sre.x; ps_[1] += (double)sim.x; ps_[2] += (double)snn.x;
+        ps_[3] += (double)sre.y; ps_[4] += (double)sim.y; ps_[5] += (double)snn.y;
+        sre = sim = snn = make_float2(0.f, 0.f);
       }
     }
     // the slot of row t-1 is refilled at the next step
@@ -430,6 +467,9 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
     return;
   }
   if (MODE != MODE_NEG_D) {
+    double pr[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) pr[i] = pr_s[threadIdx.x][i];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // lane = 2 * (s * PAIRS + p) + hf: sum over hf and s, keep p
 #pragma unroll
