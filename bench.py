@@ -194,6 +194,62 @@ def oracle_sample(w):
     return dt, scale, threads, desc
 
 
+class Replicas:
+    """N independent replicas of the setup, one process per GPU (the path is
+    not sharded: no data-path collective).  Only the timing needs the group:
+    a barrier on both sides of the timed region and the maximum over ranks.
+    Reads RANK / WORLD_SIZE / LOCAL_RANK; backend "nccl" on GPUs, "gloo" for
+    the CPU tests of this logic."""
+
+    def __init__(self, backend: str = "nccl", device: str = "cuda"):
+        import torch
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.cuda = device == "cuda"
+        self.device = torch.device("cuda", self.local) if self.cuda else torch.device("cpu")
+        if self.cuda:
+            torch.cuda.set_device(self.local)
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=self.device)
+            else:
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def _sync(self):
+        if self.cuda:
+            import torch
+            torch.cuda.synchronize()
+
+    def barrier(self):
+        self._sync()
+        if self.dist:
+            self.dist.barrier()
+        self._sync()
+
+    def max(self, x: float) -> float:
+        if not self.dist:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def per_level(ms_max: float, world: int) -> float:
+    """Whole-job seconds per level: `world` replicas each built one level in
+    (at most) ms_max milliseconds."""
+    return ms_max / 1e3 / world
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -239,18 +295,11 @@ def run_ours(args, w):
     from paper_2502_03091_gb300 import build as B
     from paper_2502_03091_gb300 import mg
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rep = Replicas()
+    world, rank, local = rep.world, rep.rank, rep.local
     if rank == 0:
         B.build()
-    if dist:
-        dist.barrier()
+    rep.barrier()
     mg.library()
 
     prob = mg.Problem(dims=w["dims"], block=w["block"], m0=w["m0"], n_vec=w["m"], k=w["k"],
@@ -276,18 +325,7 @@ def run_ours(args, w):
         lv.run(stream)
         mg.mg_coarse_apply(prob, lv.X, lv.Y, v_in, v_out, stream)
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = rep.barrier, rep.max
 
     for _ in range(args.warmup):
         step()
@@ -335,8 +373,7 @@ def run_ours(args, w):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps)
 
     if rank != 0:
-        if dist:
-            dist.destroy_process_group()
+        rep.close()
         return
 
     # ---- roofline of the dominant kernel ----
@@ -395,7 +432,7 @@ def run_ours(args, w):
                "sample": desc}
 
     out = {
-        "metric": METRIC, "value": ms / 1e3 / world, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": per_level(ms, world), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded random SU(3) links, Gaussian starts)",
@@ -408,13 +445,12 @@ def run_ours(args, w):
         "gpu_launches": launches,
         "blk_flags_nonzero": int((flags != 0).sum()),
         "clocks": clocks,
-        "e2e": {"value": e2e_ms / 1e3 / world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": per_level(e2e_ms, world), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "cpu_baseline": cpu,
     }
     print(json.dumps(out), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    rep.close()
 
 
 def _kernel_sha1():
