@@ -145,6 +145,31 @@ def psi0(dims, m: int, seed: int, stream: int = STREAM_PSI0) -> np.ndarray:
     return (g[0::2] + 1j * g[1::2]).reshape(volume(dims), 4, 3, m)
 
 
+def psi0_sites(dims, m: int, seed: int, lo: int, hi: int,
+               stream: int = STREAM_PSI0) -> np.ndarray:
+    """Sites lo .. hi-1 of psi0(dims, m, seed): layout [hi-lo][4][3][m], the
+    same numbers (element n of the full array uses normals 2n and 2n+1), for
+    lattices whose full start set is too large to draw at once."""
+    per = 12 * m
+    g = normals(seed, stream, 2 * lo * per, 2 * (hi - lo) * per)
+    return (g[0::2] + 1j * g[1::2]).reshape(hi - lo, 4, 3, m)
+
+
+def psi0_columns(dims, m: int, seed: int, cols, stream: int = STREAM_PSI0) -> np.ndarray:
+    """Columns `cols` of psi0(dims, m, seed): layout [V][4][3][len(cols)]."""
+    V = volume(dims)
+    cols = np.asarray(cols, dtype=np.int64)
+    n = (np.arange(V * 12, dtype=np.int64)[:, None] * m + cols[None, :]).ravel()
+    key = stream_key(seed, stream)
+    ctr = np.stack([4 * n, 4 * n + 1, 4 * n + 2, 4 * n + 3], axis=1).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        bits = splitmix64((ctr + key) & _MASK)
+    u = ((bits >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+    re = np.sqrt(-2.0 * np.log(u[:, 0])) * np.cos(2.0 * np.pi * u[:, 1])
+    im = np.sqrt(-2.0 * np.log(u[:, 2])) * np.cos(2.0 * np.pi * u[:, 3])
+    return (re + 1j * im).reshape(V, 4, 3, len(cols))
+
+
 def coarse_vectors(n_coarse: int, two_k: int, nrhs: int, seed: int) -> np.ndarray:
     """Complex Gaussian coarse vectors, layout [nc][2k][nrhs]."""
     n = n_coarse * two_k * nrhs
