@@ -119,10 +119,21 @@ def random_su3(seed: int, stream: int, n: int, eps, start: int = 0,
     return out
 
 
-def gauge_field(dims, eps: float, seed: int) -> np.ndarray:
-    """Random SU(3) gauge field U[V][4][3][3] (complex128), U_mu(x) = exp(i eps H)."""
+def gauge_field(dims, eps: float, seed: int, threads: int = 1) -> np.ndarray:
+    """Random SU(3) gauge field U[V][4][3][3] (complex128), U_mu(x) = exp(i eps H).
+    threads > 1 draws contiguous chunks of links on host threads (the same
+    numbers: link j always uses normals 8j .. 8j+7)."""
     V = volume(dims)
-    return random_su3(seed, STREAM_GAUGE, 4 * V, eps).reshape(V, 4, 3, 3)
+    n = 4 * V
+    if threads <= 1 or n < 65536:
+        return random_su3(seed, STREAM_GAUGE, n, eps).reshape(V, 4, 3, 3)
+    import concurrent.futures as cf
+    step = -(-n // threads)
+    parts = [(lo, min(n, lo + step)) for lo in range(0, n, step)]
+    with cf.ThreadPoolExecutor(threads) as ex:
+        out = list(ex.map(lambda r: random_su3(seed, STREAM_GAUGE, r[1] - r[0], eps, start=r[0]),
+                          parts))
+    return np.concatenate(out).reshape(V, 4, 3, 3)
 
 
 def unit_gauge_field(dims) -> np.ndarray:

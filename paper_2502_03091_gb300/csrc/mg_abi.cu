@@ -44,7 +44,7 @@ mg_status make_geom(const mg_problem* p, Geom* g) {
     nb *= p->block[i];
   }
   if (V > (1L << 30)) return fail(MG_ERR_SHAPE, "volume %ld too large", V);
-  if (p->precision != MG_PREC_FP32)
+  if (p->precision != MG_PREC_FP32 && p->precision != MG_PREC_MIXED)
     return fail(MG_ERR_UNSUPPORTED, "precision %d not implemented", p->precision);
   if (p->n_vec < 4 || p->n_vec > kMaxM || p->n_vec % 4 != 0)
     return fail(MG_ERR_UNSUPPORTED, "n_vec must be a multiple of 4 in [4, %d], got %d", kMaxM,
@@ -63,6 +63,7 @@ mg_status make_geom(const mg_problem* p, Geom* g) {
   g->nb = nb;
   g->nblk = V / nb;
   g->m = p->n_vec;
+  g->prec = p->precision;
   g->k = p->k;
   g->niter = p->mr_iters;
   g->m0 = p->m0;
@@ -81,7 +82,8 @@ mg_status make_geom(const mg_problem* p, Geom* g) {
 
 SmoothWs smooth_ws_layout(const Geom& g) {
   SmoothWs w{};
-  const size_t field = sizeof(float2) * (size_t)g.V * 12 * g.m;
+  // one spinor field: complex64 or, in the mixed-precision path, two FP16 per complex
+  const size_t field = (g.prec == MG_PREC_MIXED ? 4 : 8) * (size_t)g.V * 12 * g.m;
   size_t o = 0;
   w.ra = o; o = align256(o + field);
   w.wa = o; o = align256(o + field);

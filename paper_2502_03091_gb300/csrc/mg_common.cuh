@@ -25,6 +25,7 @@ struct Geom {
   double m0, xi;  // mass, anisotropy
   float hw[4];    // hop weights -1/2 w_mu
   float diag;     // m0 + sum_mu w_mu
+  int prec;       // mg_precision
 };
 
 constexpr int kMaxM = 64;  // largest m' this build supports

@@ -10,12 +10,17 @@
 // products of a_{t+1}.
 //
 // Internal "slab" layout of r, w and psi: the right-hand sides are cut into
-// slabs of 2P (P pairs); float4 f[((q*V + x)*12 + e)*P + p] holds component
+// slabs of 2P (P pairs); element f[((q*V + x)*12 + e)*P + p] holds component
 // e = spin*3 + colour of site x for the pair (2(qP+p), 2(qP+p)+1) as
 // (re_0, re_1, im_0, im_1).  The real parts and the imaginary parts of a
 // pair are packed FP32 pairs, the operands of the f32x2 instructions, and the
-// 12 x 2P numbers of one site and slab are contiguous (768 bytes for P = 4).
+// 12 x 2P numbers of one site and slab are contiguous.  Elements are float4
+// (FP32 storage, 768 bytes per site and slab for P = 4) or four halves in a
+// uint2 (FP16 storage of the mixed-precision path, 384 bytes); arithmetic is
+// FP32 in both.
 #include <cstdint>
+
+#include <cuda_fp16.h>
 
 #include "mg_common.cuh"
 
@@ -56,11 +61,37 @@ __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 struct CP {
   float2 re, im;
 };
-__device__ __forceinline__ CP cp_ld(const float4* p) {
-  const float4 v = *p;
+__device__ __forceinline__ float2 h2_to_f2(unsigned int u) {
+  __half2 h;
+  *reinterpret_cast<unsigned int*>(&h) = u;
+  return __half22float2(h);
+}
+__device__ __forceinline__ unsigned int f2_to_h2(float2 f) {
+  const __half2 h = __float22half2_rn(f);
+  return *reinterpret_cast<const unsigned int*>(&h);
+}
+// storage element <-> two right-hand sides of one component
+__device__ __forceinline__ CP cp_unpack(float4 v) {
   return CP{make_float2(v.x, v.y), make_float2(v.z, v.w)};
 }
-__device__ __forceinline__ float4 cp_f4(CP a) { return make_float4(a.re.x, a.re.y, a.im.x, a.im.y); }
+__device__ __forceinline__ CP cp_unpack(uint2 v) { return CP{h2_to_f2(v.x), h2_to_f2(v.y)}; }
+template <typename T>
+__device__ __forceinline__ T cp_pack(CP a);
+template <>
+__device__ __forceinline__ float4 cp_pack<float4>(CP a) {
+  return make_float4(a.re.x, a.re.y, a.im.x, a.im.y);
+}
+template <>
+__device__ __forceinline__ uint2 cp_pack<uint2>(CP a) {
+  return make_uint2(f2_to_h2(a.re), f2_to_h2(a.im));
+}
+template <typename T>
+__device__ __forceinline__ CP cp_ld(const T* p) {
+  return cp_unpack(*p);
+}
+__device__ __forceinline__ CP cp_neg(CP a) {
+  return CP{make_float2(-a.re.x, -a.re.y), make_float2(-a.im.x, -a.im.y)};
+}
 
 // acc += u h for a link entry u shared by both right-hand sides; nim = -Im h
 __device__ __forceinline__ void lmul(CP& acc, float2 u, const CP& h, float2 nim) {
@@ -171,8 +202,8 @@ __device__ __forceinline__ void load_link(const float2* __restrict__ u, bool u16
   }
 }
 
-template <int MU, int S, int PAIRS>
-__device__ __forceinline__ void hop(CP zu[3], CP zl[3], int hf, const float4* src,
+template <int MU, int S, int PAIRS, typename T>
+__device__ __forceinline__ void hop(CP zu[3], CP zl[3], int hf, const T* src,
                                     const float2* __restrict__ u, float hw) {
   float2 L[9];
   load_link(u, (reinterpret_cast<uintptr_t>(u) & 15) == 0, L);
@@ -278,8 +309,8 @@ constexpr int kSPC = 32;
 constexpr int kRing = 4;
 
 struct MarchArgs {
-  const float4* in;   // input s (slab)
-  float4* out;        // D s or -D s (slab)
+  const void* in;     // input s (slab, storage type of the pass)
+  void* out;          // D s or -D s (slab)
   const float2* U;    // links [V][4][3][3]
   const float2* C;    // clover [V][2][6][6] or nullptr
   double* part;       // [m'][npatch][4]
@@ -297,13 +328,16 @@ constexpr int march_threads() {
   return 2 * kSPC * PAIRS;
 }
 
-template <int PAIRS, int MODE>
+template <int PAIRS, int MODE, typename T>
 __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchArgs a) {
   constexpr int NC = 2 * kSPC * PAIRS;
-  constexpr int SS = 12 * PAIRS;  // ring site stride (float4): a row is a copy of the slab row
+  constexpr int SS = 12 * PAIRS;  // ring site stride (elements): a row is a copy of the slab row
   constexpr int NW = NC / 32;
-  constexpr uint32_t kSiteBytes = 12 * PAIRS * sizeof(float4);
-  extern __shared__ __align__(128) float4 ring[];  // [kRing][kSPC][SS]
+  constexpr uint32_t kSiteBytes = 12 * PAIRS * sizeof(T);
+  extern __shared__ __align__(128) unsigned char ring_raw[];
+  T* ring = reinterpret_cast<T*>(ring_raw);  // [kRing][kSPC][SS]
+  const T* in = static_cast<const T*>(a.in);
+  T* out = static_cast<T*>(a.out);
   __shared__ __align__(8) unsigned long long bar[kRing];
   __shared__ double red[NW][PAIRS][6];
   __shared__ double pr_s[MODE == MODE_D_DOT ? NC : 1][6];  // per-lane FP64 partial sums
@@ -342,7 +376,7 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
     const uint32_t bytes = (uint32_t)nvalid * kSiteBytes;
     mbar_expect_tx(&bar[slot], bytes);
     const int x = ((r + Lt) % Lt) * a.Vs + p0;
-    bulk_g2s(ring + slot * kSPC * SS, a.in + slab_index(q, a.V, x, 0, PAIRS, 0), bytes, &bar[slot]);
+    bulk_g2s(ring + slot * kSPC * SS, in + slab_index(q, a.V, x, 0, PAIRS, 0), bytes, &bar[slot]);
   };
   auto wait_row = [&](int r) -> bool {
     return mbar_wait(&bar[(r + 1) & 3], (uint32_t)(((r + 1) >> 2) & 1));
@@ -375,12 +409,12 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
       // lanes of a site beyond the lattice compute on site p0 and discard it
       const int xyzc = valid ? xyz : p0;
       const int sl = xyzc - p0;
-      const float4* ring_t = ring + ((t + 1) & 3) * kSPC * SS;
-      const float4* ring_f = ring + ((t + 2) & 3) * kSPC * SS;
-      const float4* ring_b = ring + (t & 3) * kSPC * SS;
+      const T* ring_t = ring + ((t + 1) & 3) * kSPC * SS;
+      const T* ring_f = ring + ((t + 2) & 3) * kSPC * SS;
+      const T* ring_b = ring + (t & 3) * kSPC * SS;
       const int x = t * a.Vs + xyzc;
       const int tb = (t - 1 + Lt) % Lt;
-      const float4* cen = ring_t + sl * SS + p;
+      const T* cen = ring_t + sl * SS + p;
       CP zu[3], zl[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -407,22 +441,22 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
         const int f = valid ? nf[mu] : p0, b = valid ? nb[mu] : p0;
         const int lf = f - p0, lb = b - p0;
         const bool rf = lf >= 0 && lf < kSPC && f < a.Vs, rb = lb >= 0 && lb < kSPC && b < a.Vs;
-        const float4* pf = rf ? ring_t + lf * SS + p : a.in + slab_index(q, a.V, tV + f, 0, PAIRS, p);
-        const float4* pb = rb ? ring_t + lb * SS + p : a.in + slab_index(q, a.V, tV + b, 0, PAIRS, p);
+        const T* pf = rf ? ring_t + lf * SS + p : in + slab_index(q, a.V, tV + f, 0, PAIRS, p);
+        const T* pb = rb ? ring_t + lb * SS + p : in + slab_index(q, a.V, tV + b, 0, PAIRS, p);
         const float2* ub = a.U + (tV + b) * 36 + mu * 9;
         if (mu == 0) {
-          hop<0, +1, PAIRS>(zu, zl, hf, pf, Ux, a.hw[0]);
-          hop<0, -1, PAIRS>(zu, zl, hf, pb, ub, a.hw[0]);
+          hop<0, +1, PAIRS, T>(zu, zl, hf, pf, Ux, a.hw[0]);
+          hop<0, -1, PAIRS, T>(zu, zl, hf, pb, ub, a.hw[0]);
         } else if (mu == 1) {
-          hop<1, +1, PAIRS>(zu, zl, hf, pf, Ux + 9, a.hw[1]);
-          hop<1, -1, PAIRS>(zu, zl, hf, pb, ub, a.hw[1]);
+          hop<1, +1, PAIRS, T>(zu, zl, hf, pf, Ux + 9, a.hw[1]);
+          hop<1, -1, PAIRS, T>(zu, zl, hf, pb, ub, a.hw[1]);
         } else {
-          hop<2, +1, PAIRS>(zu, zl, hf, pf, Ux + 18, a.hw[2]);
-          hop<2, -1, PAIRS>(zu, zl, hf, pb, ub, a.hw[2]);
+          hop<2, +1, PAIRS, T>(zu, zl, hf, pf, Ux + 18, a.hw[2]);
+          hop<2, -1, PAIRS, T>(zu, zl, hf, pb, ub, a.hw[2]);
         }
       }
-      hop<3, +1, PAIRS>(zu, zl, hf, ring_f + sl * SS + p, Ux + 27, a.hw[3]);
-      hop<3, -1, PAIRS>(zu, zl, hf, ring_b + sl * SS + p,
+      hop<3, +1, PAIRS, T>(zu, zl, hf, ring_f + sl * SS + p, Ux + 27, a.hw[3]);
+      hop<3, -1, PAIRS, T>(zu, zl, hf, ring_b + sl * SS + p,
                         a.U + ((long)tb * a.Vs + xyzc) * 36 + 27, a.hw[3]);
       if (valid) {
         const long so = slab_index(q, a.V, x, 0, PAIRS, p);
@@ -431,7 +465,7 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
           for (int k = 0; k < 6; ++k) {
             const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
             const CP w = k < 3 ? zu[k] : zl[k - 3];
-            __stcs(a.out + so + e * PAIRS, make_float4(-w.re.x, -w.re.y, -w.im.x, -w.im.y));
+            __stcs(out + so + e * PAIRS, cp_pack<T>(cp_neg(w)));
           }
         } else {
 #pragma unroll
@@ -446,7 +480,7 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
             sim = pfma(pmul(dup(-1.f), w.im), r.re, sim);
             snn = pfma(w.re, w.re, snn);
             snn = pfma(w.im, w.im, snn);
-            __stcs(a.out + so + e * PAIRS, cp_f4(w));
+            __stcs(out + so + e * PAIRS, cp_pack<T>(w));
           }
         }
       }
@@ -512,25 +546,58 @@ __device__ __forceinline__ void slab_coords(long i, int V, int& q, int& x, int& 
   q = (int)(r / V);
 }
 
-// psi_0 (ABI layout [V][12][m'] complex) -> slab layout
-template <int PAIRS>
-__global__ void to_slab(const float4* __restrict__ src, float4* __restrict__ dst, int V, int np) {
+// Partial sums of |psi_0|^2 per right-hand side over the ABI layout
+// [V][12][m'] (mixed-precision path: psi_0 is scaled to unit RMS per vector
+// before it is stored in FP16).  CTA g covers sites [g*cs, (g+1)*cs); the
+// block has np * (256 / np) threads, so every thread keeps one pair.
+__global__ void abi_norm_partials(const float4* __restrict__ src, double* __restrict__ part,
+                                  int V, int np, int cs, int nchunk) {
+  __shared__ double red[32][2];
+  const int g = blockIdx.x;
+  const int p = threadIdx.x % np;
+  if (threadIdx.x < 32) red[threadIdx.x][0] = red[threadIdx.x][1] = 0.0;
+  __syncthreads();
+  const long x0 = (long)g * cs, x1 = min((long)V, x0 + cs);
+  const long i0 = x0 * 12 * np, i1 = x1 * 12 * np;
+  float s0 = 0.f, s1 = 0.f;
+  for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const float4 v = __ldcs(src + i);
+    s0 += v.x * v.x + v.y * v.y;
+    s1 += v.z * v.z + v.w * v.w;
+  }
+  atomicAdd(&red[p][0], (double)s0);
+  atomicAdd(&red[p][1], (double)s1);
+  __syncthreads();
+  if (threadIdx.x < np) {
+    double* q0 = part + ((long)(2 * threadIdx.x) * nchunk + g) * 4;
+    double* q1 = part + ((long)(2 * threadIdx.x + 1) * nchunk + g) * 4;
+    q0[0] = 0; q0[1] = 0; q0[2] = red[threadIdx.x][0];
+    q1[0] = 0; q1[1] = 0; q1[2] = red[threadIdx.x][1];
+  }
+}
+
+// psi_0 (ABI layout [V][12][m'] complex) -> slab layout, each vector times
+// mul * scale[i] (scale == nullptr: no scaling)
+template <int PAIRS, typename T>
+__global__ void to_slab(const float4* __restrict__ src, T* __restrict__ dst,
+                        const float* __restrict__ scale, float mul, int V, int np) {
   const long n = (long)V * 12 * np;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x) {
     int q, x, e, p;
     slab_coords<PAIRS>(i, V, q, x, e, p);
-    const float4 v = __ldcs(src + ((long)x * 12 + e) * np + q * PAIRS + p);
-    __stcs(dst + i, make_float4(v.x, v.z, v.y, v.w));
+    const int gp = q * PAIRS + p;
+    const float4 v = __ldcs(src + ((long)x * 12 + e) * np + gp);
+    const float s0 = scale ? mul * scale[2 * gp] : 1.f, s1 = scale ? mul * scale[2 * gp + 1] : 1.f;
+    __stcs(dst + i, cp_pack<T>(CP{make_float2(v.x * s0, v.z * s1), make_float2(v.y * s0, v.w * s1)}));
   }
 }
 
 // MR update between two dslash passes: r <- r - a w (r_{t+1}),
-// psi <- psi + a r_t.  One float4 (a pair of right-hand sides) per thread.
-template <int PAIRS>
-__global__ void mr_update(float4* __restrict__ r, const float4* __restrict__ w,
-                          float4* __restrict__ psi, const float2* __restrict__ alpha, int V,
-                          int np) {
+// psi <- psi + a r_t.  One element (a pair of right-hand sides) per thread.
+template <int PAIRS, typename T>
+__global__ void mr_update(T* __restrict__ r, const T* __restrict__ w, T* __restrict__ psi,
+                          const float2* __restrict__ alpha, int V, int np) {
   const long n = (long)V * 12 * np;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x) {
@@ -539,27 +606,30 @@ __global__ void mr_update(float4* __restrict__ r, const float4* __restrict__ w,
     const int gp = q * PAIRS + p;
     const float2 a0 = alpha[2 * gp], a1 = alpha[2 * gp + 1];
     const float2 ar = make_float2(a0.x, a1.x), ai = make_float2(a0.y, a1.y);
-    const float4 rv = __ldcs(r + i), wv = __ldcs(w + i), pv = __ldcs(psi + i);
-    // a w and a r per right-hand side
-    const float2 wr = make_float2(wv.x, wv.y), wi = make_float2(wv.z, wv.w);
-    const float2 rr = make_float2(rv.x, rv.y), ri = make_float2(rv.z, rv.w);
-    const float awr0 = ar.x * wr.x - ai.x * wi.x, awr1 = ar.y * wr.y - ai.y * wi.y;
-    const float awi0 = ar.x * wi.x + ai.x * wr.x, awi1 = ar.y * wi.y + ai.y * wr.y;
-    const float arr0 = ar.x * rr.x - ai.x * ri.x, arr1 = ar.y * rr.y - ai.y * ri.y;
-    const float ari0 = ar.x * ri.x + ai.x * rr.x, ari1 = ar.y * ri.y + ai.y * rr.y;
-    __stcs(r + i, make_float4(rv.x - awr0, rv.y - awr1, rv.z - awi0, rv.w - awi1));
-    __stcs(psi + i, make_float4(pv.x + arr0, pv.y + arr1, pv.z + ari0, pv.w + ari1));
+    const CP rv = cp_unpack(__ldcs(r + i)), wv = cp_unpack(__ldcs(w + i));
+    const CP pv = cp_unpack(__ldcs(psi + i));
+    CP rn, pn;
+    // r - a w and psi + a r, per right-hand side (ar, ai = Re a, Im a of the pair)
+    rn.re = make_float2(rv.re.x - (ar.x * wv.re.x - ai.x * wv.im.x),
+                        rv.re.y - (ar.y * wv.re.y - ai.y * wv.im.y));
+    rn.im = make_float2(rv.im.x - (ar.x * wv.im.x + ai.x * wv.re.x),
+                        rv.im.y - (ar.y * wv.im.y + ai.y * wv.re.y));
+    pn.re = make_float2(pv.re.x + (ar.x * rv.re.x - ai.x * rv.im.x),
+                        pv.re.y + (ar.y * rv.re.y - ai.y * rv.im.y));
+    pn.im = make_float2(pv.im.x + (ar.x * rv.im.x + ai.x * rv.re.x),
+                        pv.im.y + (ar.y * rv.im.y + ai.y * rv.re.y));
+    __stcs(r + i, cp_pack<T>(rn));
+    __stcs(psi + i, cp_pack<T>(pn));
   }
 }
 
 // psi_N = psi_{N-1} + a r_{N-1} in place, partial |psi_N|^2 per right-hand side.
 // Streaming: CTA (slab q, chunk g) covers the contiguous sites
-// [g*cs, (g+1)*cs) of slab q; thread i handles float4s i, i + 256, ... of that
+// [g*cs, (g+1)*cs) of slab q; thread i handles elements i, i + 256, ... of that
 // range, all of one pair (256 is a multiple of P).  Partials go to
 // part[(rhs * nchunk + g) * 4 + 2].
-template <int PAIRS>
-__global__ void __launch_bounds__(256) last_update(const float4* __restrict__ r,
-                                                   float4* __restrict__ psi,
+template <int PAIRS, typename T>
+__global__ void __launch_bounds__(256) last_update(const T* __restrict__ r, T* __restrict__ psi,
                                                    const float2* __restrict__ alpha,
                                                    double* __restrict__ part, int V, int cs,
                                                    int nchunk) {
@@ -573,15 +643,16 @@ __global__ void __launch_bounds__(256) last_update(const float4* __restrict__ r,
   const long i0 = slab_index(q, V, (int)x0, 0, PAIRS, 0), i1 = slab_index(q, V, (int)x1, 0, PAIRS, 0);
   float s0 = 0.f, s1 = 0.f;
   for (long i = i0 + threadIdx.x; i < i1; i += 256) {
-    const float4 rc = __ldcs(r + i);
-    const float4 pc = __ldcs(psi + i);
-    const float4 pn = make_float4(pc.x + a0.x * rc.x - a0.y * rc.z,
-                                  pc.y + a1.x * rc.y - a1.y * rc.w,
-                                  pc.z + a0.x * rc.z + a0.y * rc.x,
-                                  pc.w + a1.x * rc.w + a1.y * rc.y);
-    s0 += pn.x * pn.x + pn.z * pn.z;
-    s1 += pn.y * pn.y + pn.w * pn.w;
-    __stcs(psi + i, pn);
+    const CP rc = cp_unpack(__ldcs(r + i));
+    const CP pc = cp_unpack(__ldcs(psi + i));
+    CP pn;
+    pn.re = make_float2(pc.re.x + a0.x * rc.re.x - a0.y * rc.im.x,
+                        pc.re.y + a1.x * rc.re.y - a1.y * rc.im.y);
+    pn.im = make_float2(pc.im.x + a0.x * rc.im.x + a0.y * rc.re.x,
+                        pc.im.y + a1.x * rc.im.y + a1.y * rc.re.y);
+    s0 += pn.re.x * pn.re.x + pn.im.x * pn.im.x;
+    s1 += pn.re.y * pn.re.y + pn.im.y * pn.im.y;
+    __stcs(psi + i, cp_pack<T>(pn));
   }
   double n0 = s0, n1 = s1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -633,8 +704,8 @@ __global__ void fill_kernel(float* __restrict__ v, int n, float x) {
 }
 
 // psi (ABI layout) = scale * psi_slab
-template <int PAIRS>
-__global__ void scale_to_abi(const float4* __restrict__ src, float4* __restrict__ dst,
+template <int PAIRS, typename T>
+__global__ void scale_to_abi(const T* __restrict__ src, float4* __restrict__ dst,
                              const float* __restrict__ scale, int V, int np) {
   const long n = (long)V * 12 * np;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
@@ -642,9 +713,10 @@ __global__ void scale_to_abi(const float4* __restrict__ src, float4* __restrict_
     int q, x, e, p;
     slab_coords<PAIRS>(i, V, q, x, e, p);
     const int gp = q * PAIRS + p;
-    const float4 v = __ldcs(src + i);
+    const CP v = cp_unpack(__ldcs(src + i));
     const float s0 = scale[2 * gp], s1 = scale[2 * gp + 1];
-    __stcs(dst + ((long)x * 12 + e) * np + gp, make_float4(v.x * s0, v.z * s0, v.y * s1, v.w * s1));
+    __stcs(dst + ((long)x * 12 + e) * np + gp,
+           make_float4(v.re.x * s0, v.im.x * s0, v.re.y * s1, v.im.y * s1));
   }
 }
 
@@ -775,19 +847,18 @@ __global__ void clover_kernel(int L0, int L1, int L2, int L3, float csw,
     for (int i = 0; i < 36; ++i) out[al * 36 + i] = acc[al][i];
 }
 
-template <int PAIRS, int MODE>
+template <int PAIRS, int MODE, typename T>
 cudaError_t run_march(const MarchArgs& a, int nsl, cudaStream_t s) {
   static const char* names[2] = {"mr_neg_dslash", "mr_dslash_dot"};
-  constexpr int SS = 12 * PAIRS;
-  const size_t smem = sizeof(float4) * (size_t)kRing * kSPC * SS;
-  static bool attr = false;  // (SS as in the kernel)
+  const size_t smem = sizeof(T) * (size_t)kRing * kSPC * 12 * PAIRS;
+  static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(march_kernel<PAIRS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    cudaFuncSetAttribute(march_kernel<PAIRS, MODE, T>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   TimedScope ts(names[MODE], s);
-  march_kernel<PAIRS, MODE><<<nsl * a.npatch, march_threads<PAIRS>(), smem, s>>>(a);
+  march_kernel<PAIRS, MODE, T><<<nsl * a.npatch, march_threads<PAIRS>(), smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -798,12 +869,14 @@ int* status_word() {
 }
 
 // common part of the smoother and the operator apply: the slab copy of the
-// input (into ps) and the march arguments
-template <int PAIRS>
+// input (into ps; in FP16 storage each vector is first scaled to unit RMS,
+// which neither the normalised smoother output nor the linear operator
+// notices once the scale is undone) and the march arguments
+template <int PAIRS, typename T>
 cudaError_t march_setup(const Geom& g, const float2* U, const float2* C, const float2* in,
-                        char* ws, MarchArgs& a, cudaStream_t s) {
+                        char* ws, MarchArgs& a, bool unit_rms, cudaStream_t s) {
   const SmoothWs lay = smooth_ws_layout(g);
-  float4* ps = reinterpret_cast<float4*>(ws + lay.ps);
+  T* ps = reinterpret_cast<T*>(ws + lay.ps);
   a = MarchArgs{};
   a.U = U;
   a.C = C;
@@ -819,25 +892,41 @@ cudaError_t march_setup(const Geom& g, const float2* U, const float2* C, const f
   a.np = g.m / 2;
   a.npatch = (a.Vs + kSPC - 1) / kSPC;
   a.diag = g.diag;
+  const float* scl = nullptr;
+  float mul = 1.f;
+  if (unit_rms) {
+    float2* alpha = reinterpret_cast<float2*>(ws + lay.alpha);
+    float* scale = reinterpret_cast<float*>(ws + lay.scale);
+    const int G = a.npatch, cs = (a.V + G - 1) / G;
+    TimedScope ts("mr_input_norm", s);
+    abi_norm_partials<<<G, a.np * (256 / a.np), 0, s>>>(reinterpret_cast<const float4*>(in),
+                                                       a.part, a.V, a.np, cs, G);
+    finish_reduction<<<(g.m + 63) / 64, 64, 0, s>>>(a.part, G, g.m, 1, alpha, scale);
+    scl = scale;
+    mul = (float)sqrt(12.0 * (double)g.V);
+  }
   {
     TimedScope ts("mr_to_slab", s);
-    to_slab<PAIRS><<<4096, 256, 0, s>>>(reinterpret_cast<const float4*>(in), ps, a.V, a.np);
+    to_slab<PAIRS, T><<<4096, 256, 0, s>>>(reinterpret_cast<const float4*>(in), ps, scl, mul,
+                                           a.V, a.np);
   }
   return cudaGetLastError();
 }
 
-template <int PAIRS>
+template <int PAIRS, typename T>
 cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const float2* psi0,
                           float2* psi, char* ws, cudaStream_t s) {
   const SmoothWs lay = smooth_ws_layout(g);
-  float4* r = reinterpret_cast<float4*>(ws + lay.ra);
-  float4* w = reinterpret_cast<float4*>(ws + lay.wa);
-  float4* ps = reinterpret_cast<float4*>(ws + lay.ps);
+  T* r = reinterpret_cast<T*>(ws + lay.ra);
+  T* w = reinterpret_cast<T*>(ws + lay.wa);
+  T* ps = reinterpret_cast<T*>(ws + lay.ps);
   double* part = reinterpret_cast<double*>(ws + lay.part);
   float2* alpha = reinterpret_cast<float2*>(ws + lay.alpha);
   float* scale = reinterpret_cast<float*>(ws + lay.scale);
   MarchArgs a;
-  cudaError_t e = march_setup<PAIRS>(g, U, C, psi0, ws, a, s);
+  // MR is invariant under a per-vector scale of psi_0 and the output is
+  // normalised, so the FP16 path may start from unit-RMS vectors
+  cudaError_t e = march_setup<PAIRS, T>(g, U, C, psi0, ws, a, sizeof(T) < sizeof(float4), s);
   if (e != cudaSuccess) return e;
   const int nsl = a.np / PAIRS;
   const int G = a.npatch;  // partial sums per right-hand side
@@ -850,56 +939,60 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
   // r_0 = -D psi_0
   a.in = ps;
   a.out = r;
-  if ((e = run_march<PAIRS, MODE_NEG_D>(a, nsl, s)) != cudaSuccess) return e;
+  if ((e = run_march<PAIRS, MODE_NEG_D, T>(a, nsl, s)) != cudaSuccess) return e;
   // w_0 = D r_0 -> a_0
   a.in = r;
   a.out = w;
-  if ((e = run_march<PAIRS, MODE_D_DOT>(a, nsl, s)) != cudaSuccess) return e;
+  if ((e = run_march<PAIRS, MODE_D_DOT, T>(a, nsl, s)) != cudaSuccess) return e;
   reduce(0);
   for (int t = 1; t < g.niter; ++t) {
     // r_t = r_{t-1} - a w_{t-1}, psi_t = psi_{t-1} + a r_{t-1}; w_t = D r_t -> a_t
     {
       TimedScope ts("mr_update", s);
-      mr_update<PAIRS><<<4096, 256, 0, s>>>(r, w, ps, alpha, a.V, a.np);
+      mr_update<PAIRS, T><<<4096, 256, 0, s>>>(r, w, ps, alpha, a.V, a.np);
     }
-    if ((e = run_march<PAIRS, MODE_D_DOT>(a, nsl, s)) != cudaSuccess) return e;
+    if ((e = run_march<PAIRS, MODE_D_DOT, T>(a, nsl, s)) != cudaSuccess) return e;
     reduce(0);
   }
-  // psi_N = psi_{N-1} + a_{N-1} r_{N-1}, partial |psi_N|^2
-  // |psi_N|^2 partials over npatch chunks of the slab (the partial-sum array
-  // holds npatch entries per right-hand side)
+  // psi_N = psi_{N-1} + a_{N-1} r_{N-1}; |psi_N|^2 partials over npatch
+  // chunks of the slab (the partial-sum array holds npatch entries per
+  // right-hand side)
   {
     const int cs = (a.V + G - 1) / G;
     TimedScope ts("mr_last_update", s);
-    last_update<PAIRS><<<nsl * G, 256, 0, s>>>(r, ps, alpha, part, a.V, cs, G);
+    last_update<PAIRS, T><<<nsl * G, 256, 0, s>>>(r, ps, alpha, part, a.V, cs, G);
   }
   reduce(1);
   {
     TimedScope ts("mr_scale", s);
-    scale_to_abi<PAIRS><<<2048, 256, 0, s>>>(ps, reinterpret_cast<float4*>(psi), scale, a.V, a.np);
+    scale_to_abi<PAIRS, T><<<2048, 256, 0, s>>>(ps, reinterpret_cast<float4*>(psi), scale, a.V,
+                                                a.np);
   }
   return cudaGetLastError();
 }
 
-template <int PAIRS>
+// out = D in: the input is copied to the slab as it is (no scaling, so FP16
+// storage needs |in| within the FP16 range)
+template <int PAIRS, typename T>
 cudaError_t dirac_impl(const Geom& g, const float2* U, const float2* C, const float2* in,
                        float2* out, char* ws, cudaStream_t s) {
   const SmoothWs lay = smooth_ws_layout(g);
-  float4* r = reinterpret_cast<float4*>(ws + lay.ra);
-  float4* ps = reinterpret_cast<float4*>(ws + lay.ps);
+  T* r = reinterpret_cast<T*>(ws + lay.ra);
+  T* ps = reinterpret_cast<T*>(ws + lay.ps);
   float* scale = reinterpret_cast<float*>(ws + lay.scale);
   MarchArgs a;
-  cudaError_t e = march_setup<PAIRS>(g, U, C, in, ws, a, s);
+  cudaError_t e = march_setup<PAIRS, T>(g, U, C, in, ws, a, false, s);
   if (e != cudaSuccess) return e;
   a.in = ps;
   a.out = r;
-  if ((e = run_march<PAIRS, MODE_NEG_D>(a, a.np / PAIRS, s)) != cudaSuccess) return e;
+  if ((e = run_march<PAIRS, MODE_NEG_D, T>(a, a.np / PAIRS, s)) != cudaSuccess) return e;
   {
     TimedScope ts("fill", s);
     fill_kernel<<<1, 64, 0, s>>>(scale, g.m, -1.0f);
   }
   TimedScope ts("mr_scale", s);
-  scale_to_abi<PAIRS><<<2048, 256, 0, s>>>(r, reinterpret_cast<float4*>(out), scale, a.V, a.np);
+  scale_to_abi<PAIRS, T><<<2048, 256, 0, s>>>(r, reinterpret_cast<float4*>(out), scale, a.V,
+                                              a.np);
   return cudaGetLastError();
 }
 
@@ -915,14 +1008,22 @@ cudaError_t launch_clover(const Geom& g, double csw, const float2* U, float2* C,
 
 cudaError_t launch_dirac(const Geom& g, const float2* U, const float2* C, const float2* in,
                          float2* out, char* ws, cudaStream_t s) {
-  if (g.m % 8 == 0) return dirac_impl<4>(g, U, C, in, out, ws, s);
-  return dirac_impl<2>(g, U, C, in, out, ws, s);
+  if (g.prec == MG_PREC_MIXED) {
+    if (g.m % 8 == 0) return dirac_impl<4, uint2>(g, U, C, in, out, ws, s);
+    return dirac_impl<2, uint2>(g, U, C, in, out, ws, s);
+  }
+  if (g.m % 8 == 0) return dirac_impl<4, float4>(g, U, C, in, out, ws, s);
+  return dirac_impl<2, float4>(g, U, C, in, out, ws, s);
 }
 
 cudaError_t launch_smoother(const Geom& g, const float2* U, const float2* C,
                             const float2* psi0, float2* psi, char* ws, cudaStream_t s) {
-  if (g.m % 8 == 0) return smoother_impl<4>(g, U, C, psi0, psi, ws, s);
-  return smoother_impl<2>(g, U, C, psi0, psi, ws, s);
+  if (g.prec == MG_PREC_MIXED) {
+    if (g.m % 8 == 0) return smoother_impl<4, uint2>(g, U, C, psi0, psi, ws, s);
+    return smoother_impl<2, uint2>(g, U, C, psi0, psi, ws, s);
+  }
+  if (g.m % 8 == 0) return smoother_impl<4, float4>(g, U, C, psi0, psi, ws, s);
+  return smoother_impl<2, float4>(g, U, C, psi0, psi, ws, s);
 }
 
 cudaError_t read_device_status(int* out, cudaStream_t s) {

@@ -52,18 +52,6 @@ WORKLOADS = {
 _POOL = 16
 
 
-def _gauge(dims, eps, seed):
-    """G.gauge_field drawn in chunks on host threads (the same numbers)."""
-    V = G.volume(dims)
-    n = 4 * V
-    step = -(-n // _POOL)
-    parts = [(lo, min(n, lo + step)) for lo in range(0, n, step)]
-    with cf.ThreadPoolExecutor(_POOL) as ex:
-        out = list(ex.map(lambda r: G.random_su3(seed, G.STREAM_GAUGE, r[1] - r[0], eps,
-                                                 start=r[0]), parts))
-    return np.concatenate(out).reshape(V, 4, 3, 3)
-
-
 def _psi0_device(dims, m, seed):
     """psi0(dims, m, seed) as complex64 on the device, drawn in site chunks."""
     V = G.volume(dims)
@@ -104,7 +92,7 @@ def _run(name):
     if name in _runs:
         return _runs[name]
     dims, block, eps, csw, xi, m0, m, k, N, gs, ps, cols, blocks = WORKLOADS[name]
-    U = G.round_to_c64(_gauge(dims, eps, gs))
+    U = G.round_to_c64(G.gauge_field(dims, eps, gs, threads=_POOL))
     C = G.round_to_c64(O.clover(dims, U, csw)) if csw else None
     prob = mg.Problem(dims=dims, block=block, m0=m0, n_vec=m, k=k, mr_iters=N, csw=csw, xi=xi)
     Ud = torch.from_numpy(U.astype(np.complex64)).cuda()

@@ -22,3 +22,8 @@ def test_random_su3_chunks_match_gauge_field():
     parts = [G.random_su3(seed, G.STREAM_GAUGE, b - a, eps, start=a)
              for a, b in ((0, 37), (37, 100), (100, n))]
     assert np.allclose(np.concatenate(parts).reshape(U.shape), U, rtol=0, atol=1e-15)
+
+
+def test_threaded_gauge_field_matches():
+    d, eps, seed = [8, 8, 8, 8], 0.25, 3
+    assert np.array_equal(G.gauge_field(d, eps, seed, threads=4), G.gauge_field(d, eps, seed))
