@@ -266,3 +266,73 @@ def _galerkin_identity(c, P, X, Y, nprobe=4, tol=1e-6):
         lhs = prolong(dims, block, P, O.coarse_apply(cd, X, Y, rz[..., None])[..., 0])
         rhs = prolong(dims, block, P, restrict(dims, block, P, D(prolong(dims, block, P, rz))))
         assert np.linalg.norm(lhs - rhs) <= tol * normD * np.linalg.norm(z)
+
+
+# ---------------------------------------------------------------------------
+# Mixed-precision path (MG_PREC_MIXED): the smoother's fields are stored in
+# FP16 (unit roundoff u16 = 2^-11 = 4.9e-4) with FP32 arithmetic; truncation
+# and coarsening as the FP32 path.  Tolerances:
+#   * operator: input and output rounded to FP16 once each: <= 4 u16 = 2e-3
+#     relative per vector;
+#   * smoother: the MR trajectory amplifies storage rounding (the FP32 path
+#     shows the same factor, ~50x its unit roundoff): <= 100 u16 = 5e-2
+#     relative per vector;
+#   * end to end: retained singular values <= 1e-2 relative, the 16 lowest
+#     |eigenvalues| of sigma_3 D_c <= 2e-2 relative, and the quality of the
+#     coarse space (their mean) within 1% of the FP64 oracle's.
+# ---------------------------------------------------------------------------
+U16 = 2.0 ** -11
+MIXED_CASES = ["8^4 clover m'=48 k=24", "8^3x16 aniso m'=64 k=24"]
+
+
+def _mixed(c):
+    p = c["prob"]
+    return mg.Problem(dims=p.dims, block=p.block, m0=p.m0, n_vec=p.n_vec, k=p.k,
+                      mr_iters=p.mr_iters, csw=p.csw, xi=p.xi, precision=mg.MG_PREC_MIXED)
+
+
+@pytest.mark.parametrize("name", MIXED_CASES)
+def test_mixed_dirac_apply(name):
+    c = _case(name)
+    p = _mixed(c)
+    U, C = _dev(c)
+    vin = to_dev(c["p0"])
+    out = torch.empty_like(vin)
+    mg.mg_apply_dirac(p, U, C, vin, out, mg.workspace(p, mg.MG_CALL_SMOOTH))
+    mg.mg_sync_status()
+    ref = O.apply_D(c["dims"], c["m0"], c["xi"], c["U"], c["C"], c["p0"])
+    got = to_host(out)
+    err = np.linalg.norm((got - ref).reshape(-1, c["m"]), axis=0) / \
+        np.linalg.norm(ref.reshape(-1, c["m"]), axis=0)
+    assert err.max() <= 4 * U16, err.max()
+    # FP16 storage halves the smoother workspace
+    assert mg.mg_workspace_size(p, mg.MG_CALL_SMOOTH) < \
+        0.6 * mg.mg_workspace_size(c["prob"], mg.MG_CALL_SMOOTH)
+
+
+@pytest.mark.parametrize("name", MIXED_CASES)
+def test_mixed_smoother_and_end_to_end(name):
+    c = _case(name)
+    p = _mixed(c)
+    k = c["k"]
+    U, C = _dev(c)
+    # a per-vector scale of the starts changes nothing (MR is scale invariant
+    # and the output is normalised); large scales would overflow unscaled FP16
+    p0 = c["p0"] * np.where(np.arange(c["m"]) % 2 == 0, 1.0e5, 1.0e-5)
+    lv = mg.Level.allocate(p, U, C, to_dev(p0))
+    lv.run()
+    mg.mg_sync_status()
+    got = to_host(lv.psi)
+    assert np.all(np.isfinite(got))
+    err = np.linalg.norm((got - c["psi"]).reshape(-1, c["m"]), axis=0)
+    assert err.max() <= 100 * U16, err.max()
+    assert np.all(lv.flags.cpu().numpy() == 0)
+    Ur, sr = O.chiral_truncate(c["dims"], c["block"], c["psi"], k)
+    np.testing.assert_allclose(lv.sigma.cpu().numpy(), sr[..., :k], rtol=1e-2)
+    Po = O.prolongator(c["dims"], c["block"], Ur)
+    Xo, Yo = O.coarsen(c["dims"], c["block"], c["m0"], c["xi"], c["U"], c["C"], Po)
+    cd = O.coarse_dims(c["dims"], c["block"])
+    lo = np.sort(np.abs(_lowest_sigma3(cd, Xo, Yo, k)))
+    lg = np.sort(np.abs(_lowest_sigma3(cd, to_host(lv.X), to_host(lv.Y), k)))
+    assert np.max(np.abs(lg - lo) / lo) <= 2e-2
+    assert abs(lg.mean() - lo.mean()) <= 1e-2 * lo.mean()
