@@ -482,6 +482,70 @@ def accuracy_check(w):
     return out
 
 
+def batch_measure(args):
+    """The 24-hierarchy batch (mg_inputs.batch_workload, FP32 path): one CUDA
+    graph launch per batch (levels fanned out over tuned streams) against the
+    same 24 levels built one after the other with the single calls."""
+    import numpy as np
+    import torch
+
+    import mg_inputs as G
+    from paper_2502_03091_gb300 import mg
+
+    with open(os.path.join(ROOT, "tests", "golden", "m0.json")) as fh:
+        wl = json.load(fh)["workloads"]
+    m0s = {v["eps"]: v["m0"] for k, v in wl.items() if k.startswith("Wilson eps=")}
+    levels, sites = [], 0
+    for h in G.batch_workload(30, m0s):
+        p = mg.Problem(dims=h["dims"], block=h["block"], m0=h["m0"], n_vec=h["m"], k=h["k"],
+                       mr_iters=h["N"])
+        U = torch.from_numpy(G.gauge_field(h["dims"], h["eps"], h["gauge_seed"], threads=16)
+                             .astype(np.complex64)).cuda()
+        gen = torch.Generator(device="cuda").manual_seed(h["psi_seed"])
+        shape = mg.shape_psi(p)
+        p0 = torch.complex(torch.randn(shape, device="cuda", generator=gen),
+                           torch.randn(shape, device="cuda", generator=gen))
+        levels.append(mg.Level.allocate(p, U, None, p0))
+        sites += p.volume
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    batch = mg.Batch(levels, n_streams=0, stream=stream)
+    create_s = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_batch = timed(lambda: batch.launch(stream))
+    mg.mg_sync_status(stream)
+
+    def solo():
+        for lv in levels:
+            lv.run(stream)
+
+    ms_solo = timed(solo)
+    out = {"config": "24 hierarchies: 8 each of 8^4, 12^3x24, 16^3x32; m' in {32,48,64}, "
+                     "k in {16,24}, aggregates 2^4 or 4^4, eps in [0.15,0.35] (batch seed 30), "
+                     "20 MR iterations, FP32 path",
+           "ms_per_batch": ms_batch, "levels_per_s": 24e3 / ms_batch,
+           "sites_per_s": sites * 1e3 / ms_batch, "n_streams": batch.n_streams,
+           "ms_one_after_another": ms_solo, "create_s": create_s,
+           "tuned_slab_pairs": sorted({(tuple(lv.prob.dims), lv.prob.n_vec,
+                                        mg.mg_tuned_pairs(lv.prob)) for lv in levels})}
+    batch.close()
+    del levels
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, w):
     import numpy as np
     import torch
@@ -553,6 +617,8 @@ def run_ours(args, w):
             "blk_flags_nonzero": q["flags"]}
     if world == 1 and not args.no_accuracy and len(precs) == 2:
         out["accuracy"] = accuracy_check(w)
+    if world == 1 and not args.no_batch:
+        out["batch"] = batch_measure(args)
     print(json.dumps(out), flush=True)
     rep.close()
 
@@ -581,6 +647,8 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "fp32", "mixed"],
                     help="both: the mixed path is the headline value, the FP32 plain path "
                          "is reported beside it")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 24-hierarchy batched-setup measurement")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the lowest-16 eigenvalue check against the oracle")
     args = ap.parse_args()

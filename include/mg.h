@@ -83,7 +83,8 @@ typedef enum {
 typedef enum {
   MG_PREC_FP32 = 0,  /* complex64 storage, FP32 arithmetic; FP64 for the small
                         Cholesky / R-factor eigen problems */
-  MG_PREC_MIXED = 1  /* reserved: FP16 smoother storage, BF16 contractions */
+  MG_PREC_MIXED = 1  /* FP16 storage of the smoother's fields (FP32 arithmetic);
+                        truncation and coarsening as MG_PREC_FP32 */
 } mg_precision;
 
 typedef struct {
@@ -207,6 +208,55 @@ typedef struct {
 
 mg_status mg_timing_enable(int on);
 int mg_timing_read(mg_timing_entry* out, int max);
+
+/* ------------------------------------------------------------------------
+ * Batched setup (not in the paper: many independent levels, e.g. hierarchies
+ * of lattices of uneven volume, built together).  One descriptor per level
+ * holds that level's problem and arrays exactly as the single calls take them
+ * (ws_smooth / ws_trunc: mg_workspace_size(prob, MG_CALL_SMOOTH / _TRUNCATE)
+ * bytes; the arrays of different levels must not overlap).
+ * mg_batch_create validates the descriptors, tunes the smoother's slab width
+ * once per distinct shape by timing both variants on the level's own buffers
+ * (it runs the smoother, so psi and ws_smooth are overwritten), and captures
+ * every level's four calls (smoother, truncation, prolongator, coarsening;
+ * no coarse test vectors) into one CUDA graph that forks over n_streams
+ * streams from the launching stream and joins back; n_streams <= 0 tunes the
+ * stream count (1, 2, 4, 8) as well.  It synchronises `stream`.
+ * mg_batch_launch enqueues the whole batch on `stream` (one graph launch);
+ * the descriptors' arrays must stay valid while the batch exists.
+ * mg_batch_destroy releases the graph.  Errors: MG_ERR_INVALID for a bad
+ * descriptor (mg_last_error() names the level), MG_ERR_CUDA otherwise.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  mg_problem prob;
+  const void* U;
+  const void* C;        /* NULL for pure Wilson */
+  const void* psi0;
+  void* psi;
+  void* Uk;
+  double* sigma;
+  int32_t* blk_flags;
+  void* P;
+  void* X;
+  void* Y;
+  void* ws_smooth;
+  size_t ws_smooth_bytes;
+  void* ws_trunc;
+  size_t ws_trunc_bytes;
+} mg_level_desc;
+
+typedef struct mg_batch mg_batch;
+
+mg_status mg_batch_create(const mg_level_desc* levels, int n, int n_streams, void* stream,
+                          mg_batch** out);
+mg_status mg_batch_launch(mg_batch* batch, void* stream);
+/* Number of streams the batch's graph forks over (0 for NULL). */
+int mg_batch_streams(const mg_batch* batch);
+void mg_batch_destroy(mg_batch* batch);
+/* Slab width (pairs of right-hand sides per CTA, 2 or 4) the smoother uses for
+ * this problem's shape: the tuned value if a batch tuned it, else the default;
+ * -1 for an invalid problem. */
+int mg_tuned_pairs(const mg_problem* prob);
 
 /* Device status of the work enqueued so far on `stream` (not in the paper;
  * the failure-detection side of the library).  Waits for the stream, then

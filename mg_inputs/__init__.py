@@ -149,11 +149,20 @@ def gauge_transform(dims, seed: int, eps: float = 1.0) -> np.ndarray:
     return random_su3(seed, STREAM_GAUGE_TRANSFORM, volume(dims), eps)
 
 
-def psi0(dims, m: int, seed: int, stream: int = STREAM_PSI0) -> np.ndarray:
-    """m complex Gaussian vectors, layout [V][4][3][m]; re and im are N(0,1)."""
-    n = volume(dims) * 12 * m
+def psi0(dims, m: int, seed: int, stream: int = STREAM_PSI0, threads: int = 1) -> np.ndarray:
+    """m complex Gaussian vectors, layout [V][4][3][m]; re and im are N(0,1).
+    threads > 1 draws site chunks on host threads (the same numbers)."""
+    V = volume(dims)
+    if threads > 1 and V >= 4096:
+        import concurrent.futures as cf
+        step = -(-V // threads)
+        parts = [(lo, min(V, lo + step)) for lo in range(0, V, step)]
+        with cf.ThreadPoolExecutor(threads) as ex:
+            out = list(ex.map(lambda r: psi0_sites(dims, m, seed, r[0], r[1], stream), parts))
+        return np.concatenate(out)
+    n = V * 12 * m
     g = normals(seed, stream, 0, 2 * n)
-    return (g[0::2] + 1j * g[1::2]).reshape(volume(dims), 4, 3, m)
+    return (g[0::2] + 1j * g[1::2]).reshape(V, 4, 3, m)
 
 
 def psi0_sites(dims, m: int, seed: int, lo: int, hi: int,
@@ -191,3 +200,26 @@ def coarse_vectors(n_coarse: int, two_k: int, nrhs: int, seed: int) -> np.ndarra
 def round_to_c64(a: np.ndarray) -> np.ndarray:
     """Round complex128 values to complex64 and back, so both sides see the same numbers."""
     return np.asarray(a, dtype=np.complex64).astype(np.complex128)
+
+
+def batch_workload(seed: int = 30, m0_table=None):
+    """The 24-hierarchy batch: 8 each of 8^4, 12^3x24 and 16^3x32, with m' drawn
+    from {32, 48, 64}, k from {16, 24}, aggregates 2^4 or 4^4 and the gauge
+    spread eps uniform in [0.15, 0.35], all from the batch seed (stream MISC,
+    four uniforms per hierarchy).  Hierarchy i uses gauge and start seed
+    300 + i.  m0 (if a table {eps: m0} is given) is the entry of the nearest
+    tabulated eps; 20 smoother iterations.  Returns a list of dicts."""
+    vols = [[8, 8, 8, 8]] * 8 + [[12, 12, 12, 24]] * 8 + [[16, 16, 16, 32]] * 8
+    u = uniforms(seed, STREAM_MISC, 0, 4 * len(vols)).reshape(len(vols), 4)
+    out = []
+    for i, d in enumerate(vols):
+        m = (32, 48, 64)[min(2, int(u[i, 0] * 3))]
+        k = (16, 24)[min(1, int(u[i, 1] * 2))]
+        b = 2 if u[i, 2] < 0.5 else 4
+        eps = 0.15 + 0.2 * u[i, 3]
+        m0 = None
+        if m0_table:
+            m0 = m0_table[min(m0_table, key=lambda e: abs(e - eps))]
+        out.append(dict(dims=list(d), block=[b] * 4, m=m, k=k, eps=float(eps), m0=m0, N=20,
+                        gauge_seed=300 + i, psi_seed=300 + i))
+    return out

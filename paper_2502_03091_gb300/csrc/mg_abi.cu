@@ -29,6 +29,8 @@ mg_status cuda_status(cudaError_t e, const char* where) {
   return fail(MG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+}  // namespace
+
 // Validate the problem and fill the geometry.
 mg_status make_geom(const mg_problem* p, Geom* g) {
   if (!p) return fail(MG_ERR_INVALID, "problem is NULL");
@@ -77,8 +79,6 @@ mg_status make_geom(const mg_problem* p, Geom* g) {
   g->diag = (float)(p->m0 + wsum);
   return MG_OK;
 }
-
-}  // namespace
 
 SmoothWs smooth_ws_layout(const Geom& g) {
   SmoothWs w{};
@@ -149,7 +149,7 @@ cudaEvent_t pool_get(TimingState& t) {
 
 int timing_begin(const char* name, cudaStream_t s) {
   TimingState& t = timing();
-  if (!t.on.load(std::memory_order_relaxed)) return -1;
+  if (!t.on.load(std::memory_order_relaxed) || timing_suspended()) return -1;
   std::lock_guard<std::mutex> g(t.mu);
   int kind = -1;
   for (size_t i = 0; i < t.kinds.size(); ++i)

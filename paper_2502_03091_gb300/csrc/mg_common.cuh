@@ -49,6 +49,15 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Sets the message mg_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 
+// Tuned slab width of the smoother passes for g's shape (0: not tuned), and
+// whether the calling thread is capturing a batch graph (no timing events).
+int tuned_pairs(const Geom& g);
+void set_tuned_pairs(const Geom& g, int pairs);
+bool timing_suspended();
+
+// Validates a problem and fills the derived geometry (mg_abi.cu).
+mg_status make_geom(const mg_problem* p, Geom* g);
+
 // ---------------------------------------------------------------------------
 // optional per-kernel timing (mg_timing_enable): a scope records a CUDA event
 // pair around the launches it encloses on stream s

@@ -550,13 +550,11 @@ __device__ __forceinline__ void slab_coords(long i, int V, int& q, int& x, int& 
 // [V][12][m'] (mixed-precision path: psi_0 is scaled to unit RMS per vector
 // before it is stored in FP16).  CTA g covers sites [g*cs, (g+1)*cs); the
 // block has np * (256 / np) threads, so every thread keeps one pair.
-__global__ void abi_norm_partials(const float4* __restrict__ src, double* __restrict__ part,
-                                  int V, int np, int cs, int nchunk) {
-  __shared__ double red[32][2];
+__global__ void __launch_bounds__(256) abi_norm_partials(const float4* __restrict__ src,
+                                                         double* __restrict__ part, int V, int np,
+                                                         int cs, int nchunk) {
+  __shared__ float red[256][2];
   const int g = blockIdx.x;
-  const int p = threadIdx.x % np;
-  if (threadIdx.x < 32) red[threadIdx.x][0] = red[threadIdx.x][1] = 0.0;
-  __syncthreads();
   const long x0 = (long)g * cs, x1 = min((long)V, x0 + cs);
   const long i0 = x0 * 12 * np, i1 = x1 * 12 * np;
   float s0 = 0.f, s1 = 0.f;
@@ -565,14 +563,20 @@ __global__ void abi_norm_partials(const float4* __restrict__ src, double* __rest
     s0 += v.x * v.x + v.y * v.y;
     s1 += v.z * v.z + v.w * v.w;
   }
-  atomicAdd(&red[p][0], (double)s0);
-  atomicAdd(&red[p][1], (double)s1);
+  red[threadIdx.x][0] = s0;
+  red[threadIdx.x][1] = s1;
   __syncthreads();
-  if (threadIdx.x < np) {
+  // fixed summation order (deterministic): thread p adds threads p, p + np, ...
+  if ((int)threadIdx.x < np) {
+    double t0 = 0, t1 = 0;
+    for (int j = threadIdx.x; j < (int)blockDim.x; j += np) {
+      t0 += (double)red[j][0];
+      t1 += (double)red[j][1];
+    }
     double* q0 = part + ((long)(2 * threadIdx.x) * nchunk + g) * 4;
     double* q1 = part + ((long)(2 * threadIdx.x + 1) * nchunk + g) * 4;
-    q0[0] = 0; q0[1] = 0; q0[2] = red[threadIdx.x][0];
-    q1[0] = 0; q1[1] = 0; q1[2] = red[threadIdx.x][1];
+    q0[0] = 0; q0[1] = 0; q0[2] = t0;
+    q1[0] = 0; q1[1] = 0; q1[2] = t1;
   }
 }
 
@@ -1006,23 +1010,27 @@ cudaError_t launch_clover(const Geom& g, double csw, const float2* U, float2* C,
   return cudaGetLastError();
 }
 
+// slab width: 4 pairs of right-hand sides per CTA when m' allows it, unless a
+// batch tuned this shape to 2
+static bool wide_slab(const Geom& g) { return g.m % 8 == 0 && tuned_pairs(g) != 2; }
+
 cudaError_t launch_dirac(const Geom& g, const float2* U, const float2* C, const float2* in,
                          float2* out, char* ws, cudaStream_t s) {
   if (g.prec == MG_PREC_MIXED) {
-    if (g.m % 8 == 0) return dirac_impl<4, uint2>(g, U, C, in, out, ws, s);
+    if (wide_slab(g)) return dirac_impl<4, uint2>(g, U, C, in, out, ws, s);
     return dirac_impl<2, uint2>(g, U, C, in, out, ws, s);
   }
-  if (g.m % 8 == 0) return dirac_impl<4, float4>(g, U, C, in, out, ws, s);
+  if (wide_slab(g)) return dirac_impl<4, float4>(g, U, C, in, out, ws, s);
   return dirac_impl<2, float4>(g, U, C, in, out, ws, s);
 }
 
 cudaError_t launch_smoother(const Geom& g, const float2* U, const float2* C,
                             const float2* psi0, float2* psi, char* ws, cudaStream_t s) {
   if (g.prec == MG_PREC_MIXED) {
-    if (g.m % 8 == 0) return smoother_impl<4, uint2>(g, U, C, psi0, psi, ws, s);
+    if (wide_slab(g)) return smoother_impl<4, uint2>(g, U, C, psi0, psi, ws, s);
     return smoother_impl<2, uint2>(g, U, C, psi0, psi, ws, s);
   }
-  if (g.m % 8 == 0) return smoother_impl<4, float4>(g, U, C, psi0, psi, ws, s);
+  if (wide_slab(g)) return smoother_impl<4, float4>(g, U, C, psi0, psi, ws, s);
   return smoother_impl<2, float4>(g, U, C, psi0, psi, ws, s);
 }
 

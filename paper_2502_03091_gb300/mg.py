@@ -28,7 +28,8 @@ MG_CALL_SMOOTH, MG_CALL_TRUNCATE, MG_CALL_COARSEN = 0, 1, 2
 EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_apply_dirac", "mg_smooth_testvecs", "mg_chiral_truncate",
            "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply", "mg_chiral_truncate_static",
            "mg_timing_enable",
-           "mg_timing_read", "mg_sync_status", "mg_last_error", "mg_version")
+           "mg_timing_read", "mg_batch_create", "mg_batch_launch", "mg_batch_streams",
+           "mg_batch_destroy", "mg_tuned_pairs", "mg_sync_status", "mg_last_error", "mg_version")
 
 
 class MgError(RuntimeError):
@@ -46,6 +47,15 @@ class _Problem(ctypes.Structure):
                 ("m0", ctypes.c_double), ("csw", ctypes.c_double), ("xi", ctypes.c_double),
                 ("n_vec", ctypes.c_int32), ("k", ctypes.c_int32), ("mr_iters", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class _LevelDesc(ctypes.Structure):
+    _fields_ = [("prob", _Problem), ("U", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("psi0", ctypes.c_void_p), ("psi", ctypes.c_void_p), ("Uk", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("blk_flags", ctypes.c_void_p),
+                ("P", ctypes.c_void_p), ("X", ctypes.c_void_p), ("Y", ctypes.c_void_p),
+                ("ws_smooth", ctypes.c_void_p), ("ws_smooth_bytes", ctypes.c_size_t),
+                ("ws_trunc", ctypes.c_void_p), ("ws_trunc_bytes", ctypes.c_size_t)]
 
 
 @dataclass
@@ -125,6 +135,17 @@ def library(path: str = LIB_PATH):
     lib.mg_timing_enable.restype = ctypes.c_int
     lib.mg_timing_read.argtypes = [ctypes.POINTER(_TimingEntry), ctypes.c_int]
     lib.mg_timing_read.restype = ctypes.c_int
+    lib.mg_batch_create.argtypes = [ctypes.POINTER(_LevelDesc), ctypes.c_int, ctypes.c_int, P,
+                                    ctypes.POINTER(ctypes.c_void_p)]
+    lib.mg_batch_create.restype = ctypes.c_int
+    lib.mg_batch_launch.argtypes = [P, P]
+    lib.mg_batch_launch.restype = ctypes.c_int
+    lib.mg_batch_streams.argtypes = [P]
+    lib.mg_batch_streams.restype = ctypes.c_int
+    lib.mg_batch_destroy.argtypes = [P]
+    lib.mg_batch_destroy.restype = None
+    lib.mg_tuned_pairs.argtypes = [Pp]
+    lib.mg_tuned_pairs.restype = ctypes.c_int
     lib.mg_sync_status.argtypes = [P]
     lib.mg_sync_status.restype = ctypes.c_int
     lib.mg_last_error.restype = ctypes.c_char_p
@@ -383,3 +404,47 @@ class Level:
                            self.ws_trunc, stream)
         mg_build_prolongator(p, self.Uk, self.P, stream)
         mg_coarsen(p, self.U, self.C, self.P, self.X, self.Y, None, stream)
+
+
+class Batch:
+    """mg_batch_create / mg_batch_launch / mg_batch_destroy over a list of
+    allocated Levels (every level's arrays must stay alive with the batch)."""
+
+    def __init__(self, levels, n_streams: int = 0, stream=None):
+        self.levels = list(levels)
+        descs = (_LevelDesc * len(self.levels))()
+        for d, lv in zip(descs, self.levels):
+            d.prob = lv.prob.c()
+            d.U, d.C, d.psi0 = _ptr(lv.U), _ptr(lv.C), _ptr(lv.psi0)
+            d.psi, d.Uk, d.sigma = _ptr(lv.psi), _ptr(lv.Uk), _ptr(lv.sigma)
+            d.blk_flags, d.P, d.X, d.Y = _ptr(lv.flags), _ptr(lv.P), _ptr(lv.X), _ptr(lv.Y)
+            d.ws_smooth, d.ws_smooth_bytes = _ptr(lv.ws_smooth), lv.ws_smooth.numel()
+            d.ws_trunc, d.ws_trunc_bytes = _ptr(lv.ws_trunc), lv.ws_trunc.numel()
+        self._descs = descs
+        h = ctypes.c_void_p()
+        _check(library().mg_batch_create(descs, len(self.levels), int(n_streams),
+                                          _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def n_streams(self) -> int:
+        return int(library().mg_batch_streams(self._h))
+
+    def launch(self, stream=None):
+        _check(library().mg_batch_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            library().mg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def mg_tuned_pairs(prob: Problem) -> int:
+    pc = prob.c()
+    return int(library().mg_tuned_pairs(ctypes.byref(pc)))

@@ -27,3 +27,20 @@ def test_random_su3_chunks_match_gauge_field():
 def test_threaded_gauge_field_matches():
     d, eps, seed = [8, 8, 8, 8], 0.25, 3
     assert np.array_equal(G.gauge_field(d, eps, seed, threads=4), G.gauge_field(d, eps, seed))
+
+
+def test_threaded_psi0_matches():
+    d, m, seed = [8, 8, 8, 8], 8, 4
+    assert np.array_equal(G.psi0(d, m, seed, threads=3), G.psi0(d, m, seed))
+
+
+def test_batch_workload_draw():
+    w = G.batch_workload(30)
+    assert len(w) == 24
+    assert [h["dims"] for h in w] == [[8] * 4] * 8 + [[12, 12, 12, 24]] * 8 + [[16, 16, 16, 32]] * 8
+    for h in w:
+        assert h["m"] in (32, 48, 64) and h["k"] in (16, 24) and h["block"] in ([2] * 4, [4] * 4)
+        assert 0.15 <= h["eps"] <= 0.35
+        assert 6 * int(np.prod(h["block"])) >= h["m"] and h["k"] <= h["m"]
+    assert w == G.batch_workload(30)          # a pure function of the seed
+    assert w != G.batch_workload(31)
