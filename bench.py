@@ -102,6 +102,7 @@ def kernel_work(w, prec="fp32"):
         "mr_last_update": ("hbm", 3 * spinor, "B"),
         "mr_scale": ("hbm", spinor + abi, "B"),
         "trunc_gram": ("hbm", abi, "B"),               # read every block once
+        "trunc_gram_tc": ("hbm", abi, "B"),            # the same on BF16 tensor cores
         "trunc_gram_q1": ("fp32", nbc * (8 * K * m * m + 4 * K * m * m), "flop"),
         "trunc_form_uk": ("fp32", nbc * (4 * K * m * m + 8 * K * m * k), "flop"),
         "trunc_chol64": ("fp64", nbc * (8 * m ** 3 / 3 + 8 * m ** 3 / 3), "flop"),

@@ -84,7 +84,8 @@ typedef enum {
   MG_PREC_FP32 = 0,  /* complex64 storage, FP32 arithmetic; FP64 for the small
                         Cholesky / R-factor eigen problems */
   MG_PREC_MIXED = 1  /* FP16 storage of the smoother's fields (FP32 arithmetic);
-                        truncation and coarsening as MG_PREC_FP32 */
+                        first Gram of the truncation on BF16 tensor cores (FP32
+                        accumulation); the rest as MG_PREC_FP32 */
 } mg_precision;
 
 typedef struct {
@@ -263,8 +264,9 @@ int mg_tuned_pairs(const mg_problem* prob);
  * reads and clears the library's device status word.  Returns MG_OK, or
  * MG_ERR_TIMEOUT if a smoother or operator pass since the previous call gave
  * up waiting (after a bounded number of polls, about a second) for input it
- * had staged into shared memory: that pass stopped early and its outputs are
- * not valid.  MG_ERR_CUDA if the stream reports a CUDA error.  The status
+ * had staged into shared memory, or a tensor-core Gram of the mixed-precision
+ * truncation gave up waiting for its matrix multiplies: that kernel stopped
+ * early and its outputs are not valid.  MG_ERR_CUDA if the stream reports a CUDA error.  The status
  * word is shared by every stream of the process on the current device. */
 mg_status mg_sync_status(void* stream);
 

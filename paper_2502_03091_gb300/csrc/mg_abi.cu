@@ -225,6 +225,10 @@ mg_status mg_sync_status(void* stream) {
     return fail(MG_ERR_TIMEOUT,
                 "a smoother or operator pass gave up waiting for its staged input; its "
                 "outputs are not valid");
+  if (st & 2)
+    return fail(MG_ERR_TIMEOUT,
+                "a tensor-core Gram gave up waiting for its matrix multiplies; the "
+                "truncation's outputs are not valid");
   return MG_OK;
 }
 

@@ -84,8 +84,16 @@ cudaError_t launch_smoother(const Geom& g, const float2* U, const float2* C,
                             const float2* psi0, float2* psi, char* ws, cudaStream_t s);
 
 // Synchronises s, then reads and clears the device status word (bit 0: a
-// smoother pass gave up waiting for its staged input).
+// smoother pass gave up waiting for its staged input; bit 1: a tensor-core
+// contraction gave up waiting for its MMAs).
 cudaError_t read_device_status(int* out, cudaStream_t s);
+// Device address of that word (nullptr on a CUDA error).
+int* device_status_word();
+
+// Tensor-core (tcgen05, BF16) first Gram of the truncation, mixed precision.
+bool gram_tc_supported(const Geom& g);
+cudaError_t launch_gram_tc(const Geom& g, const float2* psi, double2* G, int* status,
+                           cudaStream_t s);
 
 cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double* sigma,
                             float2* coarse_tv, int32_t* flags, char* ws, cudaStream_t s);

@@ -27,7 +27,8 @@
 namespace mg {
 namespace {
 
-// device status word: bit 0 = a pass gave up waiting for its staged input
+// device status word: bit 0 = a smoother pass gave up waiting for its staged
+// input; bit 1 = a tensor-core Gram gave up waiting for its MMAs
 __device__ int g_status;
 
 // ---------------------------------------------------------------------------
@@ -866,11 +867,6 @@ cudaError_t run_march(const MarchArgs& a, int nsl, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int* status_word() {
-  void* p = nullptr;
-  if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
-  return static_cast<int*>(p);
-}
 
 // common part of the smoother and the operator apply: the slab copy of the
 // input (into ps; in FP16 storage each vector is first scaled to unit RMS,
@@ -885,7 +881,7 @@ cudaError_t march_setup(const Geom& g, const float2* U, const float2* C, const f
   a.U = U;
   a.C = C;
   a.part = reinterpret_cast<double*>(ws + lay.part);
-  a.status = status_word();
+  a.status = device_status_word();
   if (!a.status) return cudaErrorInvalidSymbol;
   for (int i = 0; i < 4; ++i) {
     a.L[i] = g.L[i];
@@ -1032,6 +1028,12 @@ cudaError_t launch_smoother(const Geom& g, const float2* U, const float2* C,
   }
   if (wide_slab(g)) return smoother_impl<4, float4>(g, U, C, psi0, psi, ws, s);
   return smoother_impl<2, float4>(g, U, C, psi0, psi, ws, s);
+}
+
+int* device_status_word() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+  return static_cast<int*>(p);
 }
 
 cudaError_t read_device_status(int* out, cudaStream_t s) {

@@ -783,7 +783,14 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
     cudaFuncSetAttribute(form_uk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
     attr_done = true;
   }
-  {
+  if (g.prec == MG_PREC_MIXED && gram_tc_supported(g)) {
+    // mixed precision: G1 on the tensor cores in BF16 (CholeskyQR2's second
+    // pass, below, is FP32 and restores the orthonormality)
+    int* st = device_status_word();
+    if (!st) return cudaErrorInvalidSymbol;
+    cudaError_t e = launch_gram_tc(g, psi, G, st, s);
+    if (e != cudaSuccess) return e;
+  } else {
     TimedScope ts("trunc_gram", s);
     gram_kernel<false><<<nbc, kThreads, sm_gram0, s>>>(psi, nullptr, G, bg);
   }
