@@ -280,22 +280,98 @@ __global__ void __launch_bounds__(kThreads, 2) chol_stage1(const double2* __rest
 }
 
 // ---------------------------------------------------------------------------
-// FP64 top-k eigenpairs of a Hermitian m x m matrix in shared memory:
-// Householder tridiagonalisation, Sturm multisection, inverse iteration.
+// Double-float numbers: value = hi + lo, two FP32 with |lo| <= ulp(hi) / 2.
+// Sums by Knuth's TwoSum and products by the FMA form of Dekker's TwoProduct
+// (error-free transformations; cf. Hida, Li, Bailey, "Algorithms for quad-double
+// precision", 2001) give about 2^-44 relative accuracy on the FP32 pipe, which
+// on this GPU issues 64 times the FP64 rate.  The _rn intrinsics keep the
+// compiler from fusing the operations the transformations rely on.
+// ---------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+struct dz {  // complex double-float
+  df re, im;
+};
+
+__device__ __forceinline__ df df_from(double x) {
+  const float h = (float)x;
+  return df{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  const df t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ dz dz_from(double2 v) { return dz{df_from(v.x), df_from(v.y)}; }
+__device__ __forceinline__ double2 dz_to(dz a) { return make_double2(df_to(a.re), df_to(a.im)); }
+__device__ __forceinline__ dz dz_zero() { return dz{df{0.f, 0.f}, df{0.f, 0.f}}; }
+__device__ __forceinline__ dz dz_add(dz a, dz b) { return dz{df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dz dz_sub(dz a, dz b) { return dz{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ dz dz_mul(dz a, dz b) {  // a b
+  return dz{df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)),
+            df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ dz dz_mulc(dz a, dz b) {  // conj(a) b
+  return dz{df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)),
+            df_sub(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ dz dz_conj(dz a) { return dz{a.re, df_neg(a.im)}; }
+__device__ __forceinline__ dz dz_scale(dz a, df s) { return dz{df_mul(a.re, s), df_mul(a.im, s)}; }
+__device__ __forceinline__ df df_shfl_xor(df a, int o) {
+  return df{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ dz dz_warp_sum(dz a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a.re = df_add(a.re, df_shfl_xor(a.re, o));
+    a.im = df_add(a.im, df_shfl_xor(a.im, o));
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// Top-k eigenpairs of a Hermitian m x m matrix in shared memory: Householder
+// tridiagonalisation (double-float), Sturm multisection (FP32), inverse
+// iteration and Rayleigh quotients (FP64).
 // ---------------------------------------------------------------------------
 
-// Hs: Hermitian (full, leading dimension ld).  On exit: d[0..m), e[0..m-1)
-// complex subdiagonal T[j+1][j], reflector j stored in column j of Hs rows
-// j+1.. (u_j), tau[j].  H = Q T Q^dag with Q = H_0 H_1 ... H_{m-3},
-// H_j = I - tau_j u_j u_j^dag.
-__device__ void tridiagonalise(double2* Hs, int m, int ld, double* d, double2* e, double* tau,
-                               double2* uv, double2* pv, double* red) {
+// Hs: Hermitian (full, leading dimension ld), double-float.  On exit:
+// d[0..m), e[0..m-1) complex subdiagonal T[j+1][j], reflector j stored in
+// column j of Hs rows j+1.. (u_j), tau[j].  H = Q T Q^dag with
+// Q = H_0 H_1 ... H_{m-3}, H_j = I - tau_j u_j u_j^dag.  The scalars of each
+// reflector (norms, tau, beta) are formed in FP64.
+__device__ void tridiagonalise(dz* Hs, int m, int ld, double* d, double2* e, double* tau,
+                               dz* uv, dz* pv, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j + 2 < m; ++j) {
     const int n = m - j - 1;  // length of x = H[j+1.., j]
     double tail = 0;
-    for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) tail += zabs2(Hs[i * ld + j]);
+    for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) tail += zabs2(dz_to(Hs[i * ld + j]));
     tail = block_sum(tail, red);
-    const double2 x0 = Hs[(j + 1) * ld + j];
+    const double2 x0 = dz_to(Hs[(j + 1) * ld + j]);
     double t = 0.0;
     double2 beta = x0;
     if (tail > 0.0) {
@@ -305,35 +381,35 @@ __device__ void tridiagonalise(double2* Hs, int m, int ld, double* d, double2* e
       beta = zscale(ph, -nx);
       const double2 u0 = zsub(x0, beta);
       t = 2.0 / (zabs2(u0) + tail);
+      const df tdf = df_from(t);
       // u (contiguous copy) and its column copy for the back-transform
-      for (int a = threadIdx.x; a < n; a += blockDim.x) uv[a] = a == 0 ? u0 : Hs[(j + 1 + a) * ld + j];
+      for (int a = threadIdx.x; a < n; a += blockDim.x)
+        uv[a] = a == 0 ? dz_from(u0) : Hs[(j + 1 + a) * ld + j];
       __syncthreads();
-      if (threadIdx.x == 0) Hs[(j + 1) * ld + j] = u0;
+      if (threadIdx.x == 0) Hs[(j + 1) * ld + j] = dz_from(u0);
       // p = t A u over the trailing block A = H[j+1.., j+1..], one warp per row
-      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
       for (int a = w; a < n; a += nw) {
-        double2 sacc = make_double2(0.0, 0.0);
-        const double2* row = Hs + (j + 1 + a) * ld + j + 1;
-        for (int b = lane; b < n; b += 32) sacc = zadd(sacc, zmul(row[b], uv[b]));
-        for (int o = 16; o > 0; o >>= 1) {
-          sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
-          sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
-        }
-        if (lane == 0) pv[a] = zscale(sacc, t);
+        dz sacc = dz_zero();
+        const dz* row = Hs + (j + 1 + a) * ld + j + 1;
+        for (int b = lane; b < n; b += 32) sacc = dz_add(sacc, dz_mul(row[b], uv[b]));
+        sacc = dz_warp_sum(sacc);
+        if (lane == 0) pv[a] = dz_scale(sacc, tdf);
       }
       __syncthreads();
       // K = t/2 u^dag p (real); w = p - K u (stored over p)
       double kr = 0;
-      for (int a = threadIdx.x; a < n; a += blockDim.x) kr += zmulc(uv[a], pv[a]).x;
+      for (int a = threadIdx.x; a < n; a += blockDim.x) kr += zmulc(dz_to(uv[a]), dz_to(pv[a])).x;
       kr = 0.5 * t * block_sum(kr, red);
-      for (int a = threadIdx.x; a < n; a += blockDim.x) pv[a] = zsub(pv[a], zscale(uv[a], kr));
+      const df krdf = df_from(kr);
+      for (int a = threadIdx.x; a < n; a += blockDim.x)
+        pv[a] = dz_sub(pv[a], dz_scale(uv[a], krdf));
       __syncthreads();
       // A -= u w^dag + w u^dag
       for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int ra = idx / n, cb = idx % n;
-        double2 v = Hs[(j + 1 + ra) * ld + j + 1 + cb];
-        v = zsub(v, zmul(uv[ra], zconj(pv[cb])));
-        v = zsub(v, zmul(pv[ra], zconj(uv[cb])));
+        dz v = Hs[(j + 1 + ra) * ld + j + 1 + cb];
+        v = dz_sub(v, dz_mul(uv[ra], dz_conj(pv[cb])));
+        v = dz_sub(v, dz_mul(pv[ra], dz_conj(uv[cb])));
         Hs[(j + 1 + ra) * ld + j + 1 + cb] = v;
       }
     }
@@ -345,11 +421,11 @@ __device__ void tridiagonalise(double2* Hs, int m, int ld, double* d, double2* e
   }
   if (threadIdx.x == 0) {
     if (m >= 2) {
-      e[m - 2] = Hs[(m - 1) * ld + m - 2];
+      e[m - 2] = dz_to(Hs[(m - 1) * ld + m - 2]);
       tau[m - 2] = 0.0;
     }
   }
-  for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = Hs[i * ld + i].x;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = df_to(Hs[i * ld + i].re);
   __syncthreads();
 }
 
@@ -543,19 +619,25 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
     }
     __syncthreads();
   }
+  // R in double-float, in place (a dz occupies the 16 bytes of its double2)
+  dz* Mz = reinterpret_cast<dz*>(M);
+  for (int i = threadIdx.x; i < m * ld; i += blockDim.x) Mz[i] = dz_from(M[i]);
+  __syncthreads();
   // H = R R^dag (upper triangle computed, mirrored) -> global, then back into M
+  dz* Hz = reinterpret_cast<dz*>(Hb);
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
     const int i = idx / m, jj = idx % m;
     if (jj < i) continue;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int l = jj; l < m; ++l) acc = zadd(acc, zmul(M[i * ld + l], zconj(M[jj * ld + l])));
-    Hb[i * m + jj] = acc;
-    Hb[jj * m + i] = zconj(acc);
+    dz acc = dz_zero();
+    for (int l = jj; l < m; ++l) acc = dz_add(acc, dz_mul(Mz[i * ld + l], dz_conj(Mz[jj * ld + l])));
+    Hz[i * m + jj] = acc;
+    Hz[jj * m + i] = dz_conj(acc);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) M[(i / m) * ld + i % m] = Hb[i];
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) Mz[(i / m) * ld + i % m] = Hz[i];
   __syncthreads();
-  tridiagonalise(M, m, ld, d, e, tau, uv, pv, red);
+  dz* uvz = reinterpret_cast<dz*>(uv);
+  tridiagonalise(Mz, m, ld, d, e, tau, uvz, reinterpret_cast<dz*>(pv), red);
   if (threadIdx.x == 0) {
     delta[0] = make_double2(1.0, 0.0);
     for (int j = 0; j + 1 < m; ++j) {
@@ -646,31 +728,32 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
     } while (i < k && !leader[i]);
   }
   __syncthreads();
-  // back-transform: y = Q (delta .* z); reflector j copied to uv first
+  // back-transform (double-float): y = Q (delta .* z); reflector j copied to uv first
+  dz* Ukz = reinterpret_cast<dz*>(Uk);
   for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x)
-    Uk[idx] = zscale(delta[idx / k], Uk[idx].x);
+    Ukz[idx] = dz_from(zscale(delta[idx / k], Uk[idx].x));
   __syncthreads();
   {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = m - 3; j >= 0; --j) {
       if (tau[j] == 0.0) continue;
       const int n = m - j - 1;
-      for (int a = threadIdx.x; a < n; a += blockDim.x) uv[a] = M[(j + 1 + a) * ld + j];
+      const df tj = df_from(tau[j]);
+      for (int a = threadIdx.x; a < n; a += blockDim.x) uvz[a] = Mz[(j + 1 + a) * ld + j];
       __syncthreads();
       for (int i = w; i < k; i += nw) {
-        double2 sacc = make_double2(0.0, 0.0);
-        for (int a = lane; a < n; a += 32) sacc = zadd(sacc, zmulc(uv[a], Uk[(j + 1 + a) * k + i]));
-        for (int o = 16; o > 0; o >>= 1) {
-          sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
-          sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
-        }
-        sacc = zscale(sacc, tau[j]);
+        dz sacc = dz_zero();
         for (int a = lane; a < n; a += 32)
-          Uk[(j + 1 + a) * k + i] = zsub(Uk[(j + 1 + a) * k + i], zmul(sacc, uv[a]));
+          sacc = dz_add(sacc, dz_mulc(uvz[a], Ukz[(j + 1 + a) * k + i]));
+        sacc = dz_scale(dz_warp_sum(sacc), tj);
+        for (int a = lane; a < n; a += 32)
+          Ukz[(j + 1 + a) * k + i] = dz_sub(Ukz[(j + 1 + a) * k + i], dz_mul(sacc, uvz[a]));
       }
       __syncthreads();
     }
   }
+  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) Uk[idx] = dz_to(Ukz[idx]);
+  __syncthreads();
   if (threadIdx.x < k) sigma[(long)bc * k + threadIdx.x] = sqrt(fmax(lam[threadIdx.x], 0.0));
   if (ctv) {
     // Sigma_k V_k^dag = U~_k^dag R  (R from global)
