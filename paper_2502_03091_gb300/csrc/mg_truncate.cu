@@ -65,14 +65,48 @@ __device__ void load_chunk(const float2* __restrict__ psi, const BlockGeom& g, i
   }
 }
 
-// Qs[r][c] = sum_{l <= c} As[r][l] Zs[l][c]   (Zs upper triangular, m x m)
-__device__ void right_mul_upper(const float2* As, const float2* Zs, float2* Qs, int rows, int m) {
-  for (int idx = threadIdx.x; idx < rows * m; idx += blockDim.x) {
-    const int r = idx / m, c = idx % m;
-    float2 s = make_float2(0.f, 0.f);
-    for (int l = 0; l <= c; ++l) cfma(s, As[r * m + l], Zs[l * m + c]);
-    Qs[idx] = s;
+// C[r][c] = sum_l A[r][l] B[l][c] for r < rows (a multiple of TR), c < n,
+// l < kd (UPPER: B upper triangular, only l <= c is read).  Each thread
+// computes a TR x TC register tile; the B row segment of a tile is read as
+// float4 pairs when TC is even.  A is rows x lda, B is kd x ldb, C is rows x ldc.
+template <int TR, int TC, bool UPPER>
+__device__ void tile_gemm(const float2* A, int lda, const float2* B, int ldb, float2* C, int ldc,
+                          int rows, int n, int kd) {
+  const int rg = rows / TR, cg = (n + TC - 1) / TC;
+  for (int t = threadIdx.x; t < rg * cg; t += blockDim.x) {
+    const int r0 = (t / cg) * TR, c0 = (t % cg) * TC;
+    float2 acc[TR][TC];
+#pragma unroll
+    for (int i = 0; i < TR; ++i)
+#pragma unroll
+      for (int j = 0; j < TC; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    const int lmax = UPPER ? min(kd, c0 + TC) : kd;
+    for (int l = 0; l < lmax; ++l) {
+      float2 a[TR], b[TC];
+#pragma unroll
+      for (int i = 0; i < TR; ++i) a[i] = A[(r0 + i) * lda + l];
+#pragma unroll
+      for (int j = 0; j < TC; ++j) {
+        const int c = c0 + j;
+        b[j] = (c < n && (!UPPER || l <= c)) ? B[l * ldb + c] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TC; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < TR; ++i)
+#pragma unroll
+      for (int j = 0; j < TC; ++j)
+        if (c0 + j < n) C[(r0 + i) * ldc + c0 + j] = acc[i][j];
   }
+}
+
+// Qs[r][c] = sum_{l <= c} As[r][l] Zs[l][c]   (Zs upper triangular, m x m)
+__device__ __forceinline__ void right_mul_upper(const float2* As, const float2* Zs, float2* Qs,
+                                                int rows, int m) {
+  tile_gemm<3, 4, true>(As, m, Zs, m, Qs, m, rows, m, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -813,21 +847,28 @@ __global__ void __launch_bounds__(kThreads) form_uk(const float2* __restrict__ p
   const int bc = blockIdx.x;
   for (int i = threadIdx.x; i < m * m; i += blockDim.x) Zs[i] = Z1[(long)bc * m * m + i];
   for (int i = threadIdx.x; i < m * k; i += blockDim.x) Ws[i] = W2[(long)bc * m * k + i];
+  __syncthreads();
+  // U_k = (A Z1) W2 = A M with M = Z1 W2 (m x k, Z1 upper triangular), formed
+  // once per block-chirality in the Q area
+  float2* Ms = Qs;
+  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) {
+    const int i = idx / k, c = idx % k;
+    float2 sacc = make_float2(0.f, 0.f);
+    for (int l = i; l < m; ++l) cfma(sacc, Zs[i * m + l], Ws[l * k + c]);
+    Ms[idx] = sacc;
+  }
   const int nch = (g.nb + kChunkSites - 1) / kChunkSites;
   float2* out = Uk + (long)bc * 6 * g.nb * k;
+  float2* Us = Ws + m * k;  // chunk of U_k (kChunkRows x k)
   for (int ch = 0; ch < nch; ++ch) {
     __syncthreads();
     load_chunk(psi, g, bc, ch, As);
     __syncthreads();
-    right_mul_upper(As, Zs, Qs, kChunkRows, m);
+    tile_gemm<3, 2, false>(As, m, Ms, k, Us, k, kChunkRows, k, m);
     __syncthreads();
     const int rows = min(kChunkRows, 6 * (g.nb - ch * kChunkSites));
-    for (int idx = threadIdx.x; idx < rows * k; idx += blockDim.x) {
-      const int r = idx / k, c = idx % k;
-      float2 s = make_float2(0.f, 0.f);
-      for (int l = 0; l < m; ++l) cfma(s, Qs[r * m + l], Ws[l * k + c]);
-      out[(long)(ch * kChunkRows + r) * k + c] = s;
-    }
+    for (int idx = threadIdx.x; idx < rows * k; idx += blockDim.x)
+      out[(long)(ch * kChunkRows) * k + idx] = Us[idx];
   }
 }
 
@@ -856,7 +897,7 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
   const size_t sm_gram1 = sm_gram0 + sizeof(float2) * (size_t)m * m;
   const size_t sm_chol = sizeof(double2) * (size_t)m * (m + 1) + sizeof(float2) * (size_t)m * m;
   const size_t sm_svd = sizeof(double2) * ((size_t)m * (m + 1) + (size_t)m * k);
-  const size_t sm_uk = sm_gram1 + sizeof(float2) * (size_t)m * k;
+  const size_t sm_uk = sm_gram1 + sizeof(float2) * ((size_t)m * k + (size_t)kChunkRows * k);
   static bool attr_done = false;
   if (!attr_done) {
     cudaFuncSetAttribute(gram_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
