@@ -426,8 +426,13 @@ def _measure(args, w, prec, rep, U_host, psi0):
     rep.barrier()
     mg.mg_sync_status(stream)
     e2e_ms = rep.max(e0.elapsed_time(e1) / e2e_steps)
+    # singular-value decay of block 0 (the paper's diagnostic of how much of
+    # the m' vectors' span the rank-k truncation keeps)
+    sig0 = lv.sigma[0].cpu().tolist()
+    decay = {f"alpha{a}": {"sigma_1": sig0[a][0], "sigma_k": sig0[a][-1],
+                           "sigma_k_over_sigma_1": sig0[a][-1] / sig0[a][0]} for a in range(2)}
     res = dict(ms=ms, kern=kern, clocks=clocks, flags=int((flags != 0).sum()), e2e_ms=e2e_ms,
-               e2e_steps=e2e_steps, h2d=h2d, d2h=d2h)
+               e2e_steps=e2e_steps, h2d=h2d, d2h=d2h, sigma_decay=decay)
     del lv, psi0_host, X_host, Y_host, s_host, U, C
     torch.cuda.empty_cache()
     return res
@@ -624,6 +629,7 @@ def run_ours(args, w):
         "stages": stages,
         "gpu_launches": launches,
         "blk_flags_nonzero": r["flags"],
+        "sigma_decay_block0": r["sigma_decay"],
         "clocks": r["clocks"],
         "e2e": {"value": per_level(r["e2e_ms"], world), "unit": UNIT,
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],

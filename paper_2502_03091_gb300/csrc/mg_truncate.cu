@@ -2,13 +2,15 @@
 // Sec. 3 Eq. 4).  For every block Lambda_j and chirality alpha the
 // K x m' matrix A = Psi^(alpha)(Lambda_j), K = 6 |Lambda_j| (rows: site,
 // spin in chirality, colour), is factored as
-//   G1 = A^dag A                  (FP32 products, FP64 across row chunks)
+//   G1 = A^dag A                  (FP32 products, FP64 across row chunks; BF16
+//                                  tensor cores in the mixed-precision path)
 //   R1 = chol(G1)                 (FP64)
 //   Q1 = A R1^{-1}, G2 = Q1^dag Q1 (FP32, Q1 never stored)
 //   R2 = chol(G2), R = R2 R1      (FP64)          -- CholeskyQR2: A = Q R
-//   R R^dag = U~ S^2 U~^dag       (FP64 Householder tridiagonalisation,
-//                                  bisection, inverse iteration; top k only)
-//   U_k = Q1 (R2^{-1} U~_k), Sigma_k = S_k
+//   R R^dag = U~ S^2 U~^dag       (double-float Householder tridiagonalisation,
+//                                  FP32 multisection, FP64 inverse iteration and
+//                                  Rayleigh quotients; top k only)
+//   U_k = A (Z1 R2^{-1} U~_k), Sigma_k = S_k     (Z1 = R1^{-1})
 // so U_k are the k leading left singular vectors of A (A = Q R, R = U~ S V~^dag),
 // the best rank-k basis of Eq. (4).  The chiral split itself is only the
 // choice of rows: chirality 0 is spins {0,1}, chirality 1 spins {2,3}.
@@ -67,8 +69,8 @@ __device__ void load_chunk(const float2* __restrict__ psi, const BlockGeom& g, i
 
 // C[r][c] = sum_l A[r][l] B[l][c] for r < rows (a multiple of TR), c < n,
 // l < kd (UPPER: B upper triangular, only l <= c is read).  Each thread
-// computes a TR x TC register tile; the B row segment of a tile is read as
-// float4 pairs when TC is even.  A is rows x lda, B is kd x ldb, C is rows x ldc.
+// computes a TR x TC register tile (TR + TC shared-memory loads per TR * TC
+// complex multiply-adds).  A is rows x lda, B is kd x ldb, C is rows x ldc.
 template <int TR, int TC, bool UPPER>
 __device__ void tile_gemm(const float2* A, int lda, const float2* B, int ldb, float2* C, int ldc,
                           int rows, int n, int kd) {
@@ -689,23 +691,24 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
     tnorm = fmax(tnorm, r);
   }
   const double tiny = 1e-300 + 1e-15 * tnorm;
-  // multisection: kBisect threads per eigenvalue (the i-th largest)
-  if (threadIdx.x < k) {
-    lo[threadIdx.x] = -tnorm;
-    hi[threadIdx.x] = tnorm;
+  // multisection: kBisect points per eigenvalue (the ei-th largest); the
+  // k * kBisect (eigenvalue, point) pairs are spread over the block's threads
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    lo[i] = -tnorm;
+    hi[i] = tnorm;
   }
   __syncthreads();
   {
-    const int ei = threadIdx.x / kBisect, sp = threadIdx.x % kBisect;
     const float tiny32 = 1e-30f + 1e-20f * (float)tnorm;
     for (int it = 0; it < 9; ++it) {
-      if (ei < k) {
+      for (int w = threadIdx.x; w < k * kBisect; w += blockDim.x) {
+        const int ei = w / kBisect, sp = w % kBisect;
         const double l0 = lo[ei], h0 = hi[ei];
         const double x = l0 + (h0 - l0) * (double)(sp + 1) / (double)(kBisect + 1);
         cnt[ei][sp] = sturm_count32(d32, f232, m, (float)x, tiny32);
       }
       __syncthreads();
-      if (ei < k && sp == 0) {
+      for (int ei = threadIdx.x; ei < k; ei += blockDim.x) {
         const int target = m - 1 - ei;  // index among ascending eigenvalues
         const double l0 = lo[ei], h0 = hi[ei];
         double nl = l0, nh = h0;

@@ -162,6 +162,41 @@ def test_truncation(name):
                 2 * bound[j, al] * np.linalg.norm(A_o)
 
 
+@pytest.mark.parametrize("precision", [mg.MG_PREC_FP32, mg.MG_PREC_MIXED])
+def test_conventional_setup_k_equals_m(precision):
+    """k = m': no truncation, the conventional per-block orthonormalisation of
+    the chirally split vectors (Sec. 2, the paper's comparison setup).  U U^dag
+    must be the orthogonal projector onto each block-chirality's range (the
+    oracle's k = m' case, pinned on the CPU against that projector), with all
+    m' singular values, and the coarse operator must keep sigma_3-hermiticity.
+    The mixed path takes its first Gram in BF16 on the tensor cores; the
+    second, FP32 CholeskyQR pass gives the same orthonormal basis."""
+    dims, block, m = [8, 8, 8, 8], [4, 4, 4, 4], 32
+    p = mg.Problem(dims=dims, block=block, m0=-0.1, n_vec=m, k=m, mr_iters=1,
+                   precision=precision)
+    psi = G.round_to_c64(G.psi0(dims, m, 17))
+    Uk, sig, flags = _truncate({"prob": p}, psi)
+    assert np.all(flags == 0)
+    Ur, sr = O.chiral_truncate(dims, block, psi, m)
+    np.testing.assert_allclose(sig, sr[..., :m], rtol=1e-5)
+    for j in range(Uk.shape[0]):
+        for al in range(2):
+            Ug = Uk[j, al].reshape(-1, m)
+            np.testing.assert_allclose(Ug.conj().T @ Ug, np.eye(m), atol=1e-5)
+            assert projector_error(Ug, Ur[j, al].reshape(-1, m)) <= 1e-5
+    U = G.round_to_c64(G.gauge_field(dims, 0.25, 3))
+    P = torch.empty(mg.shape_P(p), dtype=torch.complex64, device="cuda")
+    X = torch.empty(mg.shape_X(p), dtype=torch.complex64, device="cuda")
+    Y = torch.empty(mg.shape_Y(p), dtype=torch.complex64, device="cuda")
+    mg.mg_build_prolongator(p, to_dev(Uk), P)
+    mg.mg_coarsen(p, to_dev(U), None, P, X, Y)
+    torch.cuda.synchronize()
+    Dc = dense_coarse(O.coarse_dims(dims, block), to_host(X), to_host(Y))
+    s3 = np.tile(np.r_[np.ones(m), -np.ones(m)], Dc.shape[0] // (2 * m))
+    H = s3[:, None] * Dc
+    assert np.linalg.norm(H - H.conj().T) <= 1e-5 * np.linalg.norm(H)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_prolongator_pack_exact(name):
     c = _case(name)
