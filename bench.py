@@ -343,9 +343,9 @@ def _roofline_table(w, prec, kern, steps):
     if os.path.exists(prof):
         with open(prof) as fh:
             pj = json.load(fh)
-        ent = pj.get(top, {})
+        ent = pj.get(prec, {}).get(top, {})
         if (ent.get("source_sha1") == _kernel_sha1() and ent.get("workload") == w["workload"]
-                and ent.get("precision", "fp32") == prec):
+                and ent.get("precision") == prec):
             traffic = ent.get("dram_bytes_per_launch")
     roofline["traffic"] = traffic
     dl, dt = kern["mr_dslash_dot"]
