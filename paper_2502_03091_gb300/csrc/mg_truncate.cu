@@ -6,7 +6,8 @@
 //                                  tensor cores in the mixed-precision path)
 //   R1 = chol(G1)                 (FP64)
 //   Q1 = A R1^{-1}, G2 = Q1^dag Q1 (FP32, Q1 never stored)
-//   R2 = chol(G2), R = R2 R1      (FP64)          -- CholeskyQR2: A = Q R
+//   R2 = chol(G2), R = R2 R1      (FP32 on the deviations from 1; R in FP64)
+//                                                 -- CholeskyQR2: A = Q R
 //   R R^dag = U~ S^2 U~^dag       (double-float Householder tridiagonalisation,
 //                                  FP32 multisection, FP64 inverse iteration and
 //                                  Rayleigh quotients; top k only)
@@ -74,22 +75,24 @@ __device__ void load_chunk(const float2* __restrict__ psi, const BlockGeom& g, i
 template <int TR, int TC, bool UPPER>
 __device__ void tile_gemm(const float2* A, int lda, const float2* B, int ldb, float2* C, int ldc,
                           int rows, int n, int kd) {
+  // thread t: rows r0 .. r0+TR-1, columns c0, c0 + cg, ..., c0 + (TC-1) cg, so
+  // that neighbouring threads read neighbouring B entries (no bank conflicts)
   const int rg = rows / TR, cg = (n + TC - 1) / TC;
   for (int t = threadIdx.x; t < rg * cg; t += blockDim.x) {
-    const int r0 = (t / cg) * TR, c0 = (t % cg) * TC;
+    const int r0 = (t / cg) * TR, c0 = t % cg;
     float2 acc[TR][TC];
 #pragma unroll
     for (int i = 0; i < TR; ++i)
 #pragma unroll
       for (int j = 0; j < TC; ++j) acc[i][j] = make_float2(0.f, 0.f);
-    const int lmax = UPPER ? min(kd, c0 + TC) : kd;
+    const int lmax = UPPER ? min(kd, min(n, c0 + (TC - 1) * cg + 1)) : kd;
     for (int l = 0; l < lmax; ++l) {
       float2 a[TR], b[TC];
 #pragma unroll
       for (int i = 0; i < TR; ++i) a[i] = A[(r0 + i) * lda + l];
 #pragma unroll
       for (int j = 0; j < TC; ++j) {
-        const int c = c0 + j;
+        const int c = c0 + j * cg;
         b[j] = (c < n && (!UPPER || l <= c)) ? B[l * ldb + c] : make_float2(0.f, 0.f);
       }
 #pragma unroll
@@ -101,7 +104,7 @@ __device__ void tile_gemm(const float2* A, int lda, const float2* B, int ldb, fl
     for (int i = 0; i < TR; ++i)
 #pragma unroll
       for (int j = 0; j < TC; ++j)
-        if (c0 + j < n) C[(r0 + i) * ldc + c0 + j] = acc[i][j];
+        if (c0 + j * cg < n) C[(r0 + i) * ldc + c0 + j * cg] = acc[i][j];
   }
 }
 
@@ -242,6 +245,61 @@ __device__ bool chol_upper(double2* Gs, int m, int ld, double tol, int* s_fail) 
   }
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x)
     if (idx / m > idx % m) Gs[(idx / m) * ld + idx % m] = make_double2(0.0, 0.0);
+  __syncthreads();
+  return *s_fail == 0;
+}
+
+// Cholesky of a Hermitian matrix close to the identity, G = 1 + E, in
+// deviations: R = 1 + F with F upper triangular.  Every update acts on the
+// small quantities only (the diagonal is kept as delta_jj = a_jj - 1 and
+// r_jj - 1 = delta_jj / (1 + sqrt(1 + delta_jj)) has no cancellation), so FP32
+// gives F to FP32 relative accuracy, i.e. R to ~1e-7 |E| absolute.  Gs (FP64,
+// leading dimension ld) holds G on entry and R (upper, 1 + F) on exit; the
+// FP32 deviations live in the first 8 bytes of each 16-byte entry meanwhile.
+// Returns false if a pivot 1 + delta_jj is not positive (it is then set to 1).
+__device__ bool chol_upper_near1(double2* Gs, int m, int ld, int* s_fail) {
+  float2* Ef = reinterpret_cast<float2*>(Gs);  // entry e at Ef[2 e]
+  if (threadIdx.x == 0) *s_fail = 0;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int i = idx / m, c = idx % m;
+    const double2 v = Gs[i * ld + c];
+    Ef[2 * (i * ld + c)] = make_float2((float)(v.x - (i == c ? 1.0 : 0.0)), (float)v.y);
+  }
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (threadIdx.x == 0) {
+      float dj = Ef[2 * (j * ld + j)].x;
+      if (!(1.0f + dj > 1e-6f)) {
+        *s_fail = 1;
+        dj = 0.f;
+      }
+      Ef[2 * (j * ld + j)] = make_float2(dj / (1.0f + sqrtf(1.0f + dj)), 0.f);
+    }
+    __syncthreads();
+    const float inv = 1.0f / (1.0f + Ef[2 * (j * ld + j)].x);
+    for (int l = j + 1 + threadIdx.x; l < m; l += blockDim.x) {
+      float2& r = Ef[2 * (j * ld + l)];
+      r = make_float2(r.x * inv, r.y * inv);
+    }
+    __syncthreads();
+    const int n = m - j - 1;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int r = j + 1 + idx / n, c = j + 1 + idx % n;
+      if (c >= r) {
+        const float2 a = Ef[2 * (j * ld + r)], b = Ef[2 * (j * ld + c)];
+        float2& e = Ef[2 * (r * ld + c)];
+        // e -= conj(a) b
+        e = make_float2(e.x - (a.x * b.x + a.y * b.y), e.y - (a.x * b.y - a.y * b.x));
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int i = idx / m, c = idx % m;
+    const float2 f = Ef[2 * (i * ld + c)];
+    Gs[i * ld + c] = c < i ? make_double2(0.0, 0.0)
+                           : make_double2((i == c ? 1.0 : 0.0) + (double)f.x, (double)f.y);
+  }
   __syncthreads();
   return *s_fail == 0;
 }
@@ -576,7 +634,10 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
   double maxd = 0;
   for (int i = 0; i < (int)(blockDim.x >> 5); ++i) maxd = fmax(maxd, red[i]);
   int32_t flag = 0;
-  if (!chol_upper(M, m, ld, 1e-13 * maxd, &s_fail)) flag |= 4;
+  // G2 = Q1^dag Q1 is the identity up to the rounding of Q1: the Cholesky of
+  // its deviation in FP32 keeps R2 - 1 to FP32 relative accuracy
+  (void)maxd;
+  if (!chol_upper_near1(M, m, ld, &s_fail)) flag |= 4;
   for (int i = threadIdx.x; i < m * m; i += blockDim.x) Gb[i] = M[(i / m) * ld + i % m];
   __syncthreads();
   // R = R2 R1 = R1 + (R2 - 1) R1.  After CholeskyQR2's first pass R2 = 1 + D
