@@ -16,6 +16,9 @@ Every function follows one passage of the paper:
   coarsen(...)               D_c = R D P with R = P^dagger (Eq. 3)
   coarse_apply(...)          D_c v on the coarse stencil
   svd(A)                     thin SVD of one block (Householder QR + one-sided Jacobi)
+
+The second level (the same steps on D_c, chirality sigma_3) is in ``level2``
+(numpy over coarse_apply and svd).
 """
 from __future__ import annotations
 
