@@ -355,7 +355,93 @@ def _roofline_table(w, prec, kern, steps):
     return stages, top, roofline, dslash
 
 
-def _measure(args, w, prec, rep, U_host, psi0):
+# the second level, built on the first level's own coarse operator D_c: the
+# paper keeps k = 32 at l = 1 (Sec. 4); m = 64 vectors, 2^4 aggregates of the
+# coarse lattice, the fine level's 20 MR iterations
+LEVEL2 = dict(block=[2, 2, 2, 2], m=64, k=32, N=20, psi_seed=22)
+
+
+def level2_work(cp):
+    """{kernel: (bound, amount, unit)} of the second level (per launch)."""
+    V, n, m, k = cp.volume, 2 * cp.nc, cp.n_vec, cp.k
+    nb = cp.block_volume
+    nbc = 2 * cp.n_blocks
+    K = cp.nc * nb
+    return {
+        # out = D_c v: 9 n x n by n x m complex products per site
+        "c_mr_apply": ("fp32", V * 9 * n * n * m * 8, "flop"),
+        "c_mr_update": ("hbm", V * n * m * 8 * 5, "B"),
+        "c_mr_scale": ("hbm", V * n * m * 8 * 2, "B"),
+        "trunc_gram_q1": ("fp32", nbc * (8 * K * m * m + 4 * K * m * m), "flop"),
+        "trunc_form_uk": ("fp32", nbc * (4 * K * m * m + 8 * K * m * k), "flop"),
+        # per term: T = M P(y) (n x 2k, depth nc) and P(x)^dag T (2k x 2k, depth nc)
+        "c_galerkin": ("fp32", V * 9 * (n * 2 * k * cp.nc + 4 * k * k * cp.nc) * 8, "flop"),
+    }
+
+
+def level2_measure(args, prob, lv, stream):
+    """Time the second level (smoother, sigma_3 truncation, prolongator,
+    Galerkin product) on the level's own D_c, resident in HBM."""
+    import torch
+
+    from paper_2502_03091_gb300 import mg
+
+    cp = mg.CoarseProblem.below(prob, LEVEL2["block"], LEVEL2["m"], LEVEL2["k"], LEVEL2["N"])
+    gen = torch.Generator(device="cuda").manual_seed(LEVEL2["psi_seed"])
+    shape = mg.shape_cvec(cp, cp.n_vec)
+    q0 = torch.complex(torch.randn(shape, device="cuda", generator=gen),
+                       torch.randn(shape, device="cuda", generator=gen))
+    lv2 = mg.CoarseLevel.allocate(cp, lv.X, lv.Y, q0)
+    for _ in range(max(1, args.warmup)):
+        lv2.run(stream)
+    mg.mg_sync_status(stream)
+    steps = max(1, args.steps)
+    mg.mg_timing_enable(True)
+    mg.mg_timing_read()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        lv2.run(stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    kern = mg.mg_timing_read()
+    mg.mg_timing_enable(False)
+    mg.mg_sync_status(stream)
+    work = level2_work(cp)
+    hbm_peak, _ = _peaks()
+    stages, top = {}, None
+    for name, (launches, tot) in kern.items():
+        per = tot / launches
+        e = {"launches_per_step": launches / steps, "ms_per_step": tot / steps}
+        if name in work:
+            bound, amount, unit = work[name]
+            if unit == "flop":
+                ach = amount / (per * 1e-3) / 1e12
+                pk = FP32_TFLOPS if bound == "fp32" else FP64_TFLOPS
+                e["roofline"] = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                                 "frac": ach / pk}
+            else:
+                ach = amount / (per * 1e-3) / 1e9
+                e["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                                 "unit": "GB/s", "frac": ach / hbm_peak}
+        stages[name] = e
+        if top is None or tot > kern[top][1]:
+            top = name
+    sig0 = lv2.sigma[0].cpu().tolist()
+    out = {"value": ms / 1e3, "unit": "s/level", "ms_per_step": ms, "steps": steps,
+           "workload": (f"second level on the first level's D_c: {'x'.join(map(str, cp.dims))} "
+                        f"coarse lattice, {2 * cp.nc} components, m={cp.n_vec}, k={cp.k}, "
+                        f"{'x'.join(map(str, cp.block))} aggregates, {cp.mr_iters} MR iterations"),
+           "dtype": "f32", "top_kernel": top, "stages": stages,
+           "gpu_launches": sum(l for l, _ in kern.values()) / steps,
+           "blk_flags_nonzero": int((lv2.flags.cpu().numpy() != 0).sum()),
+           "sigma_decay_block0": {f"alpha{a}": sig0[a][-1] / sig0[a][0] for a in range(2)}}
+    del lv2, q0
+    return out
+
+
+def _measure(args, w, prec, rep, U_host, psi0, level2=False):
     """One precision: warm-up, the device-resident timed steps (CUDA events on
     the launching stream, per-kernel event timing, clocks sampled meanwhile),
     then the end-to-end steps through the public API with host buffers."""
@@ -433,6 +519,8 @@ def _measure(args, w, prec, rep, U_host, psi0):
                            "sigma_k_over_sigma_1": sig0[a][-1] / sig0[a][0]} for a in range(2)}
     res = dict(ms=ms, kern=kern, clocks=clocks, flags=int((flags != 0).sum()), e2e_ms=e2e_ms,
                e2e_steps=e2e_steps, h2d=h2d, d2h=d2h, sigma_decay=decay)
+    if level2:
+        res["level2"] = level2_measure(args, prob, lv, stream)
     del lv, psi0_host, X_host, Y_host, s_host, U, C
     torch.cuda.empty_cache()
     return res
@@ -600,7 +688,8 @@ def run_ours(args, w):
                          torch.randn(shape, device="cuda", generator=gen))
 
     precs = ["mixed", "fp32"] if args.precision == "both" else [args.precision]
-    res = {p: _measure(args, w, p, rep, U_host, psi0) for p in precs}
+    res = {p: _measure(args, w, p, rep, U_host, psi0,
+                       level2=(p == precs[0] and not args.no_level2)) for p in precs}
     if rank != 0:
         rep.close()
         return
@@ -645,6 +734,8 @@ def run_ours(args, w):
             "dslash": ds, "stages": {n: v["ms_per_step"] for n, v in st.items()},
             "gpu_launches": sum(l for l, _ in q["kern"].values()), "clocks": q["clocks"],
             "blk_flags_nonzero": q["flags"]}
+    if "level2" in r:
+        out["level2"] = r["level2"]
     if world == 1 and not args.no_accuracy and len(precs) == 2:
         out["accuracy"] = accuracy_check(w)
     if world == 1 and not args.no_batch:
@@ -683,6 +774,8 @@ def main():
                     help="skip the setup-serving measurement (p50/p99 under Poisson load)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 24-hierarchy batched-setup measurement")
+    ap.add_argument("--no-level2", action="store_true",
+                    help="skip the second level built on the first level's D_c")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the lowest-16 eigenvalue check against the oracle")
     args = ap.parse_args()

@@ -174,6 +174,84 @@ mg_status mg_coarsen(const mg_problem* prob, const void* U, const void* C, const
 mg_status mg_coarse_apply(const mg_problem* prob, const void* X, const void* Y,
                           const void* v_in, void* v_out, int32_t nrhs, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Levels l >= 1 (Sec. 2: the hierarchy is built recursively, D_{l+1} = R D_l P,
+ * and for l > 0 the chiral split uses gamma_5^l = sigma_3).  The operator D_l
+ * is a coarse stencil (X, Y) -- the output of mg_coarsen, or of
+ * mg_coarse_coarsen one level up -- on the periodic lattice `dims` with
+ * 2*nc complex components per site; chirality alpha is the component block
+ * alpha*nc .. alpha*nc + nc - 1.  Each call repeats the fine-level call of
+ * the same name with D -> D_l and gamma_5 -> sigma_3, and follows the same
+ * conventions (caller-owned device memory, stream semantics, errors).
+ * Array layouts (complex64 unless noted; V = volume of dims, nb = |block|,
+ * nblk = V / nb, m = n_vec, k = problem.k):
+ *  X      [V][2nc][2nc]            D_l self coupling
+ *  Y      [V][8][2nc][2nc]         D_l hops (d = 0..3 to x + mu_d, 4..7 to x - mu_{d-4})
+ *  v, psi [V][2nc][nrhs or m]      vectors, right-hand sides fastest
+ *  Uk     [nblk][2][nb][nc][k]     truncated left singular vectors
+ *  sigma  [nblk][2][k]             retained singular values (double)
+ *  P      [V][2][nc][k]            prolongator; row (alpha, e) is component
+ *                                  alpha*nc + e, column (alpha, i) is coarse
+ *                                  index alpha*k + i
+ *  X2     [nblk][2k][2k]           D_{l+1} self coupling
+ *  Y2     [nblk][8][2k][2k]        D_{l+1} hops
+ * X, Y, v and psi must be 16-byte aligned (they are staged by bulk copies).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t dims[4];   /* lattice of D_l (the coarse lattice of level l - 1) */
+  int32_t block[4];  /* aggregate extents on that lattice, each divides dims[i] */
+  int32_t nc;        /* D_l has 2*nc components per site; 1 <= nc <= 32 */
+  int32_t n_vec;     /* m test vectors; 4 <= m <= 64, m % 4 == 0, nc*nb >= m */
+  int32_t k;         /* kept per chirality, 1 <= k <= min(m, 32) */
+  int32_t mr_iters;  /* smoother iterations N >= 1 */
+} mg_coarse_problem;
+
+/* Scratch bytes of mg_coarse_smooth_testvecs (MG_CALL_SMOOTH) or
+ * mg_coarse_chiral_truncate (MG_CALL_TRUNCATE); 0 for MG_CALL_COARSEN and
+ * for an invalid problem (mg_last_error() then says why). */
+size_t mg_coarse_workspace_size(const mg_coarse_problem* prob, int which);
+
+/* out = D_l v for 1 <= nrhs <= 64 right-hand sides (Sec. 2, Eq. 3: the
+ * coarse stencil applied as a nearest-neighbour operator):
+ *   out(x) = X(x) v(x) + sum_{d<4} Y_d(x) v(x + mu_d) + Y_{4+d}(x) v(x - mu_d).
+ * Only prob->dims and prob->nc are read (so the same call applies D_{l+1}
+ * with dims = the aggregated lattice and nc = k).  In: X, Y, v_in.  Out:
+ * v_out (must not alias v_in).  FP32 arithmetic. */
+mg_status mg_coarse_op_apply(const mg_coarse_problem* prob, const void* X, const void* Y,
+                             const void* v_in, void* v_out, int32_t nrhs, void* stream);
+
+/* Smoother on D_l psi_i ~ 0 (Sec. 2, Eq. 1 with D -> D_l): the minimal
+ * residual recurrence of mg_smooth_testvecs, mr_iters iterations, one step
+ * length per vector, then every vector to unit 2-norm.  In: X, Y, psi0.
+ * Out: psi (may alias psi0).  ws: mg_coarse_workspace_size(prob,
+ * MG_CALL_SMOOTH) bytes.  FP32 arithmetic, FP64 sums of the inner products. */
+mg_status mg_coarse_smooth_testvecs(const mg_coarse_problem* prob, const void* X, const void* Y,
+                                    const void* psi0, void* psi, void* ws, size_t ws_bytes,
+                                    void* stream);
+
+/* Chiral split by sigma_3 and rank-k truncation (Sec. 2 Eq. 2, Sec. 3 Eq. 4)
+ * of the nc*nb x m matrices Psi^(alpha)(Lambda_j) (rows: site, component of
+ * chirality alpha), by the kernels of mg_chiral_truncate.  In: psi.  Out:
+ * Uk, sigma, optional coarse_tv ([nblk][2][k][m], NULL to skip), blk_flags
+ * (as mg_chiral_truncate).  ws: mg_coarse_workspace_size(prob,
+ * MG_CALL_TRUNCATE) bytes. */
+mg_status mg_coarse_chiral_truncate(const mg_coarse_problem* prob, const void* psi, void* Uk,
+                                    double* sigma, void* coarse_tv, int32_t* blk_flags, void* ws,
+                                    size_t ws_bytes, void* stream);
+
+/* Prolongator of level l (Sec. 3, Eq. 5 with gamma_5 -> sigma_3):
+ * P_{alpha i j}(x) = u_i^(alpha)(x) for x in Lambda_j.  In: Uk.  Out: P. */
+mg_status mg_coarse_build_prolongator(const mg_coarse_problem* prob, const void* Uk, void* P,
+                                      void* stream);
+
+/* D_{l+1} = P^dag D_l P (Sec. 2, Eq. 3), term by term: for every site x of
+ * block j, P(x)^dag X(x) P(x) and every hop P(x)^dag Y_d(x) P(x +- mu_d) go to
+ * X2(j), except a hop from a site on the block's +mu (-mu) face in direction
+ * +mu (-mu), which goes to Y2_d(j).  Every direction is computed (no symmetry
+ * is assumed of D_l).  In: X, Y, P.  Out: X2, Y2.  FP32 arithmetic. */
+mg_status mg_coarse_coarsen(const mg_coarse_problem* prob, const void* X, const void* Y,
+                            const void* P, void* X2, void* Y2, void* stream);
+
 /* mg_chiral_truncate for callers that cannot allocate device memory (the
  * paper has no counterpart; this is a service of this library).  A host
  * application whose device memory is owned by its own pool allocator, or a

@@ -19,7 +19,10 @@ the same shapes, see Sec. 4 of the paper for the lattices they mimic):
     Hermitian H, so U is in SU(3));
   * complex Gaussian test-vector starts psi0 (the "m random initial guesses"
     of Eq. (1) of the paper);
-  * random SU(3) gauge transformations (for covariance tests).
+  * random SU(3) gauge transformations (for covariance tests);
+  * random nearest-neighbour stencils with 2 nc components per site and the
+    structure of a coarse operator (stand-ins for the operator of a level
+    l >= 1), and complex Gaussian coarse vectors.
 
 Layouts (lexicographic site index s = x + Lx*(y + Ly*(z + Lz*t))):
   U    complex128 [V][4 mu][3][3]          (U_mu(x) links x -> x + mu)
@@ -40,6 +43,7 @@ STREAM_PSI0 = 2
 STREAM_GAUGE_TRANSFORM = 3
 STREAM_COARSE_VEC = 4
 STREAM_MISC = 5
+STREAM_STENCIL = 6
 
 
 def splitmix64(x: np.ndarray) -> np.ndarray:
@@ -223,3 +227,52 @@ def batch_workload(seed: int = 30, m0_table=None):
         out.append(dict(dims=list(d), block=[b] * 4, m=m, k=k, eps=float(eps), m0=m0, N=20,
                         gauge_seed=300 + i, psi_seed=300 + i))
     return out
+
+
+def stencil_operator(cdims, nc: int, seed: int, diag: float = 3.0, hop: float = 0.3,
+                     threads: int = 1):
+    """A random nearest-neighbour operator on the periodic lattice cdims with
+    n = 2 nc components per site, in the coarse-operator layout X [V][n][n],
+    Y [V][8][n][n] (d = 0..3 hop to x + mu_d, 4..7 to x - mu_{d-4}).  It has
+    the symmetry of a coarse Wilson operator under s3 = diag(1_nc, -1_nc):
+      X = S + s3 S^dag s3,  S = Z_0 + diag 1,   Y_mu(x) = hop Z_{1+mu}(x),
+      Y_{4+mu}(x + mu) = s3 Y_mu(x)^dag s3,
+    with Z_i(x) complex Gaussian n x n matrices drawn from stream STENCIL
+    (site by site, so any chunk of sites can be drawn on its own).
+    complex128."""
+    V = volume(cdims)
+    n = 2 * nc
+    per = 5 * n * n
+
+    # one complex number per pair of normals: site x takes normals
+    # 2 x per .. 2 (x + 1) per - 1, so a chunk of sites is drawn on its own
+    def site_block(lo, hi):
+        g = normals(seed, STREAM_STENCIL, 2 * lo * per, 2 * (hi - lo) * per)
+        return (g[0::2] + 1j * g[1::2]).reshape(hi - lo, 5, n, n)
+
+    step = 256
+    chunks = [(lo, min(V, lo + step)) for lo in range(0, V, step)]
+    if threads > 1:
+        import concurrent.futures as cf
+        with cf.ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(lambda c: site_block(*c), chunks))
+    else:
+        parts = [site_block(*c) for c in chunks]
+    Z = np.concatenate(parts, axis=0)
+    s3 = np.r_[np.ones(nc), -np.ones(nc)]
+    S = Z[:, 0] + diag * np.eye(n)
+    X = S + s3[:, None] * S.conj().transpose(0, 2, 1) * s3[None, :]
+    Y = np.empty((V, 8, n, n), dtype=np.complex128)
+    s = np.arange(V)
+    c = []
+    t = s.copy()
+    for L in cdims:
+        c.append(t % L)
+        t = t // L
+    for mu in range(4):
+        Y[:, mu] = hop * Z[:, 1 + mu]
+        cf_ = [a.copy() for a in c]
+        cf_[mu] = (cf_[mu] + 1) % cdims[mu]
+        fwd = cf_[0] + cdims[0] * (cf_[1] + cdims[1] * (cf_[2] + cdims[2] * cf_[3]))
+        Y[fwd, 4 + mu] = s3[:, None] * Y[:, mu].conj().transpose(0, 2, 1) * s3[None, :]
+    return X, Y

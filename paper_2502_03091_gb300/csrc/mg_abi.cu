@@ -80,6 +80,60 @@ mg_status make_geom(const mg_problem* p, Geom* g) {
   return MG_OK;
 }
 
+// Validates a level-l (l >= 1) problem.  full = false checks only what the
+// stencil apply reads (dims, nc); full = true also the aggregation and the
+// truncation parameters and fills g as the fine-level kernels of the
+// truncation and the prolongator read it (rps = nc rows per site and
+// chirality).
+mg_status make_cgeom(const mg_coarse_problem* p, StencilGeom* sg, Geom* g, bool full) {
+  if (!p) return fail(MG_ERR_INVALID, "problem is NULL");
+  long V = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (p->dims[i] < 1) return fail(MG_ERR_SHAPE, "dims extents must be >= 1");
+    V *= p->dims[i];
+  }
+  if (V > (1L << 26)) return fail(MG_ERR_SHAPE, "coarse volume %ld too large", V);
+  if (p->nc < 1 || p->nc > 32)
+    return fail(MG_ERR_UNSUPPORTED, "nc = %d must be in [1, 32]", p->nc);
+  for (int i = 0; i < 4; ++i) sg->L[i] = p->dims[i];
+  sg->V = V;
+  sg->n = 2 * p->nc;
+  if (!full) return MG_OK;
+  int nb = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (p->block[i] < 1) return fail(MG_ERR_SHAPE, "block extents must be >= 1");
+    if (p->dims[i] % p->block[i] != 0)
+      return fail(MG_ERR_SHAPE, "block extent %d does not divide lattice extent %d (direction %d)",
+                  p->block[i], p->dims[i], i);
+    nb *= p->block[i];
+  }
+  if (p->n_vec < 4 || p->n_vec > kMaxM || p->n_vec % 4 != 0)
+    return fail(MG_ERR_UNSUPPORTED, "n_vec must be a multiple of 4 in [4, %d], got %d", kMaxM,
+                p->n_vec);
+  if (p->nc * nb < p->n_vec)
+    return fail(MG_ERR_SHAPE, "block has nc*|Lambda| = %d rows < n_vec = %d", p->nc * nb,
+                p->n_vec);
+  if (p->k < 1 || p->k > p->n_vec || p->k > kMaxK)
+    return fail(MG_ERR_SHAPE, "k = %d must be in [1, min(n_vec, %d)]", p->k, kMaxK);
+  *g = Geom{};
+  for (int i = 0; i < 4; ++i) {
+    g->L[i] = p->dims[i];
+    g->b[i] = p->block[i];
+    g->Lc[i] = p->dims[i] / p->block[i];
+  }
+  g->V = V;
+  g->nb = nb;
+  g->nblk = V / nb;
+  g->m = p->n_vec;
+  g->k = p->k;
+  g->niter = p->mr_iters;
+  g->xi = 1.0;
+  g->prec = MG_PREC_FP32;
+  g->rps = p->nc;
+  g->cps = 2 * p->nc;
+  return MG_OK;
+}
+
 SmoothWs smooth_ws_layout(const Geom& g) {
   SmoothWs w{};
   // one spinor field: complex64 or, in the mixed-precision path, two FP16 per complex
@@ -348,6 +402,118 @@ mg_status mg_coarse_apply(const mg_problem* prob, const void* X, const void* Y,
                                          static_cast<float2*>(v_out), nrhs,
                                          static_cast<cudaStream_t>(stream)),
                      "mg_coarse_apply");
+}
+
+// ---------------------------------------------------------------------------
+// levels l >= 1
+// ---------------------------------------------------------------------------
+namespace {
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+}  // namespace
+
+size_t mg_coarse_workspace_size(const mg_coarse_problem* prob, int which) {
+  StencilGeom sg;
+  Geom g;
+  if (make_cgeom(prob, &sg, &g, true) != MG_OK) return 0;
+  switch (which) {
+    case MG_CALL_SMOOTH: return stencil_smooth_ws_layout(sg, g.m).bytes;
+    case MG_CALL_TRUNCATE: return trunc_ws_layout(g).bytes;
+    case MG_CALL_COARSEN: return 0;
+    default: fail(MG_ERR_INVALID, "unknown call %d", which); return 0;
+  }
+}
+
+mg_status mg_coarse_op_apply(const mg_coarse_problem* prob, const void* X, const void* Y,
+                             const void* v_in, void* v_out, int32_t nrhs, void* stream) {
+  StencilGeom sg;
+  Geom g;
+  mg_status st = make_cgeom(prob, &sg, &g, false);
+  if (st != MG_OK) return st;
+  if (!X || !Y || !v_in || !v_out) return fail(MG_ERR_INVALID, "mg_coarse_op_apply: NULL array");
+  if (!aligned16(X) || !aligned16(Y) || !aligned16(v_in) || !aligned16(v_out))
+    return fail(MG_ERR_INVALID, "mg_coarse_op_apply: arrays must be 16-byte aligned");
+  if (nrhs < 1 || nrhs > 64) return fail(MG_ERR_INVALID, "nrhs = %d must be in [1, 64]", nrhs);
+  if (v_in == v_out) return fail(MG_ERR_INVALID, "mg_coarse_op_apply: v_out aliases v_in");
+  return cuda_status(launch_stencil_apply(sg, static_cast<const float2*>(X),
+                                          static_cast<const float2*>(Y),
+                                          static_cast<const float2*>(v_in),
+                                          static_cast<float2*>(v_out), nrhs,
+                                          static_cast<cudaStream_t>(stream)),
+                     "mg_coarse_op_apply");
+}
+
+mg_status mg_coarse_smooth_testvecs(const mg_coarse_problem* prob, const void* X, const void* Y,
+                                    const void* psi0, void* psi, void* ws, size_t ws_bytes,
+                                    void* stream) {
+  StencilGeom sg;
+  Geom g;
+  mg_status st = make_cgeom(prob, &sg, &g, true);
+  if (st != MG_OK) return st;
+  if (g.niter < 1) return fail(MG_ERR_INVALID, "mr_iters must be >= 1");
+  if (!X || !Y || !psi0 || !psi || !ws)
+    return fail(MG_ERR_INVALID, "mg_coarse_smooth_testvecs: NULL array");
+  if (!aligned16(X) || !aligned16(Y) || !aligned16(psi0) || !aligned16(psi) || !aligned16(ws))
+    return fail(MG_ERR_INVALID, "mg_coarse_smooth_testvecs: arrays must be 16-byte aligned");
+  const size_t need = stencil_smooth_ws_layout(sg, g.m).bytes;
+  if (ws_bytes < need)
+    return fail(MG_ERR_INVALID, "mg_coarse_smooth_testvecs: workspace %zu < %zu bytes", ws_bytes,
+                need);
+  return cuda_status(launch_stencil_smoother(sg, g.m, g.niter, static_cast<const float2*>(X),
+                                             static_cast<const float2*>(Y),
+                                             static_cast<const float2*>(psi0),
+                                             static_cast<float2*>(psi), static_cast<char*>(ws),
+                                             static_cast<cudaStream_t>(stream)),
+                     "mg_coarse_smooth_testvecs");
+}
+
+mg_status mg_coarse_chiral_truncate(const mg_coarse_problem* prob, const void* psi, void* Uk,
+                                    double* sigma, void* coarse_tv, int32_t* blk_flags, void* ws,
+                                    size_t ws_bytes, void* stream) {
+  StencilGeom sg;
+  Geom g;
+  mg_status st = make_cgeom(prob, &sg, &g, true);
+  if (st != MG_OK) return st;
+  if (!psi || !Uk || !sigma || !blk_flags || !ws)
+    return fail(MG_ERR_INVALID, "mg_coarse_chiral_truncate: NULL array");
+  if (!aligned16(psi)) return fail(MG_ERR_INVALID, "mg_coarse_chiral_truncate: psi not 16-byte aligned");
+  const size_t need = trunc_ws_layout(g).bytes;
+  if (ws_bytes < need)
+    return fail(MG_ERR_INVALID, "mg_coarse_chiral_truncate: workspace %zu < %zu bytes", ws_bytes,
+                need);
+  return cuda_status(
+      launch_truncate(g, static_cast<const float2*>(psi), static_cast<float2*>(Uk), sigma,
+                      static_cast<float2*>(coarse_tv), blk_flags, static_cast<char*>(ws),
+                      static_cast<cudaStream_t>(stream)),
+      "mg_coarse_chiral_truncate");
+}
+
+mg_status mg_coarse_build_prolongator(const mg_coarse_problem* prob, const void* Uk, void* P,
+                                      void* stream) {
+  StencilGeom sg;
+  Geom g;
+  mg_status st = make_cgeom(prob, &sg, &g, true);
+  if (st != MG_OK) return st;
+  if (!Uk || !P) return fail(MG_ERR_INVALID, "mg_coarse_build_prolongator: NULL array");
+  return cuda_status(launch_prolongator(g, static_cast<const float2*>(Uk),
+                                        static_cast<float2*>(P), static_cast<cudaStream_t>(stream)),
+                     "mg_coarse_build_prolongator");
+}
+
+mg_status mg_coarse_coarsen(const mg_coarse_problem* prob, const void* X, const void* Y,
+                            const void* P, void* X2, void* Y2, void* stream) {
+  StencilGeom sg;
+  Geom g;
+  mg_status st = make_cgeom(prob, &sg, &g, true);
+  if (st != MG_OK) return st;
+  if (!X || !Y || !P || !X2 || !Y2) return fail(MG_ERR_INVALID, "mg_coarse_coarsen: NULL array");
+  if (!aligned16(X) || !aligned16(Y))
+    return fail(MG_ERR_INVALID, "mg_coarse_coarsen: X and Y must be 16-byte aligned");
+  return cuda_status(launch_stencil_galerkin(g, static_cast<const float2*>(X),
+                                             static_cast<const float2*>(Y),
+                                             static_cast<const float2*>(P),
+                                             static_cast<float2*>(X2), static_cast<float2*>(Y2),
+                                             static_cast<cudaStream_t>(stream)),
+                     "mg_coarse_coarsen");
 }
 
 }  // extern "C"

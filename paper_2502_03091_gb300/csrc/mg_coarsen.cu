@@ -16,12 +16,14 @@ namespace mg {
 namespace {
 
 
+// P[x][alpha][e][i] = U_k[j(x)][alpha][loc(x)][e][i], e < rps (rows per site and
+// chirality: 6 at the fine level, k1 at the second)
 __global__ void prolongator_kernel(const float2* __restrict__ Uk, float2* __restrict__ P, int L0,
                                    int L1, int L2, int L3, int b0, int b1, int b2, int b3,
-                                   int k) {
+                                   int k, int rps) {
   const long V = (long)L0 * L1 * L2 * L3;
   const int nb = b0 * b1 * b2 * b3;
-  const int row = 6 * k;  // complex per (site, chirality)
+  const int row = rps * k;  // complex per (site, chirality)
   const long n = V * 2 * row;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x) {
@@ -302,7 +304,7 @@ __global__ void coarse_apply_kernel(const float2* __restrict__ X, const float2* 
 cudaError_t launch_prolongator(const Geom& g, const float2* Uk, float2* P, cudaStream_t s) {
   TimedScope ts("prolongator", s);
   prolongator_kernel<<<2048, 256, 0, s>>>(Uk, P, g.L[0], g.L[1], g.L[2], g.L[3], g.b[0], g.b[1],
-                                           g.b[2], g.b[3], g.k);
+                                           g.b[2], g.b[3], g.k, g.rps);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,9 @@ struct Geom {
   float hw[4];    // hop weights -1/2 w_mu
   float diag;     // m0 + sum_mu w_mu
   int prec;       // mg_precision
+  int rps = 6;    // rows per site and chirality of the level's vectors (6 = 2 spins x 3
+                  // colours at the fine level, k1 at the second level)
+  int cps = 12;   // complex components per site (2 rps)
 };
 
 constexpr int kMaxM = 64;  // largest m' this build supports
@@ -41,7 +44,19 @@ struct TruncWs {
   size_t gram, r1, z1, w2, hm, flags, bytes;
 };
 
+// operator of a level l >= 1: a nearest-neighbour stencil (X, Y) with n = 2 nc
+// components per site on the periodic lattice L (mg_level2.cu)
+struct StencilGeom {
+  int L[4];
+  long V;
+  int n;
+};
+struct StencilSmoothWs {
+  size_t r, w, part, alpha, scale, bytes;
+};
+
 SmoothWs smooth_ws_layout(const Geom& g);
+StencilSmoothWs stencil_smooth_ws_layout(const StencilGeom& sg, int m);
 TruncWs trunc_ws_layout(const Geom& g);
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -105,6 +120,17 @@ cudaError_t launch_coarsen(const Geom& g, const float2* U, const float2* C, cons
 
 cudaError_t launch_coarse_apply(const Geom& g, const float2* X, const float2* Y,
                                 const float2* vin, float2* vout, int nrhs, cudaStream_t s);
+
+// levels l >= 1 (mg_level2.cu): out = D_l v for nrhs <= 64 right-hand sides; the
+// smoother on D_l psi = 0; the Galerkin product D_{l+1} = P^dag D_l P with g
+// describing the aggregation of the level-l lattice (g.rps = nc)
+cudaError_t launch_stencil_apply(const StencilGeom& sg, const float2* X, const float2* Y,
+                                 const float2* vin, float2* vout, int nrhs, cudaStream_t s);
+cudaError_t launch_stencil_smoother(const StencilGeom& sg, int m, int niter, const float2* X,
+                                    const float2* Y, const float2* psi0, float2* psi, char* ws,
+                                    cudaStream_t s);
+cudaError_t launch_stencil_galerkin(const Geom& g, const float2* X, const float2* Y,
+                                    const float2* P, float2* X2, float2* Y2, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // small complex helpers (float2 / double2 as complex numbers)

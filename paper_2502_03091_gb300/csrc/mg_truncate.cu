@@ -21,8 +21,7 @@ namespace mg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kChunkSites = 8;            // sites staged per chunk
-constexpr int kChunkRows = 6 * kChunkSites;  // rows per chunk
+constexpr int kChunkRows = 48;  // rows staged per chunk (8 fine sites x 6 rows)
 
 // global site of local site `loc` of block `j`
 __device__ __forceinline__ int block_site(int j, int loc, const int L[4], const int b[4],
@@ -43,28 +42,33 @@ __device__ __forceinline__ int block_site(int j, int loc, const int L[4], const 
 
 struct BlockGeom {
   int L[4], b[4], Lc[4];
-  int nb;  // sites per block
+  int nb;      // sites per block
   int m, k;
+  int rps;     // rows per site and chirality (6 at the fine level: 2 spins x 3 colours)
+  int cps;     // complex components per site (2 rps)
+  int csites;  // sites per chunk: kChunkRows / rps, so a chunk has csites * rps <= 48 rows
 };
 
-// Stage the rows of chunk `ch` (kChunkSites sites) of block-chirality bc
-// into As[row][m] (row = local_site_in_chunk*6 + spin_in_chirality*3 + colour).
-// Rows past the block end are zero.
+// Stage the rows of chunk `ch` (csites sites) of block-chirality bc into
+// As[row][m] (row = local_site_in_chunk * rps + row of the site's chirality
+// block; at the fine level spin_in_chirality * 3 + colour).  Rows past the
+// block end, and rows csites * rps .. kChunkRows - 1, are zero.
 __device__ void load_chunk(const float2* __restrict__ psi, const BlockGeom& g, int bc, int ch,
                            float2* As) {
   const int j = bc >> 1, al = bc & 1;
   const int m = g.m;
-  const int per_site4 = 6 * m / 2;  // float4 per site (6 rows of m complex)
-  for (int idx = threadIdx.x; idx < kChunkSites * per_site4; idx += blockDim.x) {
+  const int per_site4 = g.rps * m / 2;  // float4 per site (rps rows of m complex)
+  for (int idx = threadIdx.x; idx < kChunkRows * m / 2; idx += blockDim.x) {
     const int ls = idx / per_site4, o = idx % per_site4;
-    const int loc = ch * kChunkSites + ls;
+    const int loc = ch * g.csites + ls;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (loc < g.nb) {
+    if (ls < g.csites && loc < g.nb) {
       const int x = block_site(j, loc, g.L, g.b, g.Lc);
-      const float4* src = reinterpret_cast<const float4*>(psi + ((long)x * 12 + 6 * al) * m);
+      const float4* src =
+          reinterpret_cast<const float4*>(psi + ((long)x * g.cps + g.rps * al) * m);
       v = __ldg(src + o);
     }
-    reinterpret_cast<float4*>(As + ls * 6 * m)[o] = v;
+    reinterpret_cast<float4*>(As)[idx] = v;
   }
 }
 
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const float2* __restrict
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int c = 0; c < 4; ++c) dacc[a][c] = make_double2(0.0, 0.0);
-  const int nch = (g.nb + kChunkSites - 1) / kChunkSites;
+  const int nch = (g.nb + g.csites - 1) / g.csites;
   for (int ch = 0; ch < nch; ++ch) {
     __syncthreads();
     load_chunk(psi, g, bc, ch, As);
@@ -921,8 +925,8 @@ __global__ void __launch_bounds__(kThreads) form_uk(const float2* __restrict__ p
     for (int l = i; l < m; ++l) cfma(sacc, Zs[i * m + l], Ws[l * k + c]);
     Ms[idx] = sacc;
   }
-  const int nch = (g.nb + kChunkSites - 1) / kChunkSites;
-  float2* out = Uk + (long)bc * 6 * g.nb * k;
+  const int nch = (g.nb + g.csites - 1) / g.csites;
+  float2* out = Uk + (long)bc * g.rps * g.nb * k;
   float2* Us = Ws + m * k;  // chunk of U_k (kChunkRows x k)
   for (int ch = 0; ch < nch; ++ch) {
     __syncthreads();
@@ -930,9 +934,9 @@ __global__ void __launch_bounds__(kThreads) form_uk(const float2* __restrict__ p
     __syncthreads();
     tile_gemm<3, 2, false>(As, m, Ms, k, Us, k, kChunkRows, k, m);
     __syncthreads();
-    const int rows = min(kChunkRows, 6 * (g.nb - ch * kChunkSites));
+    const int rows = g.rps * min(g.csites, g.nb - ch * g.csites);
     for (int idx = threadIdx.x; idx < rows * k; idx += blockDim.x)
-      out[(long)(ch * kChunkRows) * k + idx] = Us[idx];
+      out[(long)(ch * g.csites * g.rps) * k + idx] = Us[idx];
   }
 }
 
@@ -955,6 +959,9 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
   bg.nb = g.nb;
   bg.m = g.m;
   bg.k = g.k;
+  bg.rps = g.rps;
+  bg.cps = g.cps;
+  bg.csites = kChunkRows / g.rps;
   const int nbc = (int)(2 * g.nblk);
   const int m = g.m, k = g.k;
   const size_t sm_gram0 = sizeof(float2) * (size_t)(2 * kChunkRows * m);
@@ -971,7 +978,7 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
     cudaFuncSetAttribute(form_uk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
     attr_done = true;
   }
-  if (g.prec == MG_PREC_MIXED && gram_tc_supported(g)) {
+  if (g.prec == MG_PREC_MIXED && g.rps == 6 && gram_tc_supported(g)) {
     // mixed precision: G1 on the tensor cores in BF16 (CholeskyQR2's second
     // pass, below, is FP32 and restores the orthonormality)
     int* st = device_status_word();

@@ -29,7 +29,9 @@ EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_apply_dirac", "mg_smooth_
            "mg_build_prolongator", "mg_coarsen", "mg_coarse_apply", "mg_chiral_truncate_static",
            "mg_timing_enable",
            "mg_timing_read", "mg_batch_create", "mg_batch_launch", "mg_batch_streams",
-           "mg_batch_destroy", "mg_tuned_pairs", "mg_sync_status", "mg_last_error", "mg_version")
+           "mg_batch_destroy", "mg_tuned_pairs", "mg_sync_status", "mg_last_error", "mg_version",
+           "mg_coarse_workspace_size", "mg_coarse_op_apply", "mg_coarse_smooth_testvecs",
+           "mg_coarse_chiral_truncate", "mg_coarse_build_prolongator", "mg_coarse_coarsen")
 
 
 class MgError(RuntimeError):
@@ -47,6 +49,12 @@ class _Problem(ctypes.Structure):
                 ("m0", ctypes.c_double), ("csw", ctypes.c_double), ("xi", ctypes.c_double),
                 ("n_vec", ctypes.c_int32), ("k", ctypes.c_int32), ("mr_iters", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class _CoarseProblem(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 4), ("block", ctypes.c_int32 * 4),
+                ("nc", ctypes.c_int32), ("n_vec", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("mr_iters", ctypes.c_int32)]
 
 
 class _LevelDesc(ctypes.Structure):
@@ -105,6 +113,36 @@ class Problem:
         return self.volume // self.block_volume
 
 
+@dataclass
+class CoarseProblem:
+    """Python mirror of mg_coarse_problem: a level l >= 1 whose operator is the
+    stencil (X, Y) with 2*nc components per site on the lattice dims."""
+    dims: Sequence[int]
+    block: Sequence[int]
+    nc: int
+    n_vec: int
+    k: int
+    mr_iters: int
+
+    def c(self) -> _CoarseProblem:
+        p = _CoarseProblem()
+        p.dims[:] = [int(v) for v in self.dims]
+        p.block[:] = [int(v) for v in self.block]
+        p.nc, p.n_vec, p.k, p.mr_iters = int(self.nc), int(self.n_vec), int(self.k), int(self.mr_iters)
+        return p
+
+    volume = Problem.volume
+    block_volume = Problem.block_volume
+    coarse_dims = Problem.coarse_dims
+    n_blocks = Problem.n_blocks
+
+    @classmethod
+    def below(cls, prob: "Problem", block, n_vec: int, k: int, mr_iters: int) -> "CoarseProblem":
+        """The level under the fine problem prob: its lattice is prob's coarse
+        lattice and its operator has 2 prob.k components per site."""
+        return cls(prob.coarse_dims, block, prob.k, n_vec, k, mr_iters)
+
+
 _lib = None
 
 
@@ -130,6 +168,17 @@ def library(path: str = LIB_PATH):
     for f in ("mg_clover_field", "mg_apply_dirac", "mg_smooth_testvecs", "mg_chiral_truncate",
               "mg_chiral_truncate_static", "mg_build_prolongator", "mg_coarsen",
               "mg_coarse_apply"):
+        getattr(lib, f).restype = ctypes.c_int
+    Cp = ctypes.POINTER(_CoarseProblem)
+    lib.mg_coarse_workspace_size.argtypes = [Cp, ctypes.c_int]
+    lib.mg_coarse_workspace_size.restype = ctypes.c_size_t
+    lib.mg_coarse_op_apply.argtypes = [Cp, P, P, P, P, ctypes.c_int32, P]
+    lib.mg_coarse_smooth_testvecs.argtypes = [Cp, P, P, P, P, P, ctypes.c_size_t, P]
+    lib.mg_coarse_chiral_truncate.argtypes = [Cp, P, P, P, P, P, P, ctypes.c_size_t, P]
+    lib.mg_coarse_build_prolongator.argtypes = [Cp, P, P, P]
+    lib.mg_coarse_coarsen.argtypes = [Cp, P, P, P, P, P, P]
+    for f in ("mg_coarse_op_apply", "mg_coarse_smooth_testvecs", "mg_coarse_chiral_truncate",
+              "mg_coarse_build_prolongator", "mg_coarse_coarsen"):
         getattr(lib, f).restype = ctypes.c_int
     lib.mg_timing_enable.argtypes = [ctypes.c_int]
     lib.mg_timing_enable.restype = ctypes.c_int
@@ -352,6 +401,156 @@ def mg_coarse_apply(prob: Problem, X, Y, v_in, v_out, stream=None):
     pc = prob.c()
     _check(library().mg_coarse_apply(ctypes.byref(pc), _ptr(X), _ptr(Y), _ptr(v_in), _ptr(v_out),
                                      nrhs, _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# levels l >= 1
+# ---------------------------------------------------------------------------
+def shape_cX(cp: CoarseProblem):
+    return (cp.volume, 2 * cp.nc, 2 * cp.nc)
+
+
+def shape_cY(cp: CoarseProblem):
+    return (cp.volume, 8, 2 * cp.nc, 2 * cp.nc)
+
+
+def shape_cvec(cp: CoarseProblem, nrhs: int):
+    return (cp.volume, 2 * cp.nc, nrhs)
+
+
+def shape_cUk(cp: CoarseProblem):
+    return (cp.n_blocks, 2, cp.block_volume, cp.nc, cp.k)
+
+
+def shape_cP(cp: CoarseProblem):
+    return (cp.volume, 2, cp.nc, cp.k)
+
+
+def shape_cX2(cp: CoarseProblem):
+    return (cp.n_blocks, 2 * cp.k, 2 * cp.k)
+
+
+def shape_cY2(cp: CoarseProblem):
+    return (cp.n_blocks, 8, 2 * cp.k, 2 * cp.k)
+
+
+def mg_coarse_workspace_size(cp: CoarseProblem, which: int) -> int:
+    pc = cp.c()
+    n = library().mg_coarse_workspace_size(ctypes.byref(pc), which)
+    if n == 0 and which != MG_CALL_COARSEN:
+        raise MgError(1, library().mg_last_error().decode())
+    return int(n)
+
+
+def coarse_workspace(cp: CoarseProblem, which: int, device=None):
+    import torch
+    return torch.empty(max(256, mg_coarse_workspace_size(cp, which)), dtype=torch.uint8,
+                       device=device or "cuda")
+
+
+def mg_coarse_op_apply(cp: CoarseProblem, X, Y, v_in, v_out, stream=None):
+    """v_out = D_l v_in on cp's lattice (only dims and nc are used)."""
+    import torch
+    nrhs = int(v_in.shape[-1])
+    _expect(X, shape_cX(cp), torch.complex64, "X")
+    _expect(Y, shape_cY(cp), torch.complex64, "Y")
+    _expect(v_in, shape_cvec(cp, nrhs), torch.complex64, "v_in")
+    _expect(v_out, shape_cvec(cp, nrhs), torch.complex64, "v_out")
+    pc = cp.c()
+    _check(library().mg_coarse_op_apply(ctypes.byref(pc), _ptr(X), _ptr(Y), _ptr(v_in),
+                                        _ptr(v_out), nrhs, _stream(stream)))
+
+
+def mg_coarse_smooth_testvecs(cp: CoarseProblem, X, Y, psi0, psi, ws, stream=None):
+    import torch
+    _expect(X, shape_cX(cp), torch.complex64, "X")
+    _expect(Y, shape_cY(cp), torch.complex64, "Y")
+    _expect(psi0, shape_cvec(cp, cp.n_vec), torch.complex64, "psi0")
+    _expect(psi, shape_cvec(cp, cp.n_vec), torch.complex64, "psi")
+    pc = cp.c()
+    _check(library().mg_coarse_smooth_testvecs(ctypes.byref(pc), _ptr(X), _ptr(Y), _ptr(psi0),
+                                               _ptr(psi), _ptr(ws),
+                                               ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def mg_coarse_chiral_truncate(cp: CoarseProblem, psi, Uk, sigma, coarse_tv, blk_flags, ws,
+                              stream=None):
+    import torch
+    _expect(psi, shape_cvec(cp, cp.n_vec), torch.complex64, "psi")
+    _expect(Uk, shape_cUk(cp), torch.complex64, "Uk")
+    _expect(sigma, (cp.n_blocks, 2, cp.k), torch.float64, "sigma")
+    _expect(coarse_tv, (cp.n_blocks, 2, cp.k, cp.n_vec), torch.complex64, "coarse_tv")
+    _expect(blk_flags, (cp.n_blocks, 2), torch.int32, "blk_flags")
+    pc = cp.c()
+    _check(library().mg_coarse_chiral_truncate(ctypes.byref(pc), _ptr(psi), _ptr(Uk),
+                                               _ptr(sigma), _ptr(coarse_tv), _ptr(blk_flags),
+                                               _ptr(ws), ws.numel() * ws.element_size(),
+                                               _stream(stream)))
+
+
+def mg_coarse_build_prolongator(cp: CoarseProblem, Uk, P, stream=None):
+    import torch
+    _expect(Uk, shape_cUk(cp), torch.complex64, "Uk")
+    _expect(P, shape_cP(cp), torch.complex64, "P")
+    pc = cp.c()
+    _check(library().mg_coarse_build_prolongator(ctypes.byref(pc), _ptr(Uk), _ptr(P),
+                                                 _stream(stream)))
+
+
+def mg_coarse_coarsen(cp: CoarseProblem, X, Y, P, X2, Y2, stream=None):
+    import torch
+    _expect(X, shape_cX(cp), torch.complex64, "X")
+    _expect(Y, shape_cY(cp), torch.complex64, "Y")
+    _expect(P, shape_cP(cp), torch.complex64, "P")
+    _expect(X2, shape_cX2(cp), torch.complex64, "X2")
+    _expect(Y2, shape_cY2(cp), torch.complex64, "Y2")
+    pc = cp.c()
+    _check(library().mg_coarse_coarsen(ctypes.byref(pc), _ptr(X), _ptr(Y), _ptr(P), _ptr(X2),
+                                       _ptr(Y2), _stream(stream)))
+
+
+@dataclass
+class CoarseLevel:
+    """Device buffers of one level l >= 1 (its operator X, Y comes from the
+    level above)."""
+    prob: CoarseProblem
+    X: object
+    Y: object
+    psi0: object
+    psi: object = None
+    Uk: object = None
+    sigma: object = None
+    flags: object = None
+    P: object = None
+    X2: object = None
+    Y2: object = None
+    ws_smooth: object = None
+    ws_trunc: object = None
+
+    @classmethod
+    def allocate(cls, cp: CoarseProblem, X, Y, psi0):
+        import torch
+        dev, c64 = X.device, torch.complex64
+        lv = cls(cp, X, Y, psi0)
+        lv.psi = torch.empty(shape_cvec(cp, cp.n_vec), dtype=c64, device=dev)
+        lv.Uk = torch.empty(shape_cUk(cp), dtype=c64, device=dev)
+        lv.sigma = torch.empty((cp.n_blocks, 2, cp.k), dtype=torch.float64, device=dev)
+        lv.flags = torch.empty((cp.n_blocks, 2), dtype=torch.int32, device=dev)
+        lv.P = torch.empty(shape_cP(cp), dtype=c64, device=dev)
+        lv.X2 = torch.empty(shape_cX2(cp), dtype=c64, device=dev)
+        lv.Y2 = torch.empty(shape_cY2(cp), dtype=c64, device=dev)
+        lv.ws_smooth = coarse_workspace(cp, MG_CALL_SMOOTH, dev)
+        lv.ws_trunc = coarse_workspace(cp, MG_CALL_TRUNCATE, dev)
+        return lv
+
+    def run(self, stream=None):
+        """Smoother -> sigma_3 truncation -> prolongator -> next coarse operator."""
+        p = self.prob
+        mg_coarse_smooth_testvecs(p, self.X, self.Y, self.psi0, self.psi, self.ws_smooth, stream)
+        mg_coarse_chiral_truncate(p, self.psi, self.Uk, self.sigma, None, self.flags,
+                                  self.ws_trunc, stream)
+        mg_coarse_build_prolongator(p, self.Uk, self.P, stream)
+        mg_coarse_coarsen(p, self.X, self.Y, self.P, self.X2, self.Y2, stream)
 
 
 # ---------------------------------------------------------------------------

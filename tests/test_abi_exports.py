@@ -52,3 +52,32 @@ def test_version_and_validation(lib):
     assert st == 1 and b"NULL" in lib.mg_last_error()
     st = lib.mg_coarse_apply(ctypes.byref(pc), None, None, None, None, 8, None)
     assert st == 1
+
+
+def test_coarse_level_validation(lib):
+    """Levels l >= 1: problem checks and workspace sizes on the host."""
+    cp = mg.CoarseProblem([8, 8, 8, 8], [2, 2, 2, 2], 24, 64, 32, 20)
+    V, n, m = 4096, 48, 64
+    # residual and D r fields plus one float4 partial per (site, vector)
+    assert mg.mg_coarse_workspace_size(cp, mg.MG_CALL_SMOOTH) >= 2 * V * n * m * 8 + V * m * 16
+    assert mg.mg_coarse_workspace_size(cp, mg.MG_CALL_TRUNCATE) > 0
+    assert mg.mg_coarse_workspace_size(cp, mg.MG_CALL_COARSEN) == 0
+    for bad, msg in ((dict(nc=33), "nc"), (dict(nc=0), "nc"), (dict(block=[3, 2, 2, 2]), "divide"),
+                     (dict(n_vec=30), "n_vec"), (dict(k=33), "k ="),
+                     (dict(nc=1, block=[1, 1, 1, 2], n_vec=8), "rows")):
+        kw = dict(dims=[8, 8, 8, 8], block=[2, 2, 2, 2], nc=24, n_vec=64, k=32, mr_iters=20)
+        kw.update(bad)
+        with pytest.raises(mg.MgError) as e:
+            mg.mg_coarse_workspace_size(mg.CoarseProblem(**kw), mg.MG_CALL_SMOOTH)
+        assert msg in str(e.value), (bad, str(e.value))
+    pc = cp.c()
+    st = lib.mg_coarse_smooth_testvecs(ctypes.byref(pc), None, None, None, None, None, 0, None)
+    assert st == 1 and b"NULL" in lib.mg_last_error()
+    st = lib.mg_coarse_coarsen(ctypes.byref(pc), None, None, None, None, None, None)
+    assert st == 1
+    st = lib.mg_coarse_op_apply(ctypes.byref(pc), None, None, None, None, 8, None)
+    assert st == 1
+    cp0 = mg.CoarseProblem([8, 8, 8, 8], [2, 2, 2, 2], 24, 64, 32, 0)
+    pc0 = cp0.c()
+    st = lib.mg_coarse_smooth_testvecs(ctypes.byref(pc0), None, None, None, None, None, 0, None)
+    assert st == 1 and b"mr_iters" in lib.mg_last_error()

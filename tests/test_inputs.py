@@ -44,3 +44,27 @@ def test_batch_workload_draw():
         assert 6 * int(np.prod(h["block"])) >= h["m"] and h["k"] <= h["m"]
     assert w == G.batch_workload(30)          # a pure function of the seed
     assert w != G.batch_workload(31)
+
+
+def test_stencil_operator_structure_and_chunking():
+    """The random level-l operator has the coarse-operator symmetry
+    (sigma_3 D is Hermitian) and does not depend on how it is drawn."""
+    cd, nc = [2, 3, 2, 2], 3
+    X, Y = G.stencil_operator(cd, nc, 7)
+    X4, Y4 = G.stencil_operator(cd, nc, 7, threads=4)
+    assert np.array_equal(X, X4) and np.array_equal(Y, Y4)
+    V, n = G.volume(cd), 2 * nc
+    D = np.zeros((V * n, V * n), dtype=np.complex128)
+    s = np.arange(V)
+    c = [s % 2, (s // 2) % 3, (s // 6) % 2, s // 12]
+    for x in range(V):
+        D[x * n:(x + 1) * n, x * n:(x + 1) * n] += X[x]
+        for d in range(8):
+            mu, st = d % 4, (1 if d < 4 else -1)
+            cc = [a[x] for a in c]
+            cc[mu] = (cc[mu] + st) % cd[mu]
+            y = cc[0] + 2 * (cc[1] + 3 * (cc[2] + 2 * cc[3]))
+            D[x * n:(x + 1) * n, y * n:(y + 1) * n] += Y[x, d]
+    s3 = np.tile(np.r_[np.ones(nc), -np.ones(nc)], V)
+    H = s3[:, None] * D
+    assert np.abs(H - H.conj().T).max() < 1e-12
