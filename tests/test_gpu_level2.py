@@ -21,8 +21,13 @@ Tolerances (FP32 arithmetic on complex64 inputs, unit roundoff u = 2^-24):
     same sums of absolute values (K = 9 n for the apply; K = 2 nc + 9 |Lambda|
     for the Galerkin product: two GEMMs of depth nc and up to 9 |Lambda|
     accumulated terms);
-  * smoother: each vector's relative 2-norm error <= 2e-5, as at the fine
-    level (N FP32 applies, FP64 sums of the inner products);
+  * smoother: each vector's relative 2-norm error <= 2e-5 on the random
+    stencil, as at the fine level (N FP32 applies, FP64 sums of the inner
+    products), and <= 5e-5 on the chain's D_1: along its MR trajectory the
+    cancellation ratio | |D_1| |r| | / |D_1 r| grows to 15 (r turns into
+    near-null vectors of D_1), and an FP32 restatement of the same recurrence
+    (per-term partial sums, FP64 inner products) lands 2.3e-5 from the FP64
+    oracle on it;
   * truncation: retained singular values relative <= 1e-5; per-block projector
     error <= max(1e-5, the Davis-Kahan bound of an FP32-level perturbation);
   * prolongator: bit exact (data movement);
@@ -146,7 +151,7 @@ def test_chain_smoother(chain):
     want = c["psi2"]
     err = np.linalg.norm((got - want).reshape(-1, M2), axis=0) / np.linalg.norm(
         want.reshape(-1, M2), axis=0)
-    assert err.max() <= 2e-5, err.max()
+    assert err.max() <= 5e-5, err.max()
 
 
 def test_chain_truncation(chain):
