@@ -344,7 +344,7 @@ def _roofline_table(w, prec, kern, steps):
         with open(prof) as fh:
             pj = json.load(fh)
         ent = pj.get(prec, {}).get(top, {})
-        if (ent.get("source_sha1") == _kernel_sha1() and ent.get("workload") == w["workload"]
+        if (ent.get("source_sha1") == _kernel_sha1(top) and ent.get("workload") == w["workload"]
                 and ent.get("precision") == prec):
             traffic = ent.get("dram_bytes_per_launch")
     roofline["traffic"] = traffic
@@ -746,13 +746,28 @@ def run_ours(args, w):
     rep.close()
 
 
-def _kernel_sha1():
-    """Hash of the CUDA sources: a stored ncu traffic figure is only reported
-    while the kernels it was measured on are unchanged."""
+# source files of each timed stage's kernels (prefix match, first hit wins);
+# every stage also depends on the shared header mg_common.cuh
+_STAGE_SOURCES = (("mr_", ("mg_dslash.cu", "mg_bulk.cuh")),
+                  ("trunc_gram_tc", ("mg_tc.cu",)),
+                  ("trunc_", ("mg_truncate.cu",)),
+                  ("prolongator", ("mg_coarsen.cu",)),
+                  ("coarsen", ("mg_coarsen.cu",)),
+                  ("coarse_apply", ("mg_coarsen.cu",)),
+                  ("c_", ("mg_level2.cu", "mg_bulk.cuh")))
+
+
+def _kernel_sha1(stage: str):
+    """Hash of the CUDA sources of one stage's kernels: a stored ncu traffic
+    figure is only reported while the kernels it was measured on are
+    unchanged."""
     import hashlib
+    files = next((f for pre, f in _STAGE_SOURCES if stage.startswith(pre)), None)
+    if files is None:
+        return None
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2502_03091_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in files + ("mg_common.cuh",):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
