@@ -252,6 +252,57 @@ mg_status mg_coarse_build_prolongator(const mg_coarse_problem* prob, const void*
 mg_status mg_coarse_coarsen(const mg_coarse_problem* prob, const void* X, const void* Y,
                             const void* P, void* X2, void* Y2, void* stream);
 
+/* ------------------------------------------------------------------------
+ * The solve the setup serves (Sec. 2: the multigrid hierarchy used in a
+ * K-cycle as the preconditioner of a flexible outer Krylov solver, FGMRES).
+ * A hierarchy is the output of the setup calls above: the fine operator
+ * (fine, U, C), its prolongator P and coarse operator X, Y (mg_build_prolongator,
+ * mg_coarsen), and for three levels the second level's P2, X2, Y2
+ * (mg_coarse_build_prolongator, mg_coarse_coarsen with problem `second`).
+ * Preconditioner, the K-cycle at level l applied to r:
+ *   x = nu_pre MR steps on A_l x = r from 0;  s = r - A_l x;
+ *   e = approximate solve of A_{l+1} e = P_l^dag s: coarsest_iters GMRES steps
+ *       on the coarsest level, else kcycle_iters FGMRES steps preconditioned by
+ *       the K-cycle at level l+1;
+ *   x += P_l e;  x += nu_post MR steps on A_l y = r - A_l x.
+ * n_levels = 1 is restarted GMRES on D alone (no preconditioner).
+ * Arnoldi uses classical Gram-Schmidt twice; all vectors are complex64, the
+ * Krylov bookkeeping is FP64 on the host.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  mg_problem fine;          /* fine operator and first aggregation; k = k1 (n_vec is not read) */
+  const void* U;
+  const void* C;            /* NULL for pure Wilson */
+  const void* P;            /* [V][2][2][3][k1] */
+  const void* X;            /* [nc][2k1][2k1] */
+  const void* Y;            /* [nc][8][2k1][2k1] */
+  int32_t n_levels;         /* 1, 2 or 3 */
+  mg_coarse_problem second; /* n_levels = 3: dims = the fine coarse lattice, nc = k1, block, k = k2 */
+  const void* P2;           /* [nc][2][k1][k2] */
+  const void* X2;           /* [nc2][2k2][2k2] */
+  const void* Y2;           /* [nc2][8][2k2][2k2] */
+  int32_t nu_pre, nu_post;  /* MR steps before / after the coarse correction, >= 0 */
+  int32_t kcycle_iters;     /* FGMRES steps on each intermediate level (1..64) */
+  int32_t coarsest_iters;   /* GMRES steps on the coarsest level (1..64) */
+} mg_hierarchy;
+
+/* Scratch bytes of mg_solve for nrhs systems and an outer restart length
+ * (0 for invalid arguments; mg_last_error() says why). */
+size_t mg_solve_workspace_size(const mg_hierarchy* h, int32_t nrhs, int32_t restart);
+
+/* Solves D x_c = b_c for nrhs independent systems (nrhs = 4, 8, 16, 32 or 64),
+ * b and x in the spinor layout [V][4][3][nrhs] (x must not alias b), from
+ * x = 0, by FGMRES(restart) preconditioned by the K-cycle, until every
+ * system's least-squares residual estimate is <= tol |b_c| or max_iters outer
+ * steps are done.  Out (host): *iters = outer steps taken; relres[nrhs] = the
+ * true |b_c - D x_c| / |b_c| at the end (FP32 residual, FP64 norms).
+ * ws: mg_solve_workspace_size(h, nrhs, restart) bytes, 256-byte aligned.
+ * Synchronous: the call returns when the solve is done (it synchronises
+ * `stream` at every Krylov step to read the inner products). */
+mg_status mg_solve(const mg_hierarchy* h, const void* b, void* x, int32_t nrhs, double tol,
+                   int32_t restart, int32_t max_iters, int32_t* iters, double* relres, void* ws,
+                   size_t ws_bytes, void* stream);
+
 /* mg_chiral_truncate for callers that cannot allocate device memory (the
  * paper has no counterpart; this is a service of this library).  A host
  * application whose device memory is owned by its own pool allocator, or a

@@ -1,0 +1,720 @@
+// mg_solve.cu -- the solve the setup serves (paper Sec. 2: the multigrid
+// hierarchy used in a K-cycle as the preconditioner of a flexible outer
+// Krylov solver, FGMRES).
+//
+// Outer solver: restarted FGMRES on the fine operator D.  Preconditioner, the
+// K-cycle at level l applied to r:
+//   x  = nu_pre MR steps on A_l x = r from x = 0;  s = r - A_l x
+//   e  = coarse solve of A_{l+1} e = R_l s: GMRES with coarsest_iters steps on
+//        the coarsest level, else kcycle_iters FGMRES steps preconditioned by
+//        the K-cycle at level l+1
+//   x += P_l e;  x += nu_post MR steps on A_l y = r - A_l x
+// Arnoldi uses classical Gram-Schmidt applied twice.
+//
+// nrhs independent systems are solved together.  Every vector is an R x nrhs
+// complex64 array whose column c belongs to system c: at the fine level the
+// ABI spinor layout [V][4][3][nrhs] (R = 12 V), below it the coarse vector
+// layout [V][n][nrhs] (R = n V).  Inner products, step lengths and Krylov
+// coefficients are per column; the Krylov bookkeeping (Hessenberg matrices,
+// Givens rotations, least-squares solves) runs on the host in double, the
+// vector work in the kernels of this file and the operators' kernels
+// (mg_dslash.cu at the fine level, the stencil apply of mg_level2.cu below).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "mg_common.cuh"
+
+namespace mg {
+
+// mg_abi.cu
+mg_status make_cgeom(const mg_coarse_problem* p, StencilGeom* sg, Geom* g, bool full);
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kMaxKrylov = 64;   // longest Krylov cycle on any level
+constexpr int kDotGrid = 2 * 152;
+
+using cplx = std::complex<double>;
+
+// ---------------------------------------------------------------------------
+// vector kernels on R x nrhs arrays (nrhs divides 256)
+// ---------------------------------------------------------------------------
+// part[blk][i][c] = sum over the CTA's rows r of conj(A_i[r][c]) B[r][c], i < na.
+// FP32 products summed in FP32 over 32 rows, then in FP64; fixed order.
+__global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, long astride,
+                                                  int na, const float2* __restrict__ B, long R,
+                                                  int nrhs, double2* part) {
+  __shared__ double2 red[kT];
+  const int G = kT / nrhs, c = threadIdx.x % nrhs, g = threadIdx.x / nrhs;
+  const long rstep = (long)gridDim.x * G;
+  for (int i0 = 0; i0 < na; i0 += 4) {
+    double2 acc[4];
+    float2 fac[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[u] = make_double2(0.0, 0.0);
+      fac[u] = make_float2(0.f, 0.f);
+    }
+    int cnt = 0;
+    for (long r = (long)blockIdx.x * G + g; r < R; r += rstep) {
+      const float2 bv = __ldg(B + r * nrhs + c);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u < na) cfmac(fac[u], __ldg(A + (i0 + u) * astride + r * nrhs + c), bv);
+      if (++cnt == 32) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          acc[u].x += fac[u].x;
+          acc[u].y += fac[u].y;
+          fac[u] = make_float2(0.f, 0.f);
+        }
+        cnt = 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[u].x += fac[u].x;
+      acc[u].y += fac[u].y;
+    }
+    for (int u = 0; u < 4 && i0 + u < na; ++u) {
+      red[threadIdx.x] = acc[u];
+      __syncthreads();
+      if (g == 0) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int gg = 0; gg < G; ++gg) {
+          s.x += red[gg * nrhs + c].x;
+          s.y += red[gg * nrhs + c].y;
+        }
+        part[((long)blockIdx.x * na + i0 + u) * nrhs + c] = s;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// out[j] = sum over the CTAs' partials, in CTA order
+__global__ void dots_finish(const double2* __restrict__ part, int nblk, int n, double2* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = 0; b < nblk; ++b) {
+    s.x += part[(long)b * n + j].x;
+    s.y += part[(long)b * n + j].y;
+  }
+  out[j] = s;
+}
+
+// w[r][c] += sum_{i < na} coef[i][c] A_i[r][c]
+__global__ void __launch_bounds__(kT) combo_kernel(float2* w, const float2* __restrict__ A,
+                                                   long astride, int na,
+                                                   const float2* __restrict__ coef, long n,
+                                                   int nrhs) {
+  __shared__ float2 cs[kMaxKrylov * 64];
+  for (int i = threadIdx.x; i < na * nrhs; i += blockDim.x) cs[i] = coef[i];
+  __syncthreads();
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % nrhs);
+    float2 acc = w[idx];
+    for (int i = 0; i < na; ++i) cfma(acc, cs[i * nrhs + c], __ldg(A + i * astride + idx));
+    w[idx] = acc;
+  }
+}
+
+// out[r][c] = a[c] x[r][c] + b[c] y[r][c]   (y may be null; out may alias x or y)
+__global__ void __launch_bounds__(kT) axpby_kernel(float2* out, const float2* x,
+                                                   const float2* __restrict__ a, const float2* y,
+                                                   const float2* __restrict__ b, long n,
+                                                   int nrhs) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % nrhs);
+    float2 v = cmul(__ldg(a + c), x[idx]);
+    if (y) cfma(v, __ldg(b + c), y[idx]);
+    out[idx] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// transfers between level l (lattice L, aggregates b, rps rows per site and
+// chirality) and level l+1 (kn columns per chirality of P)
+// ---------------------------------------------------------------------------
+struct Xfer {
+  int L[4], b[4], Lc[4];
+  int nb, rps, kn, nrhs;
+};
+
+__device__ __forceinline__ int xfer_site(const Xfer& t, int j, int loc) {
+  int jc[4], lc[4];
+  int u = j;
+  jc[0] = u % t.Lc[0]; u /= t.Lc[0];
+  jc[1] = u % t.Lc[1]; u /= t.Lc[1];
+  jc[2] = u % t.Lc[2]; jc[3] = u / t.Lc[2];
+  u = loc;
+  lc[0] = u % t.b[0]; u /= t.b[0];
+  lc[1] = u % t.b[1]; u /= t.b[1];
+  lc[2] = u % t.b[2]; lc[3] = u / t.b[2];
+  const int x0 = jc[0] * t.b[0] + lc[0], x1 = jc[1] * t.b[1] + lc[1];
+  const int x2 = jc[2] * t.b[2] + lc[2], x3 = jc[3] * t.b[3] + lc[3];
+  return x0 + t.L[0] * (x1 + t.L[1] * (x2 + t.L[2] * x3));
+}
+
+// out[j][a kn + i][c] = sum_{x in block j} sum_{e < rps} conj(P[x][a][e][i]) v[x][a rps + e][c]
+__global__ void __launch_bounds__(kT) restrict_kernel(Xfer t, const float2* __restrict__ P,
+                                                      const float2* __restrict__ v, float2* out) {
+  const int j = blockIdx.x;
+  const int nout = 2 * t.kn * t.nrhs;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    const int c = o % t.nrhs, ai = o / t.nrhs;
+    const int a = ai / t.kn, i = ai % t.kn;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int loc = 0; loc < t.nb; ++loc) {
+      const int x = xfer_site(t, j, loc);
+      const float2* Px = P + ((long)x * 2 + a) * t.rps * t.kn + i;
+      const float2* vx = v + ((long)x * 2 * t.rps + a * t.rps) * t.nrhs + c;
+      for (int e = 0; e < t.rps; ++e) cfmac(acc, __ldg(Px + e * t.kn), __ldg(vx + e * t.nrhs));
+    }
+    out[((long)j * 2 * t.kn + ai) * t.nrhs + c] = acc;
+  }
+}
+
+// fine[x][a rps + e][c] += sum_i P[x][a][e][i] vc[j(x)][a kn + i][c]
+__global__ void __launch_bounds__(kT) prolong_kernel(Xfer t, const float2* __restrict__ P,
+                                                     const float2* __restrict__ vc, float2* fine,
+                                                     long V) {
+  const long n = V * 2 * t.rps * t.nrhs;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % t.nrhs);
+    const long xe = idx / t.nrhs;
+    const int ae = (int)(xe % (2 * t.rps));
+    const int x = (int)(xe / (2 * t.rps));
+    const int a = ae / t.rps;
+    int u = x;
+    const int c0 = u % t.L[0]; u /= t.L[0];
+    const int c1 = u % t.L[1]; u /= t.L[1];
+    const int c2 = u % t.L[2]; const int c3 = u / t.L[2];
+    const int j = c0 / t.b[0] + t.Lc[0] * (c1 / t.b[1] + t.Lc[1] * (c2 / t.b[2] + t.Lc[2] * (c3 / t.b[3])));
+    const float2* Pr = P + ((long)x * 2 * t.rps + ae) * t.kn;
+    const float2* vj = vc + ((long)j * 2 * t.kn + a * t.kn) * t.nrhs + c;
+    float2 acc = fine[idx];
+    for (int i = 0; i < t.kn; ++i) cfma(acc, __ldg(Pr + i), __ldg(vj + (long)i * t.nrhs));
+    fine[idx] = acc;
+  }
+}
+
+int grid_for(long n) {
+  const long g = (n + kT - 1) / kT;
+  return (int)std::min<long>(g, 152L * 8);
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+struct Lvl {
+  bool fine = false;
+  long R = 0;            // rows of a vector
+  Geom g{};              // fine operator geometry (fine level only)
+  StencilGeom sg{};      // coarse operator geometry
+  const float2 *U = nullptr, *C = nullptr, *X = nullptr, *Y = nullptr;
+  const float2* P = nullptr;  // to level l+1
+  Xfer xf{};
+  long Vsites = 0;       // sites of this level's lattice
+  int kdim = 0;          // length of the Krylov cycle run on this level
+  bool flexible = false;
+  float2 *ts = nullptr, *tw = nullptr, *tx = nullptr, *mr_r = nullptr, *mr_w = nullptr;
+  float2 *rhs = nullptr, *sol = nullptr, *V = nullptr, *Z = nullptr, *kw = nullptr;
+};
+
+struct Plan {
+  std::vector<Lvl> lv;
+  int nrhs = 0;
+  char* dws = nullptr;   // fine operator workspace
+  double2* part = nullptr;
+  double2* dout = nullptr;
+  float2* coef = nullptr;
+  size_t bytes = 0;
+};
+
+class Solver {
+ public:
+  Solver(Plan& p, const mg_hierarchy& h, cudaStream_t s) : P_(p), h_(h), s_(s), n_(p.nrhs) {
+    one_.assign(n_, cplx(1, 0));
+    mone_.assign(n_, cplx(-1, 0));
+  }
+
+  cudaError_t solve(const float2* b, float2* x, double tol, int max_iters, int* iters,
+                    double* relres) {
+    int steps = 0;
+    cudaError_t e = krylov(0, b, x, P_.lv.size() > 1, tol, max_iters, &steps);
+    if (e != cudaSuccess) return e;
+    *iters = steps;
+    // true relative residual per system
+    Lvl& L = P_.lv[0];
+    if ((e = apply(0, x, L.tw)) != cudaSuccess) return e;
+    if ((e = axpby(L.ts, b, one_, L.tw, mone_, L.R)) != cudaSuccess) return e;
+    std::vector<cplx> rr, bb;
+    if ((e = dots(L.ts, 0, 1, L.ts, L.R, rr)) != cudaSuccess) return e;
+    if ((e = dots(b, 0, 1, b, L.R, bb)) != cudaSuccess) return e;
+    for (int c = 0; c < n_; ++c)
+      relres[c] = bb[c].real() > 0 ? std::sqrt(rr[c].real() / bb[c].real()) : 0.0;
+    return cudaSuccess;
+  }
+
+ private:
+  Plan& P_;
+  const mg_hierarchy& h_;
+  cudaStream_t s_;
+  int n_;
+  std::vector<cplx> one_, mone_;
+  std::vector<float2> hcoef_;
+
+  cudaError_t upload(const std::vector<cplx>& v) {
+    hcoef_.resize(v.size());
+    for (size_t i = 0; i < v.size(); ++i)
+      hcoef_[i] = make_float2((float)v[i].real(), (float)v[i].imag());
+    return cudaMemcpyAsync(P_.coef, hcoef_.data(), sizeof(float2) * v.size(),
+                           cudaMemcpyHostToDevice, s_);
+  }
+
+  // out[i * nrhs + c] = <A_i[:, c], B[:, c]>
+  cudaError_t dots(const float2* A, long astride, int na, const float2* B, long R,
+                   std::vector<cplx>& out) {
+    const int G = kT / n_;
+    const int grid = (int)std::min<long>((R + G - 1) / G, kDotGrid);
+    {
+      TimedScope ts("s_dots", s_);
+      dots_kernel<<<grid, kT, 0, s_>>>(A, astride, na, B, R, n_, P_.part);
+      const int n = na * n_;
+      dots_finish<<<(n + 127) / 128, 128, 0, s_>>>(P_.part, grid, n, P_.dout);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::vector<double2> tmp(na * n_);
+    if ((e = cudaMemcpyAsync(tmp.data(), P_.dout, sizeof(double2) * tmp.size(),
+                             cudaMemcpyDeviceToHost, s_)) != cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(s_)) != cudaSuccess) return e;
+    out.resize(tmp.size());
+    for (size_t i = 0; i < tmp.size(); ++i) out[i] = cplx(tmp[i].x, tmp[i].y);
+    return cudaSuccess;
+  }
+
+  // w += sum_i coef[i][c] A_i
+  cudaError_t combo(float2* w, const float2* A, long astride, int na,
+                    const std::vector<cplx>& coef, long R) {
+    cudaError_t e = upload(coef);
+    if (e != cudaSuccess) return e;
+    TimedScope ts("s_combo", s_);
+    combo_kernel<<<grid_for(R * n_), kT, 0, s_>>>(w, A, astride, na, P_.coef, R * n_, n_);
+    return cudaGetLastError();
+  }
+
+  // out = a x + b y
+  cudaError_t axpby(float2* out, const float2* x, const std::vector<cplx>& a, const float2* y,
+                    const std::vector<cplx>& b, long R) {
+    std::vector<cplx> ab(a);
+    ab.insert(ab.end(), b.begin(), b.end());
+    cudaError_t e = upload(ab);
+    if (e != cudaSuccess) return e;
+    TimedScope ts("s_axpby", s_);
+    axpby_kernel<<<grid_for(R * n_), kT, 0, s_>>>(out, x, P_.coef, y, P_.coef + n_, R * n_, n_);
+    return cudaGetLastError();
+  }
+
+  cudaError_t copy(float2* dst, const float2* src, long R) {
+    return cudaMemcpyAsync(dst, src, sizeof(float2) * R * n_, cudaMemcpyDeviceToDevice, s_);
+  }
+  cudaError_t zero(float2* dst, long R) {
+    return cudaMemsetAsync(dst, 0, sizeof(float2) * R * n_, s_);
+  }
+
+  cudaError_t apply(int l, const float2* in, float2* out) {
+    const Lvl& L = P_.lv[l];
+    if (L.fine) return launch_dirac(L.g, L.U, L.C, in, out, P_.dws, s_);
+    return launch_stencil_apply(L.sg, L.X, L.Y, in, out, n_, s_);
+  }
+
+  // x = nu MR steps on A_l x = r from x = 0
+  cudaError_t mr(int l, const float2* r, float2* x, int nu) {
+    Lvl& L = P_.lv[l];
+    cudaError_t e;
+    if ((e = zero(x, L.R)) != cudaSuccess) return e;
+    if ((e = copy(L.mr_r, r, L.R)) != cudaSuccess) return e;
+    std::vector<cplx> wr, ww, a(n_), ma(n_);
+    for (int t = 0; t < nu; ++t) {
+      if ((e = apply(l, L.mr_r, L.mr_w)) != cudaSuccess) return e;
+      if ((e = dots(L.mr_w, 0, 1, L.mr_r, L.R, wr)) != cudaSuccess) return e;
+      if ((e = dots(L.mr_w, 0, 1, L.mr_w, L.R, ww)) != cudaSuccess) return e;
+      for (int c = 0; c < n_; ++c) {
+        a[c] = ww[c].real() > 0 ? wr[c] / ww[c].real() : cplx(0, 0);
+        ma[c] = -a[c];
+      }
+      if ((e = axpby(x, x, one_, L.mr_r, a, L.R)) != cudaSuccess) return e;
+      if ((e = axpby(L.mr_r, L.mr_r, one_, L.mr_w, ma, L.R)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  // the K-cycle at level l: x = M_l r
+  cudaError_t precond(int l, const float2* r, float2* x) {
+    Lvl& L = P_.lv[l];
+    Lvl& N = P_.lv[l + 1];
+    const bool coarsest = l + 2 == (int)P_.lv.size();
+    cudaError_t e;
+    const float2* s = r;
+    if (h_.nu_pre > 0) {
+      if ((e = mr(l, r, x, h_.nu_pre)) != cudaSuccess) return e;
+      if ((e = apply(l, x, L.tw)) != cudaSuccess) return e;
+      if ((e = axpby(L.ts, r, one_, L.tw, mone_, L.R)) != cudaSuccess) return e;
+      s = L.ts;
+    } else if ((e = zero(x, L.R)) != cudaSuccess) {
+      return e;
+    }
+    {
+      TimedScope ts("s_restrict", s_);
+      restrict_kernel<<<(unsigned)N.Vsites, kT, 0, s_>>>(L.xf, L.P, s, N.rhs);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    int steps = 0;
+    if ((e = krylov(l + 1, N.rhs, N.sol, !coarsest, -1.0, N.kdim, &steps)) != cudaSuccess)
+      return e;
+    {
+      TimedScope ts("s_prolong", s_);
+      prolong_kernel<<<grid_for(L.R * n_), kT, 0, s_>>>(L.xf, L.P, N.sol, x, L.Vsites);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (h_.nu_post > 0) {
+      if ((e = apply(l, x, L.tw)) != cudaSuccess) return e;
+      if ((e = axpby(L.ts, r, one_, L.tw, mone_, L.R)) != cudaSuccess) return e;
+      if ((e = mr(l, L.ts, L.tx, h_.nu_post)) != cudaSuccess) return e;
+      if ((e = axpby(x, x, one_, L.tx, one_, L.R)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  // (F)GMRES on level l from x = 0.  tol < 0: one cycle of L.kdim steps.
+  // Otherwise cycles of L.kdim steps until every column's least-squares
+  // residual is <= tol |b_c| or max_iters steps are done.
+  cudaError_t krylov(int l, const float2* b, float2* x, bool flexible, double tol, int max_iters,
+                     int* steps_out) {
+    Lvl& L = P_.lv[l];
+    const long R = L.R, vs = R * n_;
+    const int m = L.kdim;
+    cudaError_t e;
+    std::vector<cplx> bb;
+    if ((e = dots(b, 0, 1, b, R, bb)) != cudaSuccess) return e;
+    std::vector<double> bn(n_);
+    for (int c = 0; c < n_; ++c) bn[c] = std::sqrt(std::max(0.0, bb[c].real()));
+    if ((e = zero(x, R)) != cudaSuccess) return e;
+    int total = 0;
+    bool first = true;
+    std::vector<cplx> H((size_t)n_ * (m + 1) * m), g((size_t)n_ * (m + 1)), sn((size_t)n_ * m);
+    std::vector<double> cs((size_t)n_ * m);
+    std::vector<int> kc(n_);
+    std::vector<cplx> h, h2, hn2, coef, scale(n_);
+    for (;;) {
+      // V_0 = (b - A x) / beta
+      if (first) {
+        if ((e = copy(L.V, b, R)) != cudaSuccess) return e;
+      } else {
+        if ((e = apply(l, x, L.kw)) != cudaSuccess) return e;
+        if ((e = axpby(L.V, b, one_, L.kw, mone_, R)) != cudaSuccess) return e;
+      }
+      std::vector<cplx> beta2;
+      if ((e = dots(L.V, 0, 1, L.V, R, beta2)) != cudaSuccess) return e;
+      std::fill(H.begin(), H.end(), cplx(0, 0));
+      std::fill(g.begin(), g.end(), cplx(0, 0));
+      for (int c = 0; c < n_; ++c) {
+        const double beta = std::sqrt(std::max(0.0, beta2[c].real()));
+        g[(size_t)c * (m + 1)] = beta;
+        scale[c] = beta > 0 ? cplx(1.0 / beta, 0) : cplx(0, 0);
+        kc[c] = beta > 0 ? -1 : 0;  // -1: still growing; else the column's valid steps
+      }
+      if ((e = axpby(L.V, L.V, scale, nullptr, scale, R)) != cudaSuccess) return e;
+      const int jmax = std::min(m, max_iters - total);
+      int steps = 0;
+      for (int j = 0; j < jmax; ++j) {
+        float2* vj = L.V + j * vs;
+        float2* zj = flexible ? L.Z + j * vs : vj;
+        if (flexible && (e = precond(l, vj, zj)) != cudaSuccess) return e;
+        if ((e = apply(l, zj, L.kw)) != cudaSuccess) return e;
+        std::vector<cplx> hsum((size_t)(j + 1) * n_, cplx(0, 0));
+        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+          if ((e = dots(L.V, vs, j + 1, L.kw, R, h)) != cudaSuccess) return e;
+          coef.resize(h.size());
+          for (size_t i = 0; i < h.size(); ++i) {
+            coef[i] = -h[i];
+            hsum[i] += h[i];
+          }
+          if ((e = combo(L.kw, L.V, vs, j + 1, coef, R)) != cudaSuccess) return e;
+        }
+        if ((e = dots(L.kw, 0, 1, L.kw, R, hn2)) != cudaSuccess) return e;
+        bool all_done = true;
+        for (int c = 0; c < n_; ++c) {
+          const double hn = std::sqrt(std::max(0.0, hn2[c].real()));
+          cplx* Hc = &H[(size_t)c * (m + 1) * m];  // column-major: Hc[i + (m+1) j]
+          cplx* gc = &g[(size_t)c * (m + 1)];
+          if (kc[c] < 0) {
+            for (int i = 0; i <= j; ++i) Hc[i + (size_t)(m + 1) * j] = hsum[(size_t)i * n_ + c];
+            Hc[j + 1 + (size_t)(m + 1) * j] = hn;
+            // previous rotations, then a new one that zeroes H[j+1][j]
+            for (int i = 0; i < j; ++i) {
+              cplx& a = Hc[i + (size_t)(m + 1) * j];
+              cplx& bq = Hc[i + 1 + (size_t)(m + 1) * j];
+              const double ci = cs[(size_t)c * m + i];
+              const cplx si = sn[(size_t)c * m + i];
+              const cplx t0 = ci * a + si * bq;
+              const cplx t1 = -std::conj(si) * a + ci * bq;
+              a = t0;
+              bq = t1;
+            }
+            cplx& a = Hc[j + (size_t)(m + 1) * j];
+            const double bj = hn;
+            double cj;
+            cplx sj;
+            const double aa = std::abs(a);
+            if (bj == 0.0) {
+              cj = 1.0;
+              sj = 0.0;
+            } else if (aa == 0.0) {
+              cj = 0.0;
+              sj = 1.0;
+            } else {
+              const double t = std::sqrt(aa * aa + bj * bj);
+              cj = aa / t;
+              sj = (a / aa) * bj / t;
+            }
+            cs[(size_t)c * m + j] = cj;
+            sn[(size_t)c * m + j] = sj;
+            a = cj * a + sj * bj;
+            Hc[j + 1 + (size_t)(m + 1) * j] = 0.0;
+            gc[j + 1] = -std::conj(sj) * gc[j];
+            gc[j] = cj * gc[j];
+            if (hn == 0.0) kc[c] = j + 1;  // breakdown: exact in this column
+          }
+          scale[c] = (kc[c] < 0 && hn > 0) ? cplx(1.0 / hn, 0) : cplx(0, 0);
+          const bool conv = kc[c] >= 0 || (tol >= 0 && std::abs(gc[j + 1]) <= tol * bn[c]);
+          all_done = all_done && conv;
+        }
+        steps = j + 1;
+        if ((e = axpby(L.V + (j + 1) * vs, L.kw, scale, nullptr, scale, R)) != cudaSuccess)
+          return e;
+        if (tol >= 0 && all_done) break;
+      }
+      // y_c = H_c^-1 g_c (upper triangular after the rotations); x += Z y
+      coef.assign((size_t)steps * n_, cplx(0, 0));
+      for (int c = 0; c < n_; ++c) {
+        const int k = kc[c] < 0 ? steps : std::min(kc[c], steps);
+        const cplx* Hc = &H[(size_t)c * (m + 1) * m];
+        const cplx* gc = &g[(size_t)c * (m + 1)];
+        std::vector<cplx> y(k);
+        for (int i = k - 1; i >= 0; --i) {
+          cplx s = gc[i];
+          for (int q = i + 1; q < k; ++q) s -= Hc[i + (size_t)(m + 1) * q] * y[q];
+          const cplx d = Hc[i + (size_t)(m + 1) * i];
+          y[i] = std::abs(d) > 0 ? s / d : cplx(0, 0);
+        }
+        for (int i = 0; i < k; ++i) coef[(size_t)i * n_ + c] = y[i];
+      }
+      if (steps > 0 &&
+          (e = combo(x, flexible ? L.Z : L.V, vs, steps, coef, R)) != cudaSuccess)
+        return e;
+      total += steps;
+      if (tol < 0) break;
+      bool done = true;
+      for (int c = 0; c < n_; ++c) {
+        const cplx* gc = &g[(size_t)c * (m + 1)];
+        if (!(kc[c] >= 0 || std::abs(gc[steps]) <= tol * bn[c])) done = false;
+      }
+      if (done || total >= max_iters || steps == 0) break;
+      first = false;
+    }
+    *steps_out = total;
+    return cudaSuccess;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// plan: geometry of every level and the workspace layout
+// ---------------------------------------------------------------------------
+mg_status fail_msg(mg_status st, const char* msg) {
+  set_last_error(msg);
+  return st;
+}
+
+mg_status make_plan(const mg_hierarchy* h, int nrhs, int restart, Plan& p, char* ws) {
+  if (!h) return fail_msg(MG_ERR_INVALID, "hierarchy is NULL");
+  if (nrhs < 4 || nrhs > 64 || (256 % nrhs) != 0)
+    return fail_msg(MG_ERR_UNSUPPORTED, "nrhs must be 4, 8, 16, 32 or 64");
+  if (restart < 1 || restart > kMaxKrylov)
+    return fail_msg(MG_ERR_INVALID, "restart must be in [1, 64]");
+  if (h->n_levels < 1 || h->n_levels > 3)
+    return fail_msg(MG_ERR_UNSUPPORTED, "n_levels must be 1, 2 or 3");
+  if (h->n_levels > 1 &&
+      (h->nu_pre < 0 || h->nu_post < 0 || h->coarsest_iters < 1 ||
+       h->coarsest_iters > kMaxKrylov || (h->n_levels == 3 &&
+                                          (h->kcycle_iters < 1 || h->kcycle_iters > kMaxKrylov))))
+    return fail_msg(MG_ERR_INVALID, "K-cycle parameters out of range");
+  mg_problem fp = h->fine;
+  const int k1 = fp.k;
+  fp.n_vec = nrhs;
+  fp.k = 1;
+  fp.precision = MG_PREC_FP32;
+  Geom g0;
+  mg_status st = make_geom(&fp, &g0);
+  if (st != MG_OK) return st;
+  g0.k = k1;
+  if (h->n_levels > 1 && (k1 < 1 || k1 > kMaxK))
+    return fail_msg(MG_ERR_SHAPE, "fine.k must be in [1, 32]");
+  if (ws && !h->U) return fail_msg(MG_ERR_INVALID, "U is NULL");
+  if (ws && h->n_levels > 1 && (!h->P || !h->X || !h->Y))
+    return fail_msg(MG_ERR_INVALID, "P, X, Y are required for n_levels > 1");
+  p.nrhs = nrhs;
+  p.lv.assign(h->n_levels, Lvl{});
+  Lvl& L0 = p.lv[0];
+  L0.fine = true;
+  L0.g = g0;
+  L0.U = static_cast<const float2*>(h->U);
+  L0.C = static_cast<const float2*>(h->C);
+  L0.R = g0.V * 12;
+  L0.Vsites = g0.V;
+  L0.kdim = restart;
+  L0.flexible = h->n_levels > 1;
+  if (h->n_levels > 1) {
+    L0.P = static_cast<const float2*>(h->P);
+    for (int i = 0; i < 4; ++i) {
+      L0.xf.L[i] = g0.L[i];
+      L0.xf.b[i] = g0.b[i];
+      L0.xf.Lc[i] = g0.Lc[i];
+    }
+    L0.xf.nb = g0.nb;
+    L0.xf.rps = 6;
+    L0.xf.kn = k1;
+    L0.xf.nrhs = nrhs;
+    Lvl& L1 = p.lv[1];
+    for (int i = 0; i < 4; ++i) L1.sg.L[i] = g0.Lc[i];
+    L1.sg.V = g0.nblk;
+    L1.sg.n = 2 * k1;
+    L1.X = static_cast<const float2*>(h->X);
+    L1.Y = static_cast<const float2*>(h->Y);
+    L1.R = L1.sg.V * L1.sg.n;
+    L1.Vsites = L1.sg.V;
+    L1.kdim = h->n_levels == 2 ? h->coarsest_iters : h->kcycle_iters;
+    L1.flexible = h->n_levels == 3;
+  }
+  if (h->n_levels == 3) {
+    StencilGeom sgc;
+    Geom g1;
+    if ((st = make_cgeom(&h->second, &sgc, &g1, true)) != MG_OK) return st;
+    for (int i = 0; i < 4; ++i)
+      if (h->second.dims[i] != g0.Lc[i])
+        return fail_msg(MG_ERR_SHAPE, "second.dims must be the fine problem's coarse lattice");
+    if (h->second.nc != k1) return fail_msg(MG_ERR_SHAPE, "second.nc must equal fine.k");
+    if (ws && (!h->P2 || !h->X2 || !h->Y2))
+      return fail_msg(MG_ERR_INVALID, "P2, X2, Y2 are required for n_levels = 3");
+    Lvl& L1 = p.lv[1];
+    L1.P = static_cast<const float2*>(h->P2);
+    for (int i = 0; i < 4; ++i) {
+      L1.xf.L[i] = g1.L[i];
+      L1.xf.b[i] = g1.b[i];
+      L1.xf.Lc[i] = g1.Lc[i];
+    }
+    L1.xf.nb = g1.nb;
+    L1.xf.rps = k1;
+    L1.xf.kn = g1.k;
+    L1.xf.nrhs = nrhs;
+    Lvl& L2 = p.lv[2];
+    for (int i = 0; i < 4; ++i) L2.sg.L[i] = g1.Lc[i];
+    L2.sg.V = g1.nblk;
+    L2.sg.n = 2 * g1.k;
+    L2.X = static_cast<const float2*>(h->X2);
+    L2.Y = static_cast<const float2*>(h->Y2);
+    L2.R = L2.sg.V * L2.sg.n;
+    L2.Vsites = L2.sg.V;
+    L2.kdim = h->coarsest_iters;
+    L2.flexible = false;
+  }
+  // workspace layout
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return ws ? ws + at : nullptr;
+  };
+  p.dws = take(smooth_ws_layout(g0).bytes);
+  p.part = reinterpret_cast<double2*>(take(sizeof(double2) * kDotGrid * (kMaxKrylov + 1) * 64));
+  p.dout = reinterpret_cast<double2*>(take(sizeof(double2) * (kMaxKrylov + 1) * 64));
+  p.coef = reinterpret_cast<float2*>(take(sizeof(float2) * (kMaxKrylov + 1) * 64 * 2));
+  for (size_t l = 0; l < p.lv.size(); ++l) {
+    Lvl& L = p.lv[l];
+    const size_t vb = sizeof(float2) * (size_t)L.R * nrhs;
+    auto vec = [&]() { return reinterpret_cast<float2*>(take(vb)); };
+    L.ts = vec();
+    L.tw = vec();
+    L.tx = vec();
+    L.mr_r = vec();
+    L.mr_w = vec();
+    if (l > 0) {
+      L.rhs = vec();
+      L.sol = vec();
+    }
+    L.kw = vec();
+    L.V = reinterpret_cast<float2*>(take(vb * (L.kdim + 1)));
+    if (L.flexible) L.Z = reinterpret_cast<float2*>(take(vb * L.kdim));
+  }
+  p.bytes = o;
+  return MG_OK;
+}
+
+}  // namespace
+}  // namespace mg
+
+using namespace mg;
+
+extern "C" {
+
+size_t mg_solve_workspace_size(const mg_hierarchy* h, int32_t nrhs, int32_t restart) {
+  Plan p;
+  if (make_plan(h, nrhs, restart, p, nullptr) != MG_OK) return 0;
+  return p.bytes;
+}
+
+mg_status mg_solve(const mg_hierarchy* h, const void* b, void* x, int32_t nrhs, double tol,
+                   int32_t restart, int32_t max_iters, int32_t* iters, double* relres, void* ws,
+                   size_t ws_bytes, void* stream) {
+  Plan p;
+  mg_status st = make_plan(h, nrhs, restart, p, nullptr);
+  if (st != MG_OK) return st;
+  if (!b || !x || !iters || !relres || !ws) return fail_msg(MG_ERR_INVALID, "mg_solve: NULL argument");
+  if (b == x) return fail_msg(MG_ERR_INVALID, "mg_solve: x aliases b");
+  if (!(tol > 0) || max_iters < 1) return fail_msg(MG_ERR_INVALID, "mg_solve: tol must be > 0 and max_iters >= 1");
+  if (ws_bytes < p.bytes) return fail_msg(MG_ERR_INVALID, "mg_solve: workspace too small");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0)
+    return fail_msg(MG_ERR_INVALID, "mg_solve: workspace must be 256-byte aligned");
+  if ((st = make_plan(h, nrhs, restart, p, static_cast<char*>(ws))) != MG_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Solver solver(p, *h, s);
+  const cudaError_t e = solver.solve(static_cast<const float2*>(b), static_cast<float2*>(x), tol,
+                                     max_iters, iters, relres);
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return MG_ERR_CUDA;
+  }
+  int dev_status = 0;
+  const cudaError_t e2 = read_device_status(&dev_status, s);
+  if (e2 != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e2));
+    return MG_ERR_CUDA;
+  }
+  if (dev_status) {
+    set_last_error("mg_solve: an operator pass gave up waiting for its staged input");
+    return MG_ERR_TIMEOUT;
+  }
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -31,7 +31,8 @@ EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_apply_dirac", "mg_smooth_
            "mg_timing_read", "mg_batch_create", "mg_batch_launch", "mg_batch_streams",
            "mg_batch_destroy", "mg_tuned_pairs", "mg_sync_status", "mg_last_error", "mg_version",
            "mg_coarse_workspace_size", "mg_coarse_op_apply", "mg_coarse_smooth_testvecs",
-           "mg_coarse_chiral_truncate", "mg_coarse_build_prolongator", "mg_coarse_coarsen")
+           "mg_coarse_chiral_truncate", "mg_coarse_build_prolongator", "mg_coarse_coarsen",
+           "mg_solve_workspace_size", "mg_solve")
 
 
 class MgError(RuntimeError):
@@ -55,6 +56,15 @@ class _CoarseProblem(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 4), ("block", ctypes.c_int32 * 4),
                 ("nc", ctypes.c_int32), ("n_vec", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("mr_iters", ctypes.c_int32)]
+
+
+class _Hierarchy(ctypes.Structure):
+    _fields_ = [("fine", _Problem), ("U", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("P", ctypes.c_void_p), ("X", ctypes.c_void_p), ("Y", ctypes.c_void_p),
+                ("n_levels", ctypes.c_int32), ("second", _CoarseProblem),
+                ("P2", ctypes.c_void_p), ("X2", ctypes.c_void_p), ("Y2", ctypes.c_void_p),
+                ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
+                ("kcycle_iters", ctypes.c_int32), ("coarsest_iters", ctypes.c_int32)]
 
 
 class _LevelDesc(ctypes.Structure):
@@ -180,6 +190,13 @@ def library(path: str = LIB_PATH):
     for f in ("mg_coarse_op_apply", "mg_coarse_smooth_testvecs", "mg_coarse_chiral_truncate",
               "mg_coarse_build_prolongator", "mg_coarse_coarsen"):
         getattr(lib, f).restype = ctypes.c_int
+    Hp = ctypes.POINTER(_Hierarchy)
+    lib.mg_solve_workspace_size.argtypes = [Hp, ctypes.c_int32, ctypes.c_int32]
+    lib.mg_solve_workspace_size.restype = ctypes.c_size_t
+    lib.mg_solve.argtypes = [Hp, P, P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                             ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_double), P, ctypes.c_size_t, P]
+    lib.mg_solve.restype = ctypes.c_int
     lib.mg_timing_enable.argtypes = [ctypes.c_int]
     lib.mg_timing_enable.restype = ctypes.c_int
     lib.mg_timing_read.argtypes = [ctypes.POINTER(_TimingEntry), ctypes.c_int]
@@ -551,6 +568,58 @@ class CoarseLevel:
                                   self.ws_trunc, stream)
         mg_coarse_build_prolongator(p, self.Uk, self.P, stream)
         mg_coarse_coarsen(p, self.X, self.Y, self.P, self.X2, self.Y2, stream)
+
+
+# ---------------------------------------------------------------------------
+# the solve (FGMRES preconditioned by the K-cycle over the hierarchy)
+# ---------------------------------------------------------------------------
+@dataclass
+class KCycle:
+    """K-cycle parameters of mg_solve."""
+    nu_pre: int = 2
+    nu_post: int = 2
+    kcycle_iters: int = 2
+    coarsest_iters: int = 32
+
+
+def _hierarchy(prob: Problem, U, C, P, X, Y, second, P2, X2, Y2, kc: KCycle) -> _Hierarchy:
+    h = _Hierarchy()
+    h.fine = prob.c()
+    h.U, h.C, h.P, h.X, h.Y = _ptr(U), _ptr(C), _ptr(P), _ptr(X), _ptr(Y)
+    h.n_levels = 1 if P is None else (2 if second is None else 3)
+    if second is not None:
+        h.second = second.c()
+        h.P2, h.X2, h.Y2 = _ptr(P2), _ptr(X2), _ptr(Y2)
+    h.nu_pre, h.nu_post = int(kc.nu_pre), int(kc.nu_post)
+    h.kcycle_iters, h.coarsest_iters = int(kc.kcycle_iters), int(kc.coarsest_iters)
+    return h
+
+
+def mg_solve(prob: Problem, U, C, b, x, tol: float, restart: int = 16, max_iters: int = 500,
+             P=None, X=None, Y=None, second: Optional[CoarseProblem] = None, P2=None, X2=None,
+             Y2=None, kcycle: KCycle = KCycle(), ws=None, stream=None):
+    """Solve D x = b for the nrhs = b.shape[-1] systems of b ([V][4][3][nrhs]),
+    preconditioned by the K-cycle over the levels given (none: plain GMRES;
+    P, X, Y: two levels; plus second, P2, X2, Y2: three levels).  Returns
+    (outer steps, per-system true relative residuals)."""
+    import numpy as np
+    import torch
+    nrhs = int(b.shape[-1])
+    _expect(b, (prob.volume, 4, 3, nrhs), torch.complex64, "b")
+    _expect(x, (prob.volume, 4, 3, nrhs), torch.complex64, "x")
+    h = _hierarchy(prob, U, C, P, X, Y, second, P2, X2, Y2, kcycle)
+    lib = library()
+    need = lib.mg_solve_workspace_size(ctypes.byref(h), nrhs, restart)
+    if need == 0:
+        raise MgError(1, lib.mg_last_error().decode())
+    if ws is None or ws.numel() * ws.element_size() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=b.device)
+    iters = ctypes.c_int32(0)
+    rel = (ctypes.c_double * nrhs)()
+    _check(lib.mg_solve(ctypes.byref(h), _ptr(b), _ptr(x), nrhs, float(tol), int(restart),
+                        int(max_iters), ctypes.byref(iters), rel, _ptr(ws),
+                        ws.numel() * ws.element_size(), _stream(stream)))
+    return int(iters.value), np.array(rel[:])
 
 
 # ---------------------------------------------------------------------------

@@ -81,3 +81,34 @@ def test_coarse_level_validation(lib):
     pc0 = cp0.c()
     st = lib.mg_coarse_smooth_testvecs(ctypes.byref(pc0), None, None, None, None, None, 0, None)
     assert st == 1 and b"mr_iters" in lib.mg_last_error()
+
+
+def test_solve_validation(lib):
+    """mg_solve: argument checks and workspace sizes on the host."""
+    p = mg.Problem(dims=[8, 8, 8, 8], block=[2, 2, 2, 2], m0=-0.1, n_vec=48, k=24, mr_iters=10)
+    cp = mg.CoarseProblem([4, 4, 4, 4], [2, 2, 2, 2], 24, 64, 32, 20)
+    kc = mg.KCycle()
+
+    def size(levels, nrhs=4, restart=16, **kw):
+        h = mg._hierarchy(p, None, None, None, None, None, None, None, None, None,
+                          mg.KCycle(**kw) if kw else kc)
+        h.n_levels = levels
+        if levels == 3:
+            h.second = cp.c()
+        return lib.mg_solve_workspace_size(ctypes.byref(h), nrhs, restart)
+
+    V = 4096
+    s1, s2, s3 = size(1), size(2), size(3)
+    # one level: 4 + 17 fine vectors of 12 V x 4 complex64 at least
+    assert s1 >= 21 * V * 12 * 4 * 8
+    assert s2 > s1 and s3 > s1
+    assert size(2, nrhs=12) == 0 and b"nrhs" in lib.mg_last_error()
+    assert size(2, restart=0) == 0
+    assert size(2, coarsest_iters=0) == 0
+    assert size(4) == 0
+    h = mg._hierarchy(p, None, None, None, None, None, None, None, None, None, kc)
+    it = ctypes.c_int32(0)
+    rel = (ctypes.c_double * 4)()
+    st = lib.mg_solve(ctypes.byref(h), None, None, 4, 1e-5, 16, 10, ctypes.byref(it), rel, None,
+                      0, None)
+    assert st == 1
