@@ -437,7 +437,70 @@ def level2_measure(args, prob, lv, stream):
            "gpu_launches": sum(l for l, _ in kern.values()) / steps,
            "blk_flags_nonzero": int((lv2.flags.cpu().numpy() != 0).sum()),
            "sigma_decay_block0": {f"alpha{a}": sig0[a][-1] / sig0[a][0] for a in range(2)}}
+    if not args.no_solve:
+        out_solve = solve_measure(args, prob, lv, cp, lv2, stream)
+    else:
+        out_solve = None
     del lv2, q0
+    return out, out_solve
+
+
+# the solve the hierarchy serves: FGMRES on D preconditioned by the K-cycle
+SOLVE = dict(nrhs=4, tol=1e-5, restart=16, max_iters=200, b_seed=23, conventional_m=24)
+
+
+def solve_measure(args, prob, lv, cp, lv2, stream):
+    """Solve D x = b (4 seeded Gaussian right-hand sides, relative tolerance
+    1e-5, FGMRES(16)) with the three- and two-level K-cycle over the level's
+    own hierarchy, and with the two-level hierarchy of the conventional setup
+    (k = m' = 24 test vectors, no truncation) for the paper's comparison of
+    iteration counts.  Wall-clock seconds of the whole call (it synchronises
+    at every Krylov step)."""
+    import time
+
+    import torch
+
+    from paper_2502_03091_gb300 import mg
+
+    shape = (prob.volume, 4, 3, SOLVE["nrhs"])
+    gen = torch.Generator(device="cuda").manual_seed(SOLVE["b_seed"])
+    b = torch.complex(torch.randn(shape, device="cuda", generator=gen),
+                      torch.randn(shape, device="cuda", generator=gen))
+    x = torch.empty_like(b)
+    fp = mg.Problem(dims=prob.dims, block=prob.block, m0=prob.m0, n_vec=prob.n_vec, k=prob.k,
+                    mr_iters=prob.mr_iters, csw=prob.csw, xi=prob.xi)
+    kc = mg.KCycle()
+
+    def run(levels, P, X, Y, tag):
+        kw = dict(P=P, X=X, Y=Y)
+        if levels == 3:
+            kw.update(second=cp, P2=lv2.P, X2=lv2.X2, Y2=lv2.Y2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, rel = mg.mg_solve(fp, lv.U, lv.C, b, x, SOLVE["tol"], SOLVE["restart"],
+                                 SOLVE["max_iters"], kcycle=kc, stream=stream, **kw)
+        dt = time.perf_counter() - t0
+        return {"setup": tag, "levels": levels, "outer_steps": steps, "s": dt,
+                "relres_max": float(rel.max())}
+
+    out = {"nrhs": SOLVE["nrhs"], "tol": SOLVE["tol"], "restart": SOLVE["restart"],
+           "kcycle": {"nu_pre": kc.nu_pre, "nu_post": kc.nu_post,
+                      "kcycle_iters": kc.kcycle_iters, "coarsest_iters": kc.coarsest_iters},
+           "dtype": "f32", "runs": []}
+    run(3, lv.P, lv.X, lv.Y, "warm-up")
+    out["runs"].append(run(3, lv.P, lv.X, lv.Y, f"chiral rank-k (m'={prob.n_vec}, k={prob.k})"
+                           f" + level 2 (m={cp.n_vec}, k={cp.k})"))
+    out["runs"].append(run(2, lv.P, lv.X, lv.Y, f"chiral rank-k (m'={prob.n_vec}, k={prob.k})"))
+    # conventional setup: k = m' test vectors, the same smoother, no truncation
+    mc = SOLVE["conventional_m"]
+    pc = mg.Problem(dims=prob.dims, block=prob.block, m0=prob.m0, n_vec=mc, k=mc,
+                    mr_iters=prob.mr_iters, csw=prob.csw, xi=prob.xi,
+                    precision=prob.precision)
+    lvc = mg.Level.allocate(pc, lv.U, lv.C, lv.psi0[..., :mc].contiguous())
+    lvc.run(stream)
+    mg.mg_sync_status(stream)
+    out["runs"].append(run(2, lvc.P, lvc.X, lvc.Y, f"conventional (k = m' = {mc})"))
+    del lvc, b, x
     return out
 
 
@@ -520,7 +583,7 @@ def _measure(args, w, prec, rep, U_host, psi0, level2=False):
     res = dict(ms=ms, kern=kern, clocks=clocks, flags=int((flags != 0).sum()), e2e_ms=e2e_ms,
                e2e_steps=e2e_steps, h2d=h2d, d2h=d2h, sigma_decay=decay)
     if level2:
-        res["level2"] = level2_measure(args, prob, lv, stream)
+        res["level2"], res["solve"] = level2_measure(args, prob, lv, stream)
     del lv, psi0_host, X_host, Y_host, s_host, U, C
     torch.cuda.empty_cache()
     return res
@@ -736,6 +799,8 @@ def run_ours(args, w):
             "blk_flags_nonzero": q["flags"]}
     if "level2" in r:
         out["level2"] = r["level2"]
+    if r.get("solve"):
+        out["solve"] = r["solve"]
     if world == 1 and not args.no_accuracy and len(precs) == 2:
         out["accuracy"] = accuracy_check(w)
     if world == 1 and not args.no_batch:
@@ -791,6 +856,8 @@ def main():
                     help="skip the 24-hierarchy batched-setup measurement")
     ap.add_argument("--no-level2", action="store_true",
                     help="skip the second level built on the first level's D_c")
+    ap.add_argument("--no-solve", action="store_true",
+                    help="skip the K-cycle solves on the built hierarchy")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the lowest-16 eigenvalue check against the oracle")
     args = ap.parse_args()
