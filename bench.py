@@ -449,6 +449,37 @@ def level2_measure(args, prob, lv, stream):
 SOLVE = dict(nrhs=4, tol=1e-5, restart=16, max_iters=200, b_seed=23, conventional_m=24)
 
 
+def _solve_rhs(prob):
+    import torch
+    shape = (prob.volume, 4, 3, SOLVE["nrhs"])
+    gen = torch.Generator(device="cuda").manual_seed(SOLVE["b_seed"])
+    b = torch.complex(torch.randn(shape, device="cuda", generator=gen),
+                      torch.randn(shape, device="cuda", generator=gen))
+    return b, torch.empty_like(b)
+
+
+def _solve_run(prob, lv, levels, P, X, Y, b, x, tag, stream, cp=None, lv2=None):
+    """One mg_solve call on the level's fine operator (FP32), wall-clock timed."""
+    import time
+
+    import torch
+
+    from paper_2502_03091_gb300 import mg
+
+    fp = mg.Problem(dims=prob.dims, block=prob.block, m0=prob.m0, n_vec=prob.n_vec, k=prob.k,
+                    mr_iters=prob.mr_iters, csw=prob.csw, xi=prob.xi)
+    kw = dict(P=P, X=X, Y=Y)
+    if levels == 3:
+        kw.update(second=cp, P2=lv2.P, X2=lv2.X2, Y2=lv2.Y2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, rel = mg.mg_solve(fp, lv.U, lv.C, b, x, SOLVE["tol"], SOLVE["restart"],
+                             SOLVE["max_iters"], kcycle=mg.KCycle(), stream=stream, **kw)
+    dt = time.perf_counter() - t0
+    return {"setup": tag, "levels": levels, "outer_steps": steps, "s": dt,
+            "relres_max": float(rel.max())}
+
+
 def solve_measure(args, prob, lv, cp, lv2, stream):
     """Solve D x = b (4 seeded Gaussian right-hand sides, relative tolerance
     1e-5, FGMRES(16)) with the three- and two-level K-cycle over the level's
@@ -456,32 +487,13 @@ def solve_measure(args, prob, lv, cp, lv2, stream):
     (k = m' = 24 test vectors, no truncation) for the paper's comparison of
     iteration counts.  Wall-clock seconds of the whole call (it synchronises
     at every Krylov step)."""
-    import time
-
-    import torch
-
     from paper_2502_03091_gb300 import mg
 
-    shape = (prob.volume, 4, 3, SOLVE["nrhs"])
-    gen = torch.Generator(device="cuda").manual_seed(SOLVE["b_seed"])
-    b = torch.complex(torch.randn(shape, device="cuda", generator=gen),
-                      torch.randn(shape, device="cuda", generator=gen))
-    x = torch.empty_like(b)
-    fp = mg.Problem(dims=prob.dims, block=prob.block, m0=prob.m0, n_vec=prob.n_vec, k=prob.k,
-                    mr_iters=prob.mr_iters, csw=prob.csw, xi=prob.xi)
     kc = mg.KCycle()
+    b, x = _solve_rhs(prob)
 
     def run(levels, P, X, Y, tag):
-        kw = dict(P=P, X=X, Y=Y)
-        if levels == 3:
-            kw.update(second=cp, P2=lv2.P, X2=lv2.X2, Y2=lv2.Y2)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        steps, rel = mg.mg_solve(fp, lv.U, lv.C, b, x, SOLVE["tol"], SOLVE["restart"],
-                                 SOLVE["max_iters"], kcycle=kc, stream=stream, **kw)
-        dt = time.perf_counter() - t0
-        return {"setup": tag, "levels": levels, "outer_steps": steps, "s": dt,
-                "relres_max": float(rel.max())}
+        return _solve_run(prob, lv, levels, P, X, Y, b, x, tag, stream, cp, lv2)
 
     out = {"nrhs": SOLVE["nrhs"], "tol": SOLVE["tol"], "restart": SOLVE["restart"],
            "kcycle": {"nu_pre": kc.nu_pre, "nu_post": kc.nu_post,
@@ -584,6 +596,14 @@ def _measure(args, w, prec, rep, U_host, psi0, level2=False):
                e2e_steps=e2e_steps, h2d=h2d, d2h=d2h, sigma_decay=decay)
     if level2:
         res["level2"], res["solve"] = level2_measure(args, prob, lv, stream)
+    elif not args.no_solve and not args.no_level2:
+        # the same two-level solve on this precision's hierarchy: the quality of
+        # the coarse space measured by what it is for
+        b, x = _solve_rhs(prob)
+        res["solve_2level"] = _solve_run(prob, lv, 2, lv.P, lv.X, lv.Y, b, x,
+                                         f"chiral rank-k (m'={prob.n_vec}, k={prob.k}), "
+                                         f"{prec} setup", stream)
+        del b, x
     del lv, psi0_host, X_host, Y_host, s_host, U, C
     torch.cuda.empty_cache()
     return res
@@ -797,6 +817,8 @@ def run_ours(args, w):
             "dslash": ds, "stages": {n: v["ms_per_step"] for n, v in st.items()},
             "gpu_launches": sum(l for l, _ in q["kern"].values()), "clocks": q["clocks"],
             "blk_flags_nonzero": q["flags"]}
+        if q.get("solve_2level"):
+            out["fp32_plain" if p == "fp32" else p]["solve_2level"] = q["solve_2level"]
     if "level2" in r:
         out["level2"] = r["level2"]
     if r.get("solve"):
