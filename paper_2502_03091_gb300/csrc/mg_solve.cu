@@ -138,6 +138,42 @@ __global__ void __launch_bounds__(kT) axpby_kernel(float2* out, const float2* x,
   }
 }
 
+// w[r][c] += sign * sum_{i < na} h[i][c] A_i[r][c], coefficients from FP64 inner products
+__global__ void __launch_bounds__(kT) combo_d_kernel(float2* w, const float2* __restrict__ A,
+                                                     long astride, int na,
+                                                     const double2* __restrict__ h, float sign,
+                                                     long n, int nrhs) {
+  __shared__ float2 cs[kMaxKrylov * 64];
+  for (int i = threadIdx.x; i < na * nrhs; i += blockDim.x)
+    cs[i] = make_float2(sign * (float)h[i].x, sign * (float)h[i].y);
+  __syncthreads();
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % nrhs);
+    float2 acc = w[idx];
+    for (int i = 0; i < na; ++i) cfma(acc, cs[i * nrhs + c], __ldg(A + i * astride + idx));
+    w[idx] = acc;
+  }
+}
+
+// out[c] = 1 / sqrt(nn[c].x) (0 if nn[c].x <= 0), as a complex scale
+__global__ void inv_norm_kernel(const double2* __restrict__ nn, float2* out, int n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) out[c] = make_float2(nn[c].x > 0 ? (float)(1.0 / sqrt(nn[c].x)) : 0.f, 0.f);
+}
+
+// MR step length a = <w, r> / <w, w> per column (0 if <w, w> = 0); out a and -a
+__global__ void mr_coef_kernel(const double2* __restrict__ wr, const double2* __restrict__ ww,
+                               float2* a, float2* ma, int n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const double d = ww[c].x;
+  const float2 v = d > 0 ? make_float2((float)(wr[c].x / d), (float)(wr[c].y / d))
+                         : make_float2(0.f, 0.f);
+  a[c] = v;
+  ma[c] = make_float2(-v.x, -v.y);
+}
+
 // ---------------------------------------------------------------------------
 // transfers between level l (lattice L, aggregates b, rps rows per site and
 // chirality) and level l+1 (kn columns per chirality of P)
@@ -227,6 +263,11 @@ struct Lvl {
   bool flexible = false;
   float2 *ts = nullptr, *tw = nullptr, *tx = nullptr, *mr_r = nullptr, *mr_w = nullptr;
   float2 *rhs = nullptr, *sol = nullptr, *V = nullptr, *Z = nullptr, *kw = nullptr;
+  // device results of the Krylov cycle on this level: per step j the two
+  // Gram-Schmidt passes' inner products and |w|^2, laid out
+  // hdev[j][2 (kdim + 1) + 1][nrhs]; the start norm; the column scales
+  double2 *hdev = nullptr, *beta2 = nullptr, *mrres = nullptr;
+  float2 *scale = nullptr, *mra = nullptr;
 };
 
 struct Plan {
@@ -236,31 +277,38 @@ struct Plan {
   double2* part = nullptr;
   double2* dout = nullptr;
   float2* coef = nullptr;
+  float2* ones = nullptr;   // [2][nrhs]: 1, then -1
   size_t bytes = 0;
 };
 
 class Solver {
  public:
-  Solver(Plan& p, const mg_hierarchy& h, cudaStream_t s) : P_(p), h_(h), s_(s), n_(p.nrhs) {
-    one_.assign(n_, cplx(1, 0));
-    mone_.assign(n_, cplx(-1, 0));
-  }
+  Solver(Plan& p, const mg_hierarchy& h, cudaStream_t s) : P_(p), h_(h), s_(s), n_(p.nrhs) {}
 
   cudaError_t solve(const float2* b, float2* x, double tol, int max_iters, int* iters,
                     double* relres) {
-    int steps = 0;
-    cudaError_t e = krylov(0, b, x, P_.lv.size() > 1, tol, max_iters, &steps);
+    // constant column scales 1 and -1
+    std::vector<float2> ones(2 * n_);
+    for (int c = 0; c < n_; ++c) {
+      ones[c] = make_float2(1.f, 0.f);
+      ones[n_ + c] = make_float2(-1.f, 0.f);
+    }
+    cudaError_t e = cudaMemcpyAsync(P_.ones, ones.data(), sizeof(float2) * ones.size(),
+                                    cudaMemcpyHostToDevice, s_);
     if (e != cudaSuccess) return e;
+    int steps = 0;
+    if ((e = krylov(0, b, x, P_.lv.size() > 1, tol, max_iters, &steps)) != cudaSuccess) return e;
     *iters = steps;
     // true relative residual per system
     Lvl& L = P_.lv[0];
     if ((e = apply(0, x, L.tw)) != cudaSuccess) return e;
-    if ((e = axpby(L.ts, b, one_, L.tw, mone_, L.R)) != cudaSuccess) return e;
-    std::vector<cplx> rr, bb;
-    if ((e = dots(L.ts, 0, 1, L.ts, L.R, rr)) != cudaSuccess) return e;
-    if ((e = dots(b, 0, 1, b, L.R, bb)) != cudaSuccess) return e;
+    if ((e = axpby(L.ts, b, one(), L.tw, mone(), L.R)) != cudaSuccess) return e;
+    if ((e = dots(L.ts, 0, 1, L.ts, L.R, L.mrres)) != cudaSuccess) return e;
+    if ((e = dots(b, 0, 1, b, L.R, L.mrres + n_)) != cudaSuccess) return e;
+    std::vector<double2> rb(2 * n_);
+    if ((e = fetch(rb, L.mrres)) != cudaSuccess) return e;
     for (int c = 0; c < n_; ++c)
-      relres[c] = bb[c].real() > 0 ? std::sqrt(rr[c].real() / bb[c].real()) : 0.0;
+      relres[c] = rb[n_ + c].x > 0 ? std::sqrt(std::max(0.0, rb[c].x) / rb[n_ + c].x) : 0.0;
     return cudaSuccess;
   }
 
@@ -269,59 +317,63 @@ class Solver {
   const mg_hierarchy& h_;
   cudaStream_t s_;
   int n_;
-  std::vector<cplx> one_, mone_;
   std::vector<float2> hcoef_;
 
-  cudaError_t upload(const std::vector<cplx>& v) {
-    hcoef_.resize(v.size());
-    for (size_t i = 0; i < v.size(); ++i)
-      hcoef_[i] = make_float2((float)v[i].real(), (float)v[i].imag());
-    return cudaMemcpyAsync(P_.coef, hcoef_.data(), sizeof(float2) * v.size(),
-                           cudaMemcpyHostToDevice, s_);
+  const float2* one() const { return P_.ones; }
+  const float2* mone() const { return P_.ones + n_; }
+
+  // device -> host copy of out.size() results, then wait for the stream
+  cudaError_t fetch(std::vector<double2>& out, const double2* src) {
+    cudaError_t e = cudaMemcpyAsync(out.data(), src, sizeof(double2) * out.size(),
+                                    cudaMemcpyDeviceToHost, s_);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s_);
   }
 
-  // out[i * nrhs + c] = <A_i[:, c], B[:, c]>
+  // out[i * nrhs + c] = <A_i[:, c], B[:, c]> (device, FP64)
   cudaError_t dots(const float2* A, long astride, int na, const float2* B, long R,
-                   std::vector<cplx>& out) {
+                   double2* out) {
     const int G = kT / n_;
     const int grid = (int)std::min<long>((R + G - 1) / G, kDotGrid);
-    {
-      TimedScope ts("s_dots", s_);
-      dots_kernel<<<grid, kT, 0, s_>>>(A, astride, na, B, R, n_, P_.part);
-      const int n = na * n_;
-      dots_finish<<<(n + 127) / 128, 128, 0, s_>>>(P_.part, grid, n, P_.dout);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    std::vector<double2> tmp(na * n_);
-    if ((e = cudaMemcpyAsync(tmp.data(), P_.dout, sizeof(double2) * tmp.size(),
-                             cudaMemcpyDeviceToHost, s_)) != cudaSuccess)
-      return e;
-    if ((e = cudaStreamSynchronize(s_)) != cudaSuccess) return e;
-    out.resize(tmp.size());
-    for (size_t i = 0; i < tmp.size(); ++i) out[i] = cplx(tmp[i].x, tmp[i].y);
-    return cudaSuccess;
+    TimedScope ts("s_dots", s_);
+    dots_kernel<<<grid, kT, 0, s_>>>(A, astride, na, B, R, n_, P_.part);
+    const int n = na * n_;
+    dots_finish<<<(n + 127) / 128, 128, 0, s_>>>(P_.part, grid, n, out);
+    return cudaGetLastError();
   }
 
-  // w += sum_i coef[i][c] A_i
-  cudaError_t combo(float2* w, const float2* A, long astride, int na,
-                    const std::vector<cplx>& coef, long R) {
-    cudaError_t e = upload(coef);
+  // w += sign * sum_i h[i][c] A_i  (h: device inner products)
+  cudaError_t combo_d(float2* w, const float2* A, long astride, int na, const double2* h,
+                      float sign, long R) {
+    TimedScope ts("s_combo", s_);
+    combo_d_kernel<<<grid_for(R * n_), kT, 0, s_>>>(w, A, astride, na, h, sign, R * n_, n_);
+    return cudaGetLastError();
+  }
+
+  // w += sum_i coef[i][c] A_i  (coef: host values, uploaded)
+  cudaError_t combo_h(float2* w, const float2* A, long astride, int na,
+                      const std::vector<cplx>& coef, long R) {
+    hcoef_.resize(coef.size());
+    for (size_t i = 0; i < coef.size(); ++i)
+      hcoef_[i] = make_float2((float)coef[i].real(), (float)coef[i].imag());
+    cudaError_t e = cudaMemcpyAsync(P_.coef, hcoef_.data(), sizeof(float2) * coef.size(),
+                                    cudaMemcpyHostToDevice, s_);
     if (e != cudaSuccess) return e;
     TimedScope ts("s_combo", s_);
     combo_kernel<<<grid_for(R * n_), kT, 0, s_>>>(w, A, astride, na, P_.coef, R * n_, n_);
     return cudaGetLastError();
   }
 
-  // out = a x + b y
-  cudaError_t axpby(float2* out, const float2* x, const std::vector<cplx>& a, const float2* y,
-                    const std::vector<cplx>& b, long R) {
-    std::vector<cplx> ab(a);
-    ab.insert(ab.end(), b.begin(), b.end());
-    cudaError_t e = upload(ab);
-    if (e != cudaSuccess) return e;
+  // out = a x + b y  (a, b: device column scales; y may be null)
+  cudaError_t axpby(float2* out, const float2* x, const float2* a, const float2* y,
+                    const float2* b, long R) {
     TimedScope ts("s_axpby", s_);
-    axpby_kernel<<<grid_for(R * n_), kT, 0, s_>>>(out, x, P_.coef, y, P_.coef + n_, R * n_, n_);
+    axpby_kernel<<<grid_for(R * n_), kT, 0, s_>>>(out, x, a, y, b, R * n_, n_);
+    return cudaGetLastError();
+  }
+
+  cudaError_t inv_norm(const double2* nn, float2* out) {
+    inv_norm_kernel<<<1, 64, 0, s_>>>(nn, out, n_);
     return cudaGetLastError();
   }
 
@@ -338,23 +390,20 @@ class Solver {
     return launch_stencil_apply(L.sg, L.X, L.Y, in, out, n_, s_);
   }
 
-  // x = nu MR steps on A_l x = r from x = 0
+  // x = nu MR steps on A_l x = r from x = 0 (step lengths computed on the device)
   cudaError_t mr(int l, const float2* r, float2* x, int nu) {
     Lvl& L = P_.lv[l];
     cudaError_t e;
     if ((e = zero(x, L.R)) != cudaSuccess) return e;
     if ((e = copy(L.mr_r, r, L.R)) != cudaSuccess) return e;
-    std::vector<cplx> wr, ww, a(n_), ma(n_);
     for (int t = 0; t < nu; ++t) {
       if ((e = apply(l, L.mr_r, L.mr_w)) != cudaSuccess) return e;
-      if ((e = dots(L.mr_w, 0, 1, L.mr_r, L.R, wr)) != cudaSuccess) return e;
-      if ((e = dots(L.mr_w, 0, 1, L.mr_w, L.R, ww)) != cudaSuccess) return e;
-      for (int c = 0; c < n_; ++c) {
-        a[c] = ww[c].real() > 0 ? wr[c] / ww[c].real() : cplx(0, 0);
-        ma[c] = -a[c];
-      }
-      if ((e = axpby(x, x, one_, L.mr_r, a, L.R)) != cudaSuccess) return e;
-      if ((e = axpby(L.mr_r, L.mr_r, one_, L.mr_w, ma, L.R)) != cudaSuccess) return e;
+      if ((e = dots(L.mr_w, 0, 1, L.mr_r, L.R, L.mrres)) != cudaSuccess) return e;
+      if ((e = dots(L.mr_w, 0, 1, L.mr_w, L.R, L.mrres + n_)) != cudaSuccess) return e;
+      mr_coef_kernel<<<1, 64, 0, s_>>>(L.mrres, L.mrres + n_, L.mra, L.mra + n_, n_);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = axpby(x, x, one(), L.mr_r, L.mra, L.R)) != cudaSuccess) return e;
+      if ((e = axpby(L.mr_r, L.mr_r, one(), L.mr_w, L.mra + n_, L.R)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
@@ -369,7 +418,7 @@ class Solver {
     if (h_.nu_pre > 0) {
       if ((e = mr(l, r, x, h_.nu_pre)) != cudaSuccess) return e;
       if ((e = apply(l, x, L.tw)) != cudaSuccess) return e;
-      if ((e = axpby(L.ts, r, one_, L.tw, mone_, L.R)) != cudaSuccess) return e;
+      if ((e = axpby(L.ts, r, one(), L.tw, mone(), L.R)) != cudaSuccess) return e;
       s = L.ts;
     } else if ((e = zero(x, L.R)) != cudaSuccess) {
       return e;
@@ -389,148 +438,187 @@ class Solver {
     }
     if (h_.nu_post > 0) {
       if ((e = apply(l, x, L.tw)) != cudaSuccess) return e;
-      if ((e = axpby(L.ts, r, one_, L.tw, mone_, L.R)) != cudaSuccess) return e;
+      if ((e = axpby(L.ts, r, one(), L.tw, mone(), L.R)) != cudaSuccess) return e;
       if ((e = mr(l, L.ts, L.tx, h_.nu_post)) != cudaSuccess) return e;
-      if ((e = axpby(x, x, one_, L.tx, one_, L.R)) != cudaSuccess) return e;
+      if ((e = axpby(x, x, one(), L.tx, one(), L.R)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
 
-  // (F)GMRES on level l from x = 0.  tol < 0: one cycle of L.kdim steps.
-  // Otherwise cycles of L.kdim steps until every column's least-squares
-  // residual is <= tol |b_c| or max_iters steps are done.
+  // Per-column Arnoldi bookkeeping on the host: step j's inner products
+  // (two Gram-Schmidt passes and |w|^2, from the device) go into the
+  // Hessenberg column, previous Givens rotations are applied and a new one
+  // zeroes H[j+1][j]; returns whether every column has met the tolerance.
+  struct Hess {
+    int m, n;
+    std::vector<cplx> H, g, sn;
+    std::vector<double> cs;
+    std::vector<int> kc;  // -1: growing; else the column's number of valid steps
+    void reset(int m_, int n_, const std::vector<double2>& beta2) {
+      m = m_;
+      n = n_;
+      H.assign((size_t)n * (m + 1) * m, 0.0);
+      g.assign((size_t)n * (m + 1), 0.0);
+      sn.assign((size_t)n * m, 0.0);
+      cs.assign((size_t)n * m, 0.0);
+      kc.assign(n, 0);
+      for (int c = 0; c < n; ++c) {
+        const double beta = std::sqrt(std::max(0.0, beta2[c].x));
+        g[(size_t)c * (m + 1)] = beta;
+        kc[c] = beta > 0 ? -1 : 0;
+      }
+    }
+    cplx& h(int c, int i, int j) { return H[(size_t)c * (m + 1) * m + i + (size_t)(m + 1) * j]; }
+    double res(int c, int j) const { return std::abs(g[(size_t)c * (m + 1) + j]); }
+    // hj: [2 (m + 1) + 1][n] device layout of step j
+    void step(int j, const double2* hj) {
+      for (int c = 0; c < n; ++c) {
+        if (kc[c] >= 0) continue;
+        const double hn = std::sqrt(std::max(0.0, hj[(size_t)2 * (m + 1) * n + c].x));
+        for (int i = 0; i <= j; ++i) {
+          const double2 a1 = hj[(size_t)i * n + c], a2 = hj[(size_t)(m + 1 + i) * n + c];
+          h(c, i, j) = cplx(a1.x + a2.x, a1.y + a2.y);
+        }
+        h(c, j + 1, j) = hn;
+        for (int i = 0; i < j; ++i) {
+          cplx& a = h(c, i, j);
+          cplx& b = h(c, i + 1, j);
+          const double ci = cs[(size_t)c * m + i];
+          const cplx si = sn[(size_t)c * m + i];
+          const cplx t0 = ci * a + si * b;
+          const cplx t1 = -std::conj(si) * a + ci * b;
+          a = t0;
+          b = t1;
+        }
+        cplx& a = h(c, j, j);
+        const double aa = std::abs(a);
+        double cj;
+        cplx sj;
+        if (hn == 0.0) {
+          cj = 1.0;
+          sj = 0.0;
+        } else if (aa == 0.0) {
+          cj = 0.0;
+          sj = 1.0;
+        } else {
+          const double t = std::sqrt(aa * aa + hn * hn);
+          cj = aa / t;
+          sj = (a / aa) * hn / t;
+        }
+        cs[(size_t)c * m + j] = cj;
+        sn[(size_t)c * m + j] = sj;
+        a = cj * a + sj * hn;
+        h(c, j + 1, j) = 0.0;
+        cplx* gc = &g[(size_t)c * (m + 1)];
+        gc[j + 1] = -std::conj(sj) * gc[j];
+        gc[j] = cj * gc[j];
+        if (hn == 0.0) kc[c] = j + 1;  // breakdown: exact in this column
+      }
+    }
+    bool converged(int j, double tol, const std::vector<double>& bn) const {
+      for (int c = 0; c < n; ++c)
+        if (!(kc[c] >= 0 || res(c, j + 1) <= tol * bn[c])) return false;
+      return true;
+    }
+    // y_c = H_c^-1 g_c over the column's valid steps, as [steps][n]
+    std::vector<cplx> solve(int steps) {
+      std::vector<cplx> coef((size_t)steps * n, 0.0);
+      for (int c = 0; c < n; ++c) {
+        const int k = kc[c] < 0 ? steps : std::min(kc[c], steps);
+        std::vector<cplx> y(k);
+        for (int i = k - 1; i >= 0; --i) {
+          cplx acc = g[(size_t)c * (m + 1) + i];
+          for (int q = i + 1; q < k; ++q) acc -= h(c, i, q) * y[q];
+          const cplx d = h(c, i, i);
+          y[i] = std::abs(d) > 0 ? acc / d : 0.0;
+        }
+        for (int i = 0; i < k; ++i) coef[(size_t)i * n + c] = y[i];
+      }
+      return coef;
+    }
+  };
+
+  // (F)GMRES on level l from x = 0.  tol < 0: one cycle of L.kdim steps, the
+  // stream synchronised once at its end.  Otherwise cycles of L.kdim steps
+  // until every column's least-squares residual is <= tol |b_c| or max_iters
+  // steps are done, synchronised once per step for the test.
   cudaError_t krylov(int l, const float2* b, float2* x, bool flexible, double tol, int max_iters,
                      int* steps_out) {
     Lvl& L = P_.lv[l];
     const long R = L.R, vs = R * n_;
     const int m = L.kdim;
+    const size_t hstride = (size_t)(2 * (m + 1) + 1) * n_;  // doubles2 per step in hdev
     cudaError_t e;
-    std::vector<cplx> bb;
-    if ((e = dots(b, 0, 1, b, R, bb)) != cudaSuccess) return e;
-    std::vector<double> bn(n_);
-    for (int c = 0; c < n_; ++c) bn[c] = std::sqrt(std::max(0.0, bb[c].real()));
+    std::vector<double> bn(n_, 0.0);
+    if (tol >= 0) {
+      std::vector<double2> bb(n_);
+      if ((e = dots(b, 0, 1, b, R, L.beta2)) != cudaSuccess) return e;
+      if ((e = fetch(bb, L.beta2)) != cudaSuccess) return e;
+      for (int c = 0; c < n_; ++c) bn[c] = std::sqrt(std::max(0.0, bb[c].x));
+    }
     if ((e = zero(x, R)) != cudaSuccess) return e;
     int total = 0;
     bool first = true;
-    std::vector<cplx> H((size_t)n_ * (m + 1) * m), g((size_t)n_ * (m + 1)), sn((size_t)n_ * m);
-    std::vector<double> cs((size_t)n_ * m);
-    std::vector<int> kc(n_);
-    std::vector<cplx> h, h2, hn2, coef, scale(n_);
+    Hess hs;
+    std::vector<double2> beta2(n_), hbuf;
     for (;;) {
-      // V_0 = (b - A x) / beta
+      // V_0 = (b - A x) / |b - A x|
       if (first) {
         if ((e = copy(L.V, b, R)) != cudaSuccess) return e;
       } else {
         if ((e = apply(l, x, L.kw)) != cudaSuccess) return e;
-        if ((e = axpby(L.V, b, one_, L.kw, mone_, R)) != cudaSuccess) return e;
+        if ((e = axpby(L.V, b, one(), L.kw, mone(), R)) != cudaSuccess) return e;
       }
-      std::vector<cplx> beta2;
-      if ((e = dots(L.V, 0, 1, L.V, R, beta2)) != cudaSuccess) return e;
-      std::fill(H.begin(), H.end(), cplx(0, 0));
-      std::fill(g.begin(), g.end(), cplx(0, 0));
-      for (int c = 0; c < n_; ++c) {
-        const double beta = std::sqrt(std::max(0.0, beta2[c].real()));
-        g[(size_t)c * (m + 1)] = beta;
-        scale[c] = beta > 0 ? cplx(1.0 / beta, 0) : cplx(0, 0);
-        kc[c] = beta > 0 ? -1 : 0;  // -1: still growing; else the column's valid steps
+      if ((e = dots(L.V, 0, 1, L.V, R, L.beta2)) != cudaSuccess) return e;
+      if ((e = inv_norm(L.beta2, L.scale)) != cudaSuccess) return e;
+      if ((e = axpby(L.V, L.V, L.scale, nullptr, L.scale, R)) != cudaSuccess) return e;
+      if (tol >= 0) {
+        if ((e = fetch(beta2, L.beta2)) != cudaSuccess) return e;
+        hs.reset(m, n_, beta2);
       }
-      if ((e = axpby(L.V, L.V, scale, nullptr, scale, R)) != cudaSuccess) return e;
       const int jmax = std::min(m, max_iters - total);
       int steps = 0;
       for (int j = 0; j < jmax; ++j) {
         float2* vj = L.V + j * vs;
         float2* zj = flexible ? L.Z + j * vs : vj;
+        double2* hj = L.hdev + (size_t)j * hstride;
         if (flexible && (e = precond(l, vj, zj)) != cudaSuccess) return e;
         if ((e = apply(l, zj, L.kw)) != cudaSuccess) return e;
-        std::vector<cplx> hsum((size_t)(j + 1) * n_, cplx(0, 0));
         for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-          if ((e = dots(L.V, vs, j + 1, L.kw, R, h)) != cudaSuccess) return e;
-          coef.resize(h.size());
-          for (size_t i = 0; i < h.size(); ++i) {
-            coef[i] = -h[i];
-            hsum[i] += h[i];
-          }
-          if ((e = combo(L.kw, L.V, vs, j + 1, coef, R)) != cudaSuccess) return e;
+          double2* hp = hj + (size_t)pass * (m + 1) * n_;
+          if ((e = dots(L.V, vs, j + 1, L.kw, R, hp)) != cudaSuccess) return e;
+          if ((e = combo_d(L.kw, L.V, vs, j + 1, hp, -1.f, R)) != cudaSuccess) return e;
         }
+        double2* hn2 = hj + (size_t)2 * (m + 1) * n_;
         if ((e = dots(L.kw, 0, 1, L.kw, R, hn2)) != cudaSuccess) return e;
-        bool all_done = true;
-        for (int c = 0; c < n_; ++c) {
-          const double hn = std::sqrt(std::max(0.0, hn2[c].real()));
-          cplx* Hc = &H[(size_t)c * (m + 1) * m];  // column-major: Hc[i + (m+1) j]
-          cplx* gc = &g[(size_t)c * (m + 1)];
-          if (kc[c] < 0) {
-            for (int i = 0; i <= j; ++i) Hc[i + (size_t)(m + 1) * j] = hsum[(size_t)i * n_ + c];
-            Hc[j + 1 + (size_t)(m + 1) * j] = hn;
-            // previous rotations, then a new one that zeroes H[j+1][j]
-            for (int i = 0; i < j; ++i) {
-              cplx& a = Hc[i + (size_t)(m + 1) * j];
-              cplx& bq = Hc[i + 1 + (size_t)(m + 1) * j];
-              const double ci = cs[(size_t)c * m + i];
-              const cplx si = sn[(size_t)c * m + i];
-              const cplx t0 = ci * a + si * bq;
-              const cplx t1 = -std::conj(si) * a + ci * bq;
-              a = t0;
-              bq = t1;
-            }
-            cplx& a = Hc[j + (size_t)(m + 1) * j];
-            const double bj = hn;
-            double cj;
-            cplx sj;
-            const double aa = std::abs(a);
-            if (bj == 0.0) {
-              cj = 1.0;
-              sj = 0.0;
-            } else if (aa == 0.0) {
-              cj = 0.0;
-              sj = 1.0;
-            } else {
-              const double t = std::sqrt(aa * aa + bj * bj);
-              cj = aa / t;
-              sj = (a / aa) * bj / t;
-            }
-            cs[(size_t)c * m + j] = cj;
-            sn[(size_t)c * m + j] = sj;
-            a = cj * a + sj * bj;
-            Hc[j + 1 + (size_t)(m + 1) * j] = 0.0;
-            gc[j + 1] = -std::conj(sj) * gc[j];
-            gc[j] = cj * gc[j];
-            if (hn == 0.0) kc[c] = j + 1;  // breakdown: exact in this column
-          }
-          scale[c] = (kc[c] < 0 && hn > 0) ? cplx(1.0 / hn, 0) : cplx(0, 0);
-          const bool conv = kc[c] >= 0 || (tol >= 0 && std::abs(gc[j + 1]) <= tol * bn[c]);
-          all_done = all_done && conv;
-        }
-        steps = j + 1;
-        if ((e = axpby(L.V + (j + 1) * vs, L.kw, scale, nullptr, scale, R)) != cudaSuccess)
+        if ((e = inv_norm(hn2, L.scale)) != cudaSuccess) return e;
+        if ((e = axpby(L.V + (j + 1) * vs, L.kw, L.scale, nullptr, L.scale, R)) != cudaSuccess)
           return e;
-        if (tol >= 0 && all_done) break;
-      }
-      // y_c = H_c^-1 g_c (upper triangular after the rotations); x += Z y
-      coef.assign((size_t)steps * n_, cplx(0, 0));
-      for (int c = 0; c < n_; ++c) {
-        const int k = kc[c] < 0 ? steps : std::min(kc[c], steps);
-        const cplx* Hc = &H[(size_t)c * (m + 1) * m];
-        const cplx* gc = &g[(size_t)c * (m + 1)];
-        std::vector<cplx> y(k);
-        for (int i = k - 1; i >= 0; --i) {
-          cplx s = gc[i];
-          for (int q = i + 1; q < k; ++q) s -= Hc[i + (size_t)(m + 1) * q] * y[q];
-          const cplx d = Hc[i + (size_t)(m + 1) * i];
-          y[i] = std::abs(d) > 0 ? s / d : cplx(0, 0);
+        steps = j + 1;
+        if (tol >= 0) {
+          hbuf.resize(hstride);
+          if ((e = fetch(hbuf, hj)) != cudaSuccess) return e;
+          hs.step(j, hbuf.data());
+          if (hs.converged(j, tol, bn)) break;
         }
-        for (int i = 0; i < k; ++i) coef[(size_t)i * n_ + c] = y[i];
+      }
+      if (tol < 0) {
+        // one fetch for the whole fixed-length cycle
+        hbuf.resize(hstride * steps);
+        if ((e = cudaMemcpyAsync(beta2.data(), L.beta2, sizeof(double2) * n_,
+                                 cudaMemcpyDeviceToHost, s_)) != cudaSuccess)
+          return e;
+        if (steps > 0 && (e = fetch(hbuf, L.hdev)) != cudaSuccess) return e;
+        if (steps == 0 && (e = cudaStreamSynchronize(s_)) != cudaSuccess) return e;
+        hs.reset(m, n_, beta2);
+        for (int j = 0; j < steps; ++j) hs.step(j, hbuf.data() + (size_t)j * hstride);
       }
       if (steps > 0 &&
-          (e = combo(x, flexible ? L.Z : L.V, vs, steps, coef, R)) != cudaSuccess)
+          (e = combo_h(x, flexible ? L.Z : L.V, vs, steps, hs.solve(steps), R)) != cudaSuccess)
         return e;
       total += steps;
       if (tol < 0) break;
-      bool done = true;
-      for (int c = 0; c < n_; ++c) {
-        const cplx* gc = &g[(size_t)c * (m + 1)];
-        if (!(kc[c] >= 0 || std::abs(gc[steps]) <= tol * bn[c])) done = false;
-      }
-      if (done || total >= max_iters || steps == 0) break;
+      if (hs.converged(steps - 1, tol, bn) || total >= max_iters || steps == 0) break;
       first = false;
     }
     *steps_out = total;
@@ -649,6 +737,7 @@ mg_status make_plan(const mg_hierarchy* h, int nrhs, int restart, Plan& p, char*
   p.part = reinterpret_cast<double2*>(take(sizeof(double2) * kDotGrid * (kMaxKrylov + 1) * 64));
   p.dout = reinterpret_cast<double2*>(take(sizeof(double2) * (kMaxKrylov + 1) * 64));
   p.coef = reinterpret_cast<float2*>(take(sizeof(float2) * (kMaxKrylov + 1) * 64 * 2));
+  p.ones = reinterpret_cast<float2*>(take(sizeof(float2) * 2 * 64));
   for (size_t l = 0; l < p.lv.size(); ++l) {
     Lvl& L = p.lv[l];
     const size_t vb = sizeof(float2) * (size_t)L.R * nrhs;
@@ -663,6 +752,12 @@ mg_status make_plan(const mg_hierarchy* h, int nrhs, int restart, Plan& p, char*
       L.sol = vec();
     }
     L.kw = vec();
+    L.hdev = reinterpret_cast<double2*>(
+        take(sizeof(double2) * (size_t)L.kdim * (2 * (L.kdim + 1) + 1) * nrhs));
+    L.beta2 = reinterpret_cast<double2*>(take(sizeof(double2) * nrhs));
+    L.mrres = reinterpret_cast<double2*>(take(sizeof(double2) * 2 * nrhs));
+    L.scale = reinterpret_cast<float2*>(take(sizeof(float2) * nrhs));
+    L.mra = reinterpret_cast<float2*>(take(sizeof(float2) * 2 * nrhs));
     L.V = reinterpret_cast<float2*>(take(vb * (L.kdim + 1)));
     if (L.flexible) L.Z = reinterpret_cast<float2*>(take(vb * L.kdim));
   }
