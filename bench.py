@@ -458,7 +458,7 @@ def _solve_rhs(prob):
     return b, torch.empty_like(b)
 
 
-def _solve_run(prob, lv, levels, P, X, Y, b, x, tag, stream, cp=None, lv2=None):
+def _solve_run(prob, lv, levels, P, X, Y, b, x, tag, stream, cp=None, lv2=None, timed=False):
     """One mg_solve call on the level's fine operator (FP32), wall-clock timed."""
     import time
 
@@ -476,8 +476,21 @@ def _solve_run(prob, lv, levels, P, X, Y, b, x, tag, stream, cp=None, lv2=None):
     steps, rel = mg.mg_solve(fp, lv.U, lv.C, b, x, SOLVE["tol"], SOLVE["restart"],
                              SOLVE["max_iters"], kcycle=mg.KCycle(), stream=stream, **kw)
     dt = time.perf_counter() - t0
-    return {"setup": tag, "levels": levels, "outer_steps": steps, "s": dt,
-            "relres_max": float(rel.max())}
+    out = {"setup": tag, "levels": levels, "outer_steps": steps, "s": dt,
+           "relres_max": float(rel.max())}
+    if timed:
+        # the same solve again with per-kernel CUDA-event timing (identical
+        # arithmetic; the events add a little host work per launch)
+        mg.mg_timing_enable(True)
+        mg.mg_timing_read()
+        mg.mg_solve(fp, lv.U, lv.C, b, x, SOLVE["tol"], SOLVE["restart"], SOLVE["max_iters"],
+                    kcycle=mg.KCycle(), stream=stream, **kw)
+        kern = mg.mg_timing_read()
+        mg.mg_timing_enable(False)
+        out["kernel_ms"] = {n: round(t, 2) for n, (_, t) in
+                            sorted(kern.items(), key=lambda kv: -kv[1][1])}
+        out["launches"] = sum(n for n, _ in kern.values())
+    return out
 
 
 def solve_measure(args, prob, lv, cp, lv2, stream):
@@ -492,8 +505,8 @@ def solve_measure(args, prob, lv, cp, lv2, stream):
     kc = mg.KCycle()
     b, x = _solve_rhs(prob)
 
-    def run(levels, P, X, Y, tag):
-        return _solve_run(prob, lv, levels, P, X, Y, b, x, tag, stream, cp, lv2)
+    def run(levels, P, X, Y, tag, timed=False):
+        return _solve_run(prob, lv, levels, P, X, Y, b, x, tag, stream, cp, lv2, timed)
 
     out = {"nrhs": SOLVE["nrhs"], "tol": SOLVE["tol"], "restart": SOLVE["restart"],
            "kcycle": {"nu_pre": kc.nu_pre, "nu_post": kc.nu_post,
@@ -502,7 +515,8 @@ def solve_measure(args, prob, lv, cp, lv2, stream):
     run(3, lv.P, lv.X, lv.Y, "warm-up")
     out["runs"].append(run(3, lv.P, lv.X, lv.Y, f"chiral rank-k (m'={prob.n_vec}, k={prob.k})"
                            f" + level 2 (m={cp.n_vec}, k={cp.k})"))
-    out["runs"].append(run(2, lv.P, lv.X, lv.Y, f"chiral rank-k (m'={prob.n_vec}, k={prob.k})"))
+    out["runs"].append(run(2, lv.P, lv.X, lv.Y, f"chiral rank-k (m'={prob.n_vec}, k={prob.k})",
+                           timed=True))
     # conventional setup: k = m' test vectors, the same smoother, no truncation
     mc = SOLVE["conventional_m"]
     pc = mg.Problem(dims=prob.dims, block=prob.block, m0=prob.m0, n_vec=mc, k=mc,
