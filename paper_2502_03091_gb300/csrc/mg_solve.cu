@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kMaxKrylov = 64;   // longest Krylov cycle on any level
-constexpr int kDotGrid = 2 * 152;
+constexpr int kDotGrid = 4 * 152;
 
 using cplx = std::complex<double>;
 
@@ -43,30 +43,34 @@ using cplx = std::complex<double>;
 // vector kernels on R x nrhs arrays (nrhs divides 256)
 // ---------------------------------------------------------------------------
 // part[blk][i][c] = sum over the CTA's rows r of conj(A_i[r][c]) B[r][c], i < na.
-// FP32 products summed in FP32 over 32 rows, then in FP64; fixed order.
+// Eight vectors A_i per sweep over B (B is read ceil(na / 8) times); FP32
+// products summed in FP32 over 32 rows, then in FP64; fixed order.
+constexpr int kDotVec = 8;
 __global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, long astride,
                                                   int na, const float2* __restrict__ B, long R,
                                                   int nrhs, double2* part) {
   __shared__ double2 red[kT];
   const int G = kT / nrhs, c = threadIdx.x % nrhs, g = threadIdx.x / nrhs;
   const long rstep = (long)gridDim.x * G;
-  for (int i0 = 0; i0 < na; i0 += 4) {
-    double2 acc[4];
-    float2 fac[4];
+  for (int i0 = 0; i0 < na; i0 += kDotVec) {
+    const int nv = min(kDotVec, na - i0);
+    double2 acc[kDotVec];
+    float2 fac[kDotVec];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kDotVec; ++u) {
       acc[u] = make_double2(0.0, 0.0);
       fac[u] = make_float2(0.f, 0.f);
     }
     int cnt = 0;
     for (long r = (long)blockIdx.x * G + g; r < R; r += rstep) {
-      const float2 bv = __ldg(B + r * nrhs + c);
+      const long o = r * nrhs + c;
+      const float2 bv = __ldg(B + o);
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (i0 + u < na) cfmac(fac[u], __ldg(A + (i0 + u) * astride + r * nrhs + c), bv);
+      for (int u = 0; u < kDotVec; ++u)
+        if (u < nv) cfmac(fac[u], __ldg(A + (i0 + u) * astride + o), bv);
       if (++cnt == 32) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kDotVec; ++u) {
           acc[u].x += fac[u].x;
           acc[u].y += fac[u].y;
           fac[u] = make_float2(0.f, 0.f);
@@ -75,11 +79,11 @@ __global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, 
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kDotVec; ++u) {
       acc[u].x += fac[u].x;
       acc[u].y += fac[u].y;
     }
-    for (int u = 0; u < 4 && i0 + u < na; ++u) {
+    for (int u = 0; u < nv; ++u) {
       red[threadIdx.x] = acc[u];
       __syncthreads();
       if (g == 0) {
@@ -95,16 +99,29 @@ __global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, 
   }
 }
 
-// out[j] = sum over the CTAs' partials, in CTA order
-__global__ void dots_finish(const double2* __restrict__ part, int nblk, int n, double2* out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+// out[j] = sum over the CTAs' partials: one CTA of 64 threads per output,
+// each thread a strided share, then a fixed-order tree (deterministic)
+constexpr int kFinT = 64;
+__global__ void __launch_bounds__(kFinT) dots_finish(const double2* __restrict__ part, int nblk,
+                                                     int n, double2* out) {
+  __shared__ double2 red[kFinT];
+  const int j = blockIdx.x;
   double2 s = make_double2(0.0, 0.0);
-  for (int b = 0; b < nblk; ++b) {
-    s.x += part[(long)b * n + j].x;
-    s.y += part[(long)b * n + j].y;
+  for (int b = threadIdx.x; b < nblk; b += kFinT) {
+    const double2 v = part[(long)b * n + j];
+    s.x += v.x;
+    s.y += v.y;
   }
-  out[j] = s;
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = kFinT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      red[threadIdx.x].x += red[threadIdx.x + h].x;
+      red[threadIdx.x].y += red[threadIdx.x + h].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = red[0];
 }
 
 // w[r][c] += sum_{i < na} coef[i][c] A_i[r][c]
@@ -199,46 +216,102 @@ __device__ __forceinline__ int xfer_site(const Xfer& t, int j, int loc) {
 }
 
 // out[j][a kn + i][c] = sum_{x in block j} sum_{e < rps} conj(P[x][a][e][i]) v[x][a rps + e][c]
+// One CTA per block j.  Thread t: output row a kn + i = t % (2 kn), site group
+// t / (2 kn) (G groups share the block's sites); each thread keeps up to 8
+// right-hand sides in registers (one P load and two float4 loads of v per
+// term), then the groups' sums are added in a fixed order.
 __global__ void __launch_bounds__(kT) restrict_kernel(Xfer t, const float2* __restrict__ P,
                                                       const float2* __restrict__ v, float2* out) {
+  __shared__ float2 red[kT * 8];
   const int j = blockIdx.x;
-  const int nout = 2 * t.kn * t.nrhs;
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    const int c = o % t.nrhs, ai = o / t.nrhs;
-    const int a = ai / t.kn, i = ai % t.kn;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int loc = 0; loc < t.nb; ++loc) {
-      const int x = xfer_site(t, j, loc);
-      const float2* Px = P + ((long)x * 2 + a) * t.rps * t.kn + i;
-      const float2* vx = v + ((long)x * 2 * t.rps + a * t.rps) * t.nrhs + c;
-      for (int e = 0; e < t.rps; ++e) cfmac(acc, __ldg(Px + e * t.kn), __ldg(vx + e * t.nrhs));
+  const int nrow = 2 * t.kn;
+  const int G = kT / nrow;
+  const int ai = threadIdx.x % nrow, grp = threadIdx.x / nrow;
+  const bool active = grp < G;
+  const int a = ai / t.kn, i = ai % t.kn;
+  for (int c0 = 0; c0 < t.nrhs; c0 += 8) {
+    const int cw = min(8, t.nrhs - c0);  // 4 or 8
+    float2 acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+    if (active) {
+      for (int loc = grp; loc < t.nb; loc += G) {
+        const int x = xfer_site(t, j, loc);
+        const float2* Px = P + ((long)x * 2 + a) * t.rps * t.kn + i;
+        const float2* vx = v + ((long)x * 2 * t.rps + a * t.rps) * t.nrhs + c0;
+        for (int e = 0; e < t.rps; ++e) {
+          const float2 pv = __ldg(Px + e * t.kn);
+          const float4* v4 = reinterpret_cast<const float4*>(vx + (long)e * t.nrhs);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (2 * q < cw) {
+              const float4 w = __ldg(v4 + q);
+              cfmac(acc[2 * q], pv, make_float2(w.x, w.y));
+              cfmac(acc[2 * q + 1], pv, make_float2(w.z, w.w));
+            }
+        }
+      }
     }
-    out[((long)j * 2 * t.kn + ai) * t.nrhs + c] = acc;
+    __syncthreads();
+    if (active)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) red[(grp * nrow + ai) * 8 + q] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < nrow)
+      for (int q = 0; q < cw; ++q) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int g = 0; g < G; ++g) s = cadd(s, red[(g * nrow + threadIdx.x) * 8 + q]);
+        out[((long)j * nrow + threadIdx.x) * t.nrhs + c0 + q] = s;
+      }
   }
 }
 
 // fine[x][a rps + e][c] += sum_i P[x][a][e][i] vc[j(x)][a kn + i][c]
+// One thread per (site, row), up to 8 right-hand sides in registers.
 __global__ void __launch_bounds__(kT) prolong_kernel(Xfer t, const float2* __restrict__ P,
                                                      const float2* __restrict__ vc, float2* fine,
                                                      long V) {
-  const long n = V * 2 * t.rps * t.nrhs;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n;
-       idx += (long)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % t.nrhs);
-    const long xe = idx / t.nrhs;
+  const long nxe = V * 2 * t.rps;
+  for (long xe = blockIdx.x * (long)blockDim.x + threadIdx.x; xe < nxe;
+       xe += (long)gridDim.x * blockDim.x) {
     const int ae = (int)(xe % (2 * t.rps));
     const int x = (int)(xe / (2 * t.rps));
     const int a = ae / t.rps;
     int u = x;
-    const int c0 = u % t.L[0]; u /= t.L[0];
+    const int c0_ = u % t.L[0]; u /= t.L[0];
     const int c1 = u % t.L[1]; u /= t.L[1];
     const int c2 = u % t.L[2]; const int c3 = u / t.L[2];
-    const int j = c0 / t.b[0] + t.Lc[0] * (c1 / t.b[1] + t.Lc[1] * (c2 / t.b[2] + t.Lc[2] * (c3 / t.b[3])));
-    const float2* Pr = P + ((long)x * 2 * t.rps + ae) * t.kn;
-    const float2* vj = vc + ((long)j * 2 * t.kn + a * t.kn) * t.nrhs + c;
-    float2 acc = fine[idx];
-    for (int i = 0; i < t.kn; ++i) cfma(acc, __ldg(Pr + i), __ldg(vj + (long)i * t.nrhs));
-    fine[idx] = acc;
+    const int j = c0_ / t.b[0] +
+                  t.Lc[0] * (c1 / t.b[1] + t.Lc[1] * (c2 / t.b[2] + t.Lc[2] * (c3 / t.b[3])));
+    const float2* Pr = P + xe * t.kn;  // P[x][a][e][:]
+    for (int c0 = 0; c0 < t.nrhs; c0 += 8) {
+      const int cw = min(8, t.nrhs - c0);
+      float4* f4 = reinterpret_cast<float4*>(fine + xe * t.nrhs + c0);
+      float2 acc[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (2 * q < cw) w = f4[q];
+        acc[2 * q] = make_float2(w.x, w.y);
+        acc[2 * q + 1] = make_float2(w.z, w.w);
+      }
+      const float2* vj = vc + ((long)j * 2 * t.kn + a * t.kn) * t.nrhs + c0;
+      for (int i = 0; i < t.kn; ++i) {
+        const float2 p = __ldg(Pr + i);
+        const float4* v4 = reinterpret_cast<const float4*>(vj + (long)i * t.nrhs);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (2 * q < cw) {
+            const float4 w = __ldg(v4 + q);
+            cfma(acc[2 * q], p, make_float2(w.x, w.y));
+            cfma(acc[2 * q + 1], p, make_float2(w.z, w.w));
+          }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (2 * q < cw)
+          f4[q] = make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
+    }
   }
 }
 
@@ -338,7 +411,7 @@ class Solver {
     TimedScope ts("s_dots", s_);
     dots_kernel<<<grid, kT, 0, s_>>>(A, astride, na, B, R, n_, P_.part);
     const int n = na * n_;
-    dots_finish<<<(n + 127) / 128, 128, 0, s_>>>(P_.part, grid, n, out);
+    dots_finish<<<n, kFinT, 0, s_>>>(P_.part, grid, n, out);
     return cudaGetLastError();
   }
 
@@ -433,7 +506,7 @@ class Solver {
       return e;
     {
       TimedScope ts("s_prolong", s_);
-      prolong_kernel<<<grid_for(L.R * n_), kT, 0, s_>>>(L.xf, L.P, N.sol, x, L.Vsites);
+      prolong_kernel<<<grid_for(L.R), kT, 0, s_>>>(L.xf, L.P, N.sol, x, L.Vsites);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (h_.nu_post > 0) {
