@@ -209,6 +209,108 @@ __global__ void __launch_bounds__(kThreads, 2) stencil_apply_kernel(ApplyArgs a)
   }
 }
 
+// The same apply for m <= 4 right-hand sides (the Krylov solves below the
+// fine level): thread (row, column) = (tid / 4, tid % 4) owns one output, so
+// no thread computes a padded column.  Rows of a warp read the matrix at
+// skewed columns e = (t + row) mod n, which puts the 8 rows of a warp on
+// different banks (the row stride of 48 or 64 complex numbers is a multiple of
+// 32 words).  Operands staged exactly as in stencil_apply_kernel.
+__global__ void __launch_bounds__(kThreads) stencil_apply_small_kernel(ApplyArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ int s_abort;
+  const int n = a.n, m = a.m;
+  float2* Ms = reinterpret_cast<float2*>(smraw);  // [2][n*n]
+  float2* Vs = Ms + 2 * n * n;                     // [2][n*m]
+  const int x = blockIdx.x;
+  const int tid = threadIdx.x, row = tid >> 2, col = tid & 3;
+  const bool active = row < n && col < m;
+  const uint32_t mbytes = (uint32_t)(n * n) * 8u, vbytes = (uint32_t)(n * m) * 8u;
+
+  auto issue = [&](int d) {
+    const int slot = d & 1;
+    const float2* M = d == 0 ? a.X + (long)x * n * n : a.Y + ((long)x * 8 + d - 1) * n * n;
+    const int src = d == 0 ? x : shift_site(x, a.L, (d - 1) & 3, d <= 4 ? 1 : -1);
+    mbar_expect_tx(&bar[slot], mbytes + vbytes);
+    bulk_g2s(Ms + slot * n * n, M, mbytes, &bar[slot]);
+    bulk_g2s(Vs + slot * n * m, a.vin + (long)src * n * m, vbytes, &bar[slot]);
+  };
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+  }
+  const int r = min(row, n - 1), cq = min(col, m - 1);
+  float2 acc = make_float2(0.f, 0.f);
+  int dstop = 9;
+  for (int d = 0; d < 9; ++d) {
+    const int slot = d & 1;
+    if (!mbar_wait(&bar[slot], (uint32_t)((d >> 1) & 1))) s_abort = 1;
+    __syncthreads();
+    if (s_abort) {
+      dstop = d;
+      break;
+    }
+    const float2* Mr = Ms + slot * n * n + r * n;
+    const float2* Vb = Vs + slot * n * m;
+    float2 part = make_float2(0.f, 0.f);
+    int e = r % n;
+    for (int t = 0; t < n; ++t) {
+      cfma(part, Mr[e], Vb[e * m + cq]);
+      e = e + 1 == n ? 0 : e + 1;
+    }
+    acc = cadd(acc, part);
+    __syncthreads();  // slot free again
+    if (tid == 0 && d + 2 < 9) issue(d + 2);
+  }
+  if (dstop < 9) {
+    if (tid == 0) {
+      atomicOr(a.status, 1);
+      for (int s = dstop; s < min(dstop + 2, 9); ++s)
+        (void)mbar_wait(&bar[s & 1], (uint32_t)((s >> 1) & 1));
+    }
+    return;
+  }
+  const long base = (long)x * n * m;
+  float2 w = cscale(acc, a.scale);
+  float3 pr = make_float3(0.f, 0.f, 0.f);
+  if (active) {
+    a.vout[base + (long)row * m + col] = w;
+    if (a.part) {
+      const float2 rv = __ldg(a.vin + base + (long)row * m + col);
+      float2 wr = make_float2(0.f, 0.f);
+      cfmac(wr, w, rv);
+      pr = make_float3(wr.x, wr.y, fmaf(w.x, w.x, w.y * w.y));
+    }
+  }
+  if (a.part) {
+    float* red = reinterpret_cast<float*>(smraw);  // [64 rows][4 columns][3]
+    red[tid * 3 + 0] = pr.x;
+    red[tid * 3 + 1] = pr.y;
+    red[tid * 3 + 2] = pr.z;
+    __syncthreads();
+    if (tid < m) {
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+      for (int rr = 0; rr < n; ++rr) {
+        const float* o = red + (rr * 4 + tid) * 3;
+        s0 += o[0];
+        s1 += o[1];
+        s2 += o[2];
+      }
+      float* dst = reinterpret_cast<float*>(a.part + (long)x * m + tid);
+      dst[0] = s0;
+      dst[1] = s1;
+      dst[2] = s2;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // smoother helpers
 // ---------------------------------------------------------------------------
@@ -513,6 +615,20 @@ cudaError_t apply_q(const ApplyArgs& a, long V, cudaStream_t s) {
 }
 
 cudaError_t apply_dispatch(const ApplyArgs& a, long V, cudaStream_t s) {
+  if (a.m <= 4) {
+    const size_t stage = sizeof(float2) * 2 * ((size_t)a.n * a.n + (size_t)a.n * a.m);
+    const size_t red = a.part ? sizeof(float) * kThreads * 3 : 0;
+    const size_t smem = stage > red ? stage : red;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(stencil_apply_small_kernel,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           2 * (64 * 64 + 64 * 4) * (int)sizeof(float2));
+      attr = true;
+    }
+    stencil_apply_small_kernel<<<(unsigned)V, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  }
   switch ((a.n + 15) / 16) {
     case 1: return apply_q<1>(a, V, s);
     case 2: return apply_q<2>(a, V, s);

@@ -49,8 +49,9 @@ constexpr int kDotVec = 8;
 __global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, long astride,
                                                   int na, const float2* __restrict__ B, long R,
                                                   int nrhs, double2* part) {
-  __shared__ double2 red[kT];
+  __shared__ double2 red[kT / 32][kDotVec][64];  // [warp][vector][column]
   const int G = kT / nrhs, c = threadIdx.x % nrhs, g = threadIdx.x / nrhs;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long rstep = (long)gridDim.x * G;
   for (int i0 = 0; i0 < na; i0 += kDotVec) {
     const int nv = min(kDotVec, na - i0);
@@ -78,24 +79,31 @@ __global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, 
         cnt = 0;
       }
     }
+    // lanes of a warp with the same column: a fixed shuffle tree, then the
+    // warps' sums in warp order
 #pragma unroll
     for (int u = 0; u < kDotVec; ++u) {
-      acc[u].x += fac[u].x;
-      acc[u].y += fac[u].y;
-    }
-    for (int u = 0; u < nv; ++u) {
-      red[threadIdx.x] = acc[u];
-      __syncthreads();
-      if (g == 0) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int gg = 0; gg < G; ++gg) {
-          s.x += red[gg * nrhs + c].x;
-          s.y += red[gg * nrhs + c].y;
-        }
-        part[((long)blockIdx.x * na + i0 + u) * nrhs + c] = s;
+      double x = acc[u].x + fac[u].x, y = acc[u].y + fac[u].y;
+      for (int off = nrhs; off < 32; off <<= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, off);
+        y += __shfl_xor_sync(0xffffffffu, y, off);
       }
-      __syncthreads();
+      if (lane < min(nrhs, 32) && u < nv) red[warp][u][c] = make_double2(x, y);
     }
+    __syncthreads();
+    // nrhs <= 32: every warp holds every column; nrhs = 64: warp w holds the
+    // columns (w % 2) * 32 .. + 31
+    const int wstep = nrhs > 32 ? nrhs / 32 : 1;
+    for (int t = threadIdx.x; t < nv * nrhs; t += blockDim.x) {
+      const int u = t / nrhs, cc = t % nrhs;
+      double2 s = make_double2(0.0, 0.0);
+      for (int w = nrhs > 32 ? cc / 32 : 0; w < kT / 32; w += wstep) {
+        s.x += red[w][u][cc].x;
+        s.y += red[w][u][cc].y;
+      }
+      part[((long)blockIdx.x * na + i0 + u) * nrhs + cc] = s;
+    }
+    __syncthreads();
   }
 }
 
@@ -407,7 +415,8 @@ class Solver {
   cudaError_t dots(const float2* A, long astride, int na, const float2* B, long R,
                    double2* out) {
     const int G = kT / n_;
-    const int grid = (int)std::min<long>((R + G - 1) / G, kDotGrid);
+    // at least 16 rows per thread
+    const int grid = (int)std::max<long>(1, std::min<long>((R + 16 * G - 1) / (16 * G), kDotGrid));
     TimedScope ts("s_dots", s_);
     dots_kernel<<<grid, kT, 0, s_>>>(A, astride, na, B, R, n_, P_.part);
     const int n = na * n_;
