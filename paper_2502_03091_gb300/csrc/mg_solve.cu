@@ -341,6 +341,7 @@ struct Lvl {
   Xfer xf{};
   long Vsites = 0;       // sites of this level's lattice
   int kdim = 0;          // length of the Krylov cycle run on this level
+  long vstride = 0;      // float2 between consecutive basis vectors (padded)
   bool flexible = false;
   float2 *ts = nullptr, *tw = nullptr, *tx = nullptr, *mr_r = nullptr, *mr_w = nullptr;
   float2 *rhs = nullptr, *sol = nullptr, *V = nullptr, *Z = nullptr, *kw = nullptr;
@@ -627,7 +628,7 @@ class Solver {
   cudaError_t krylov(int l, const float2* b, float2* x, bool flexible, double tol, int max_iters,
                      int* steps_out) {
     Lvl& L = P_.lv[l];
-    const long R = L.R, vs = R * n_;
+    const long R = L.R, vs = L.vstride;
     const int m = L.kdim;
     const size_t hstride = (size_t)(2 * (m + 1) + 1) * n_;  // doubles2 per step in hdev
     cudaError_t e;
@@ -823,7 +824,13 @@ mg_status make_plan(const mg_hierarchy* h, int nrhs, int restart, Plan& p, char*
   for (size_t l = 0; l < p.lv.size(); ++l) {
     Lvl& L = p.lv[l];
     const size_t vb = sizeof(float2) * (size_t)L.R * nrhs;
-    auto vec = [&]() { return reinterpret_cast<float2*>(take(vb)); };
+    // every vector, and every basis vector, starts an odd multiple of 256 B
+    // past a whole vector from the previous one, so that a kernel streaming
+    // several of them does not address them at one large power-of-two-ish
+    // distance (a vector of the 32^3x64 lattice at nrhs = 4 is 3 * 2^28 B)
+    const size_t pad = 65 * 256;
+    L.vstride = (long)((vb + pad) / sizeof(float2));
+    auto vec = [&]() { return reinterpret_cast<float2*>(take(vb + pad)); };
     L.ts = vec();
     L.tw = vec();
     L.tx = vec();
@@ -840,8 +847,8 @@ mg_status make_plan(const mg_hierarchy* h, int nrhs, int restart, Plan& p, char*
     L.mrres = reinterpret_cast<double2*>(take(sizeof(double2) * 2 * nrhs));
     L.scale = reinterpret_cast<float2*>(take(sizeof(float2) * nrhs));
     L.mra = reinterpret_cast<float2*>(take(sizeof(float2) * 2 * nrhs));
-    L.V = reinterpret_cast<float2*>(take(vb * (L.kdim + 1)));
-    if (L.flexible) L.Z = reinterpret_cast<float2*>(take(vb * L.kdim));
+    L.V = reinterpret_cast<float2*>(take((vb + pad) * (L.kdim + 1)));
+    if (L.flexible) L.Z = reinterpret_cast<float2*>(take((vb + pad) * L.kdim));
   }
   p.bytes = o;
   return MG_OK;
