@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kMaxKrylov = 64;   // longest Krylov cycle on any level
-constexpr int kDotGrid = 4 * 152;
+constexpr int kDotGrid = 3 * 152;  // one wave at 3 resident CTAs per SM
 
 using cplx = std::complex<double>;
 
@@ -43,13 +43,16 @@ using cplx = std::complex<double>;
 // vector kernels on R x nrhs arrays (nrhs divides 256)
 // ---------------------------------------------------------------------------
 // part[blk][i][c] = sum over the CTA's rows r of conj(A_i[r][c]) B[r][c], i < na.
-// Eight vectors A_i per sweep over B (B is read ceil(na / 8) times); FP32
-// products summed in FP32 over 32 rows, then in FP64; fixed order.
-constexpr int kDotVec = 8;
-__global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, long astride,
-                                                  int na, const float2* __restrict__ B, long R,
-                                                  int nrhs, double2* part) {
-  __shared__ double2 red[kT / 32][kDotVec][64];  // [warp][vector][column]
+// Four vectors A_i per sweep over B, four rows per loop trip with all their
+// loads issued before the products (so that even one vector pair keeps eight
+// loads in flight per thread); FP32 products summed in FP32 over 32 rows, then
+// in FP64; fixed order.  Dynamic shared memory: kT / 32 * kDotVec * nrhs double2.
+constexpr int kDotVec = 4;
+constexpr int kRowUnroll = 4;
+__global__ void __launch_bounds__(kT, 3) dots_kernel(const float2* __restrict__ A, long astride,
+                                                     int na, const float2* __restrict__ B,
+                                                     long R, int nrhs, double2* part) {
+  extern __shared__ double2 dred[];  // [warp][vector][column]
   const int G = kT / nrhs, c = threadIdx.x % nrhs, g = threadIdx.x / nrhs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long rstep = (long)gridDim.x * G;
@@ -63,13 +66,23 @@ __global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, 
       fac[u] = make_float2(0.f, 0.f);
     }
     int cnt = 0;
-    for (long r = (long)blockIdx.x * G + g; r < R; r += rstep) {
-      const long o = r * nrhs + c;
-      const float2 bv = __ldg(B + o);
+    long r = (long)blockIdx.x * G + g;
+    for (; r + (kRowUnroll - 1) * rstep < R; r += kRowUnroll * rstep) {
+      float2 bv[kRowUnroll], av[kRowUnroll][kDotVec];
 #pragma unroll
-      for (int u = 0; u < kDotVec; ++u)
-        if (u < nv) cfmac(fac[u], __ldg(A + (i0 + u) * astride + o), bv);
-      if (++cnt == 32) {
+      for (int q = 0; q < kRowUnroll; ++q) {
+        const long o = (r + q * rstep) * nrhs + c;
+        bv[q] = __ldg(B + o);
+#pragma unroll
+        for (int u = 0; u < kDotVec; ++u)
+          av[q][u] = u < nv ? __ldg(A + (i0 + u) * astride + o) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < kRowUnroll; ++q)
+#pragma unroll
+        for (int u = 0; u < kDotVec; ++u) cfmac(fac[u], av[q][u], bv[q]);
+      cnt += kRowUnroll;
+      if (cnt >= 32) {
 #pragma unroll
         for (int u = 0; u < kDotVec; ++u) {
           acc[u].x += fac[u].x;
@@ -78,6 +91,13 @@ __global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, 
         }
         cnt = 0;
       }
+    }
+    for (; r < R; r += rstep) {
+      const long o = r * nrhs + c;
+      const float2 bv = __ldg(B + o);
+#pragma unroll
+      for (int u = 0; u < kDotVec; ++u)
+        if (u < nv) cfmac(fac[u], __ldg(A + (i0 + u) * astride + o), bv);
     }
     // lanes of a warp with the same column: a fixed shuffle tree, then the
     // warps' sums in warp order
@@ -88,7 +108,8 @@ __global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, 
         x += __shfl_xor_sync(0xffffffffu, x, off);
         y += __shfl_xor_sync(0xffffffffu, y, off);
       }
-      if (lane < min(nrhs, 32) && u < nv) red[warp][u][c] = make_double2(x, y);
+      if (lane < min(nrhs, 32) && u < nv)
+        dred[(warp * kDotVec + u) * nrhs + c] = make_double2(x, y);
     }
     __syncthreads();
     // nrhs <= 32: every warp holds every column; nrhs = 64: warp w holds the
@@ -96,12 +117,12 @@ __global__ void __launch_bounds__(kT) dots_kernel(const float2* __restrict__ A, 
     const int wstep = nrhs > 32 ? nrhs / 32 : 1;
     for (int t = threadIdx.x; t < nv * nrhs; t += blockDim.x) {
       const int u = t / nrhs, cc = t % nrhs;
-      double2 s = make_double2(0.0, 0.0);
+      double2 sum = make_double2(0.0, 0.0);
       for (int w = nrhs > 32 ? cc / 32 : 0; w < kT / 32; w += wstep) {
-        s.x += red[w][u][cc].x;
-        s.y += red[w][u][cc].y;
+        sum.x += dred[(w * kDotVec + u) * nrhs + cc].x;
+        sum.y += dred[(w * kDotVec + u) * nrhs + cc].y;
       }
-      part[((long)blockIdx.x * na + i0 + u) * nrhs + cc] = s;
+      part[((long)blockIdx.x * na + i0 + u) * nrhs + cc] = sum;
     }
     __syncthreads();
   }
@@ -419,7 +440,8 @@ class Solver {
     // at least 16 rows per thread
     const int grid = (int)std::max<long>(1, std::min<long>((R + 16 * G - 1) / (16 * G), kDotGrid));
     TimedScope ts("s_dots", s_);
-    dots_kernel<<<grid, kT, 0, s_>>>(A, astride, na, B, R, n_, P_.part);
+    const size_t smem = sizeof(double2) * (kT / 32) * kDotVec * n_;
+    dots_kernel<<<grid, kT, smem, s_>>>(A, astride, na, B, R, n_, P_.part);
     const int n = na * n_;
     dots_finish<<<n, kFinT, 0, s_>>>(P_.part, grid, n, out);
     return cudaGetLastError();
