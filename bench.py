@@ -73,6 +73,8 @@ def vol(d):
 # ---------------------------------------------------------------------------
 FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # CUDA-core FP32 FMA peak at max clock
 FP64_TFLOPS = 1.25                             # GB300 nominal FP64
+PEAK_SOURCE = {"fp32": "nominal FP32: 152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz",
+               "fp64": "nominal FP64 of GB300 (1.25 TFLOP/s)"}
 
 
 def dslash_bytes(w, prec="fp32"):
@@ -326,7 +328,7 @@ def _roofline_table(w, prec, kern, steps):
         pk_t = FP32_TFLOPS if bound == "fp32" else FP64_TFLOPS
         ach = amount / per / 1e12
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": pk_t, "unit": "TFLOP/s",
-                "frac": ach / pk_t, "peak_source": f"nominal {bound} (DESIGN.md)",
+                "frac": ach / pk_t, "peak_source": PEAK_SOURCE[bound],
                 "algorithmic_flop_per_launch": amount}
 
     stages = {}
