@@ -9,8 +9,9 @@ check:
     (true residual, not the estimate);
   * one MR step is x = a r with a = <Ar, r> / <Ar, Ar>, and MR never increases
     the residual;
-  * the multigrid K-cycle solve on the 4^4 workload returns numpy.linalg.solve
-    of the dense D; with an exact coarse solve and no post-smoothing the
+  * the multigrid K-cycle solve on the 4^4 workload, with two and with three
+    levels, returns numpy.linalg.solve of the dense D; with an exact coarse
+    solve and no post-smoothing the
     coarse correction leaves a residual that the restriction annihilates
     (R (r - D x) = 0, because D_c = R D P), and the two-level solve needs fewer
     steps than GMRES on D alone.
@@ -81,7 +82,7 @@ def h44():
     levels = S.fine_levels(dims, block, m0, 1.0, U, None, P, X, Y)
     g = G.normals(2, G.STREAM_MISC, 0, 2 * 256 * 12)
     b = (g[0::2] + 1j * g[1::2]).reshape(256, 4, 3)
-    return dict(dims=dims, m0=m0, U=U, levels=levels, b=b, k=k)
+    return dict(dims=dims, m0=m0, U=U, levels=levels, b=b, k=k, P=P, XY=(X, Y))
 
 
 def test_kcycle_solve_equals_dense_solve(h44):
@@ -108,3 +109,30 @@ def test_exact_coarse_correction_is_galerkin(h44):
     L0 = c["levels"][0]
     s = L0.R(r - L0.A(x))
     assert np.linalg.norm(s) <= 1e-9 * np.linalg.norm(L0.R(r))
+
+
+def test_three_level_kcycle_solve_equals_dense_solve(h44):
+    """The recursion: level 2 built by the level-2 oracle on the 4^4 hierarchy's
+    D_c (2^4 coarse sites, one aggregate), K-cycle FGMRES steps on level 1."""
+    from oracle import level2 as L2
+    c = h44
+    dims, block, k = c["dims"], [2, 2, 2, 2], c["k"]
+    L0, L1 = c["levels"]
+    cd = O.coarse_dims(dims, block)
+    X, Y = c["XY"]
+    g = G.normals(4, G.STREAM_MISC, 0, 2 * 16 * 2 * k * 16)
+    q0 = (g[0::2] + 1j * g[1::2]).reshape(16, 2 * k, 16)
+    psi2 = L2.mr(cd, X, Y, q0, 20)
+    Uk2, _ = L2.chiral_truncate(cd, [2, 2, 2, 2], k, psi2, 8)
+    P2 = L2.prolongator(cd, [2, 2, 2, 2], Uk2)
+    X2, Y2 = L2.coarsen(cd, [2, 2, 2, 2], X, Y, P2)
+    levels = S.fine_levels(dims, block, c["m0"], 1.0, c["U"], None, c["P"], X, Y,
+                           P2, [2, 2, 2, 2], X2, Y2)
+    p = S.KParams(nu_pre=2, nu_post=2, kcycle_iters=2, coarsest_iters=16)
+    x, steps = S.solve(levels, c["b"], p, 1e-10, 16, 400)
+    r = c["b"] - L0.A(x)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(c["b"]) * 1.0001
+    D = O.dense_D(dims, c["m0"], 1.0, c["U"], None)
+    xs = np.linalg.solve(D, c["b"].reshape(-1)).reshape(c["b"].shape)
+    smin = np.linalg.svd(D, compute_uv=False)[-1]
+    assert np.linalg.norm(x - xs) <= np.linalg.norm(r) / smin * 1.01
