@@ -297,8 +297,11 @@ size_t mg_solve_workspace_size(const mg_hierarchy* h, int32_t nrhs, int32_t rest
  * steps are done.  Out (host): *iters = outer steps taken; relres[nrhs] = the
  * true |b_c - D x_c| / |b_c| at the end (FP32 residual, FP64 norms).
  * ws: mg_solve_workspace_size(h, nrhs, restart) bytes, 256-byte aligned.
- * Synchronous: the call returns when the solve is done (it synchronises
- * `stream` at every Krylov step to read the inner products). */
+ * Synchronous: the call returns when the solve is done.  It synchronises
+ * `stream` once per outer step (the convergence test) and once per coarse
+ * Krylov cycle (its least-squares solve); the step lengths and Gram-Schmidt
+ * coefficients are computed on the device.  A timeout of an operator's
+ * staged input (see mg_sync_status) is returned as MG_ERR_TIMEOUT. */
 mg_status mg_solve(const mg_hierarchy* h, const void* b, void* x, int32_t nrhs, double tol,
                    int32_t restart, int32_t max_iters, int32_t* iters, double* relres, void* ws,
                    size_t ws_bytes, void* stream);
