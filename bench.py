@@ -352,8 +352,14 @@ def _roofline_table(w, prec, kern, steps):
     roofline["traffic"] = traffic
     dl, dt = kern["mr_dslash_dot"]
     d = roof("mr_dslash_dot", dl, dt)
+    # the same pass against the CUDA-core FP32 peak: 1320 flop per site and
+    # right-hand side for the eight hops, plus 48 (Wilson diagonal) or 504 (clover)
+    flop = vol(w["dims"]) * w["m"] * (1320 + (504 if w["csw"] else 48))
+    tflops = flop / (dt / max(dl, 1) * 1e-3) / 1e12
     dslash = {"kernel": "mr_dslash_dot", "gbs": d["achieved"], "frac": d["frac"],
-              "algorithmic_bytes_per_launch": d["algorithmic_bytes_per_launch"]}
+              "algorithmic_bytes_per_launch": d["algorithmic_bytes_per_launch"],
+              "tflops": tflops, "fp32_alu_frac": tflops / FP32_TFLOPS,
+              "algorithmic_flop_per_launch": flop}
     return stages, top, roofline, dslash
 
 
