@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "mg_common.cuh"
+#include "mg_krylov.h"
 
 namespace mg {
 
@@ -550,99 +551,6 @@ class Solver {
     return cudaSuccess;
   }
 
-  // Per-column Arnoldi bookkeeping on the host: step j's inner products
-  // (two Gram-Schmidt passes and |w|^2, from the device) go into the
-  // Hessenberg column, previous Givens rotations are applied and a new one
-  // zeroes H[j+1][j]; returns whether every column has met the tolerance.
-  struct Hess {
-    int m, n;
-    std::vector<cplx> H, g, sn;
-    std::vector<double> cs;
-    std::vector<int> kc;  // -1: growing; else the column's number of valid steps
-    void reset(int m_, int n_, const std::vector<double2>& beta2) {
-      m = m_;
-      n = n_;
-      H.assign((size_t)n * (m + 1) * m, 0.0);
-      g.assign((size_t)n * (m + 1), 0.0);
-      sn.assign((size_t)n * m, 0.0);
-      cs.assign((size_t)n * m, 0.0);
-      kc.assign(n, 0);
-      for (int c = 0; c < n; ++c) {
-        const double beta = std::sqrt(std::max(0.0, beta2[c].x));
-        g[(size_t)c * (m + 1)] = beta;
-        kc[c] = beta > 0 ? -1 : 0;
-      }
-    }
-    cplx& h(int c, int i, int j) { return H[(size_t)c * (m + 1) * m + i + (size_t)(m + 1) * j]; }
-    double res(int c, int j) const { return std::abs(g[(size_t)c * (m + 1) + j]); }
-    // hj: [2 (m + 1) + 1][n] device layout of step j
-    void step(int j, const double2* hj) {
-      for (int c = 0; c < n; ++c) {
-        if (kc[c] >= 0) continue;
-        const double hn = std::sqrt(std::max(0.0, hj[(size_t)2 * (m + 1) * n + c].x));
-        for (int i = 0; i <= j; ++i) {
-          const double2 a1 = hj[(size_t)i * n + c], a2 = hj[(size_t)(m + 1 + i) * n + c];
-          h(c, i, j) = cplx(a1.x + a2.x, a1.y + a2.y);
-        }
-        h(c, j + 1, j) = hn;
-        for (int i = 0; i < j; ++i) {
-          cplx& a = h(c, i, j);
-          cplx& b = h(c, i + 1, j);
-          const double ci = cs[(size_t)c * m + i];
-          const cplx si = sn[(size_t)c * m + i];
-          const cplx t0 = ci * a + si * b;
-          const cplx t1 = -std::conj(si) * a + ci * b;
-          a = t0;
-          b = t1;
-        }
-        cplx& a = h(c, j, j);
-        const double aa = std::abs(a);
-        double cj;
-        cplx sj;
-        if (hn == 0.0) {
-          cj = 1.0;
-          sj = 0.0;
-        } else if (aa == 0.0) {
-          cj = 0.0;
-          sj = 1.0;
-        } else {
-          const double t = std::sqrt(aa * aa + hn * hn);
-          cj = aa / t;
-          sj = (a / aa) * hn / t;
-        }
-        cs[(size_t)c * m + j] = cj;
-        sn[(size_t)c * m + j] = sj;
-        a = cj * a + sj * hn;
-        h(c, j + 1, j) = 0.0;
-        cplx* gc = &g[(size_t)c * (m + 1)];
-        gc[j + 1] = -std::conj(sj) * gc[j];
-        gc[j] = cj * gc[j];
-        if (hn == 0.0) kc[c] = j + 1;  // breakdown: exact in this column
-      }
-    }
-    bool converged(int j, double tol, const std::vector<double>& bn) const {
-      for (int c = 0; c < n; ++c)
-        if (!(kc[c] >= 0 || res(c, j + 1) <= tol * bn[c])) return false;
-      return true;
-    }
-    // y_c = H_c^-1 g_c over the column's valid steps, as [steps][n]
-    std::vector<cplx> solve(int steps) {
-      std::vector<cplx> coef((size_t)steps * n, 0.0);
-      for (int c = 0; c < n; ++c) {
-        const int k = kc[c] < 0 ? steps : std::min(kc[c], steps);
-        std::vector<cplx> y(k);
-        for (int i = k - 1; i >= 0; --i) {
-          cplx acc = g[(size_t)c * (m + 1) + i];
-          for (int q = i + 1; q < k; ++q) acc -= h(c, i, q) * y[q];
-          const cplx d = h(c, i, i);
-          y[i] = std::abs(d) > 0 ? acc / d : 0.0;
-        }
-        for (int i = 0; i < k; ++i) coef[(size_t)i * n + c] = y[i];
-      }
-      return coef;
-    }
-  };
-
   // (F)GMRES on level l from x = 0.  tol < 0: one cycle of L.kdim steps, the
   // stream synchronised once at its end.  Otherwise cycles of L.kdim steps
   // until every column's least-squares residual is <= tol |b_c| or max_iters
@@ -664,7 +572,7 @@ class Solver {
     if ((e = zero(x, R)) != cudaSuccess) return e;
     int total = 0;
     bool first = true;
-    Hess hs;
+    KrylovHess hs;
     std::vector<double2> beta2(n_), hbuf;
     for (;;) {
       // V_0 = (b - A x) / |b - A x|
@@ -679,7 +587,7 @@ class Solver {
       if ((e = axpby(L.V, L.V, L.scale, nullptr, L.scale, R)) != cudaSuccess) return e;
       if (tol >= 0) {
         if ((e = fetch(beta2, L.beta2)) != cudaSuccess) return e;
-        hs.reset(m, n_, beta2);
+        hs.reset(m, n_, reinterpret_cast<const double*>(beta2.data()));
       }
       const int jmax = std::min(m, max_iters - total);
       int steps = 0;
@@ -703,7 +611,7 @@ class Solver {
         if (tol >= 0) {
           hbuf.resize(hstride);
           if ((e = fetch(hbuf, hj)) != cudaSuccess) return e;
-          hs.step(j, hbuf.data());
+          hs.step(j, reinterpret_cast<const double*>(hbuf.data()));
           if (hs.converged(j, tol, bn)) break;
         }
       }
@@ -715,8 +623,9 @@ class Solver {
           return e;
         if (steps > 0 && (e = fetch(hbuf, L.hdev)) != cudaSuccess) return e;
         if (steps == 0 && (e = cudaStreamSynchronize(s_)) != cudaSuccess) return e;
-        hs.reset(m, n_, beta2);
-        for (int j = 0; j < steps; ++j) hs.step(j, hbuf.data() + (size_t)j * hstride);
+        hs.reset(m, n_, reinterpret_cast<const double*>(beta2.data()));
+        for (int j = 0; j < steps; ++j)
+          hs.step(j, reinterpret_cast<const double*>(hbuf.data() + (size_t)j * hstride));
       }
       if (steps > 0 &&
           (e = combo_h(x, flexible ? L.Z : L.V, vs, steps, hs.solve(steps), R)) != cudaSuccess)
