@@ -10,7 +10,9 @@ functions they check:
     residual orthogonal to D_c r (the minimal-residual condition), and the
     result does not depend on the scale of the starts;
   * the truncation is the best rank-k2 approximation per block (Eckart-Young)
-    with orthonormal U_k, and k2 = m'' spans each block's range.
+    with orthonormal U_k, and k2 = m'' spans each block's range;
+  * at U = 1, with the constant vectors fed to both truncations, D_cc is m0
+    times the identity (a closed form through both levels).
 """
 import numpy as np
 import pytest
@@ -129,3 +131,36 @@ def test_prolongator_and_galerkin(dc):
     s3 = np.tile(np.r_[np.ones(k2), -np.ones(k2)], nc2)
     H = s3[:, None] * D2
     assert np.abs(H - H.conj().T).max() < 1e-11 * np.abs(H).max()
+
+
+def test_free_field_constant_modes_two_levels():
+    """At U = 1 the 12 constant spin-colour vectors are eigenvectors of D with
+    eigenvalue m0; fed to the first truncation (m' = 12, k1 = 6) their coarse
+    images, the 12 constant unit vectors of the coarse lattice, are eigenvectors
+    of D_c with eigenvalue m0.  Fed in turn to the second truncation (m = 12,
+    k2 = 6, one aggregate holding the whole coarse lattice) they span range(P2),
+    so D_cc = P2^dag D_c P2 is m0 times the identity: the recursion of both
+    levels against a closed form."""
+    from conftest import dense_coarse
+    dims, block, m0 = [4, 4, 4, 4], [2, 2, 2, 2], 0.37
+    V = int(np.prod(dims))
+    psi = np.zeros((V, 4, 3, 12), dtype=np.complex128)
+    for sp in range(4):
+        for c in range(3):
+            psi[:, sp, c, sp * 3 + c] = 1.0
+    Uk, _ = O.chiral_truncate(dims, block, psi, 6)
+    P = O.prolongator(dims, block, Uk)
+    X, Y = O.coarsen(dims, block, m0, 1.0, G.unit_gauge_field(dims), None, P)
+    cd = O.coarse_dims(dims, block)
+    nc = int(np.prod(cd))
+    q = np.zeros((nc, 12, 12), dtype=np.complex128)
+    for e in range(12):
+        q[:, e, e] = 1.0
+    # the constant coarse vectors are eigenvectors of D_c with eigenvalue m0
+    assert np.abs(O.coarse_apply(cd, X, Y, q) - m0 * q).max() < 1e-12
+    Uk2, sig2 = L2.chiral_truncate(cd, [2, 2, 2, 2], 6, q, 6)
+    P2 = L2.prolongator(cd, [2, 2, 2, 2], Uk2)
+    X2, Y2 = L2.coarsen(cd, [2, 2, 2, 2], X, Y, P2)
+    D2 = dense_coarse(O.coarse_dims(cd, [2, 2, 2, 2]), X2, Y2)
+    assert D2.shape == (12, 12)
+    assert np.abs(D2 - m0 * np.eye(12)).max() < 1e-12
