@@ -576,12 +576,20 @@ def _measure(args, w, prec, rep, U_host, psi0, level2=False):
     mg.mg_timing_read()
     rep.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     e0.record(stream)
-    for _ in range(args.steps):
+    ev[0].record(stream)
+    for i in range(args.steps):
         step()
+        ev[i + 1].record(stream)
     e1.record(stream)
     rep.barrier()
     ms = e0.elapsed_time(e1) / args.steps
+    per_step = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps))
+    step_ms = {"median": per_step[(len(per_step) - 1) // 2] if len(per_step) % 2
+               else 0.5 * (per_step[len(per_step) // 2 - 1] + per_step[len(per_step) // 2]),
+               "p90": per_step[max(0, -(-9 * len(per_step) // 10) - 1)],
+               "min": per_step[0], "max": per_step[-1]}
     kern = mg.mg_timing_read()
     mg.mg_timing_enable(False)
     clocks = sampler.stop()
@@ -653,7 +661,7 @@ def _measure(args, w, prec, rep, U_host, psi0, level2=False):
     decay = {f"alpha{a}": {"sigma_1": sig0[a][0], "sigma_k": sig0[a][-1],
                            "sigma_k_over_sigma_1": sig0[a][-1] / sig0[a][0]} for a in range(2)}
     res = dict(ms=ms, kern=kern, clocks=clocks, flags=int((flags != 0).sum()), e2e_ms=e2e_ms,
-               e2e_steps=e2e_steps, h2d=h2d, d2h=d2h, sigma_decay=decay)
+               e2e_steps=e2e_steps, h2d=h2d, d2h=d2h, sigma_decay=decay, step_ms=step_ms)
     if level2:
         res["level2"], res["solve"] = level2_measure(args, prob, lv, stream)
     elif not args.no_solve and not args.no_level2:
@@ -859,6 +867,7 @@ def run_ours(args, w):
         "dslash": dslash,
         "top_kernel": top,
         "stages": stages,
+        "step_ms": r["step_ms"],
         "gpu_launches": launches,
         "blk_flags_nonzero": r["flags"],
         "sigma_decay_block0": r["sigma_decay"],
@@ -875,7 +884,8 @@ def run_ours(args, w):
         st, tp, rf, ds = _roofline_table(w, p, q["kern"], args.steps)
         out["fp32_plain" if p == "fp32" else p] = {
             "value": per_level(q["ms"], world), "ms_per_step": q["ms"],
-            "e2e": per_level(q["e2e_ms"], world), "top_kernel": tp, "roofline": rf,
+            "e2e": per_level(q["e2e_ms"], world), "step_ms": q["step_ms"],
+            "top_kernel": tp, "roofline": rf,
             "dslash": ds, "stages": {n: v["ms_per_step"] for n, v in st.items()},
             "gpu_launches": sum(l for l, _ in q["kern"].values()), "clocks": q["clocks"],
             "blk_flags_nonzero": q["flags"]}
