@@ -252,6 +252,14 @@ class Replicas:
             self.dist = None
 
 
+def step_stats(per_step_ms) -> dict:
+    """Median, p90 (nearest rank), min and max of the per-step times."""
+    v = sorted(per_step_ms)
+    n = len(v)
+    med = v[(n - 1) // 2] if n % 2 else 0.5 * (v[n // 2 - 1] + v[n // 2])
+    return {"median": med, "p90": v[max(0, -(-9 * n // 10) - 1)], "min": v[0], "max": v[-1]}
+
+
 def per_level(ms_max: float, world: int) -> float:
     """Whole-job seconds per level: `world` replicas each built one level in
     (at most) ms_max milliseconds."""
@@ -585,11 +593,7 @@ def _measure(args, w, prec, rep, U_host, psi0, level2=False):
     e1.record(stream)
     rep.barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    per_step = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps))
-    step_ms = {"median": per_step[(len(per_step) - 1) // 2] if len(per_step) % 2
-               else 0.5 * (per_step[len(per_step) // 2 - 1] + per_step[len(per_step) // 2]),
-               "p90": per_step[max(0, -(-9 * len(per_step) // 10) - 1)],
-               "min": per_step[0], "max": per_step[-1]}
+    step_ms = step_stats([ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)])
     kern = mg.mg_timing_read()
     mg.mg_timing_enable(False)
     clocks = sampler.stop()

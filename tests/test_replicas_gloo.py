@@ -122,3 +122,14 @@ def test_failed_replica_is_an_error_not_a_hang():
     assert procs[0].exitcode == 0
     rank, outcome = q.get(timeout=5)
     assert rank == 0 and outcome.startswith("error:")
+
+
+def test_step_stats():
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    assert bench.step_stats([5.0]) == {"median": 5.0, "p90": 5.0, "min": 5.0, "max": 5.0}
+    s = bench.step_stats([3.0, 1.0, 2.0, 4.0])
+    assert s["median"] == 2.5 and s["p90"] == 4.0 and s["min"] == 1.0
+    s = bench.step_stats(list(range(20, 0, -1)))
+    assert s["median"] == 10.5 and s["p90"] == 18 and s["max"] == 20
