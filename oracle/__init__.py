@@ -8,7 +8,10 @@ The arithmetic lives in ``mg_oracle.c`` (plain C99, complex128, OpenMP over
 sites and blocks); this module only compiles it and marshals numpy arrays.
 Every function follows one passage of the paper:
 
-  clover(U)                  operator input (the clover term of the ensembles, Sec. 4)
+  clover(U)                  operator input (the clover term of the ensembles, Sec. 4;
+                             sign and normalisation are this library's reading: pinned
+                             to that convention by a closed form, parity against the
+                             paper unpinned)
   apply_D / dense_D          the fine operator D (Sec. 1, 2)
   mr(...)                    smoother on D psi = 0 with m random starts (Eq. 1)
   chiral_truncate(...)       chiral split (Eq. 2) + per-block SVD, rank-k truncation (Eq. 4)
