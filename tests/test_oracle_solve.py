@@ -5,8 +5,9 @@ check:
     space span{b, Ab, ..., A^(j-1) b}, found by brute force (least squares on
     the explicit Krylov matrix); n steps solve an n x n system exactly;
   * FGMRES with the identity as preconditioner is GMRES, with the exact
-    inverse it converges in one step; restarted FGMRES reaches its tolerance
-    (true residual, not the estimate);
+    inverse it converges in one step, with a fixed linear M it is M times the
+    GMRES iterate of A M; restarted FGMRES reaches its tolerance (true
+    residual, not the estimate);
   * one MR step is x = a r with a = <Ar, r> / <Ar, Ar>, and MR never increases
     the residual;
   * the multigrid K-cycle solve on the 4^4 workload, with two and with three
@@ -54,6 +55,18 @@ def test_fgmres_preconditioners():
     x3, total = S.fgmres(op, b, None, 1e-9, 3, 200)
     assert np.linalg.norm(b - A @ x3) <= 1e-9 * np.linalg.norm(b) * 1.0001
     assert total > 3  # needed restarts
+
+
+def test_fgmres_with_linear_preconditioner_is_right_preconditioned_gmres():
+    """With a fixed linear M, one FGMRES cycle of j steps returns M y, y the
+    j-step GMRES iterate of the operator A M (right preconditioning)."""
+    A, b = _dense(10, 4)
+    Mm, _ = _dense(10, 5, shift=2.0)
+    op = lambda v: A @ v  # noqa: E731
+    for j in (2, 5):
+        x = S.arnoldi_cycle(op, b, None, j, M=lambda v: Mm @ v)[0]
+        y = S.gmres(lambda v: A @ (Mm @ v), b, j)
+        assert np.linalg.norm(x - Mm @ y) <= 1e-10 * np.linalg.norm(x)
 
 
 def test_mr_step_and_monotone_residual():
