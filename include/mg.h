@@ -317,7 +317,11 @@ mg_status mg_solve(const mg_hierarchy* h, const void* b, void* x, int32_t nrhs, 
  * scratch need (mg_workspace_size(prob, MG_CALL_TRUNCATE)) exceeds 64 MiB is
  * rejected with MG_ERR_INVALID and a message.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
+ * device current; make that first call before any stream capture.  The
+ * address is kept per device together with the id of the CUDA context it
+ * belongs to; the first call from a new context on that device (after a
+ * cudaDeviceReset, for instance) looks it up again, so make that call
+ * outside a capture too.  All calls
  * share the one array and leave their data in it (nothing in it needs to
  * start at zero); calls that overlap on the GPU race on it, so serialise
  * them (one stream, or synchronise between calls).  It allocates nothing. */

@@ -312,12 +312,11 @@ template <int T>
 cudaError_t coarsen_t(const CoarsenArgs& a, int nblk, cudaStream_t s) {
   constexpr int NP = 16 * T;
   const size_t smem = sizeof(float2) * (size_t)(2 * kChunk * 6 * NP + NP * (NP + 1));
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr_once;
+  attr_once.run([&] {
     cudaFuncSetAttribute(coarsen_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    attr = true;
-  }
+  });
   TimedScope ts("coarsen", s);
   coarsen_kernel<T><<<nblk, 256, smem, s>>>(a);
   return cudaGetLastError();
@@ -352,11 +351,10 @@ cudaError_t launch_coarse_apply(const Geom& g, const float2* X, const float2* Y,
                                 const float2* vin, float2* vout, int nrhs, cudaStream_t s) {
   const int n2 = 2 * g.k;
   const size_t smem = sizeof(float2) * (size_t)9 * n2 * nrhs;
-  static bool attr_done = false;
-  if (!attr_done) {
+  static PerDeviceOnce attr_once;
+  attr_once.run([&] {
     cudaFuncSetAttribute(coarse_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
-    attr_done = true;
-  }
+  });
   TimedScope ts("coarse_apply", s);
   coarse_apply_kernel<<<(int)g.nblk, 256, smem, s>>>(X, Y, vin, vout, g.Lc[0], g.Lc[1], g.Lc[2],
                                                      g.Lc[3], n2, nrhs);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/mg.h"
 
 namespace mg {
@@ -63,6 +65,30 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Sets the message mg_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
+
+// Runs a set-up step (cudaFuncSetAttribute, which applies to the current
+// device only) once per device, from any number of host threads.
+constexpr int kMaxDevices = 64;
+class PerDeviceOnce {
+ public:
+  template <typename F>
+  void run(F f) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+      f();  // unusual device index: set up on every call (cheap)
+      return;
+    }
+    std::lock_guard<std::mutex> g(mu_);
+    if (!done_[dev]) {
+      f();
+      done_[dev] = true;
+    }
+  }
+
+ private:
+  std::mutex mu_;
+  bool done_[kMaxDevices] = {};
+};
 
 // Tuned slab width of the smoother passes for g's shape (0: not tuned), and
 // whether the calling thread is capturing a batch graph (no timing events).

@@ -18,6 +18,7 @@
 // (FP32 storage, 768 bytes per site and slab for P = 4) or four halves in a
 // uint2 (FP16 storage of the mixed-precision path, 384 bytes); arithmetic is
 // FP32 in both.
+#include <atomic>
 #include <cstdint>
 
 #include <cuda_fp16.h>
@@ -31,32 +32,19 @@ namespace {
 // device status word: bit 0 = a smoother pass gave up waiting for its staged
 // input; bit 1 = a tensor-core Gram gave up waiting for its MMAs
 __device__ int g_status;
+// words taken from g_status by read_device_status, one slot per call
+constexpr int kStatusSlots = 64;
+__device__ int g_status_taken[kStatusSlots];
+__global__ void status_take(int* slot) { *slot = atomicExch(&g_status, 0); }
 
 // ---------------------------------------------------------------------------
 // packed FP32 pairs: component .x belongs to the first right-hand side of a
-// pair, .y to the second
+// pair, .y to the second (the f32x2 instructions of sm_100 and later, through
+// the compiler's builtins, so pairs stay in adjacent registers)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long pk(float2 a) {
-  unsigned long long u;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(a.x), "f"(a.y));
-  return u;
-}
-__device__ __forceinline__ float2 upk(unsigned long long u) {
-  float2 a;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(u));
-  return a;
-}
 // a * b + c, lane-wise
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
-  return upk(d);
-}
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
-  return upk(d);
-}
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
 // one complex component of two right-hand sides
@@ -811,12 +799,11 @@ template <int PAIRS, int MODE, typename T>
 cudaError_t run_march(const MarchArgs& a, int nsl, cudaStream_t s) {
   static const char* names[2] = {"mr_neg_dslash", "mr_dslash_dot"};
   const size_t smem = sizeof(T) * (size_t)kRing * kSPC * 12 * PAIRS;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr_once;
+  attr_once.run([&] {
     cudaFuncSetAttribute(march_kernel<PAIRS, MODE, T>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   TimedScope ts(names[MODE], s);
   march_kernel<PAIRS, MODE, T><<<nsl * a.npatch, march_threads<PAIRS>(), smem, s>>>(a);
   return cudaGetLastError();
@@ -992,12 +979,20 @@ int* device_status_word() {
 }
 
 cudaError_t read_device_status(int* out, cudaStream_t s) {
-  cudaError_t e = cudaStreamSynchronize(s);
+  // take and clear the word in one atomic step on the stream, into a slot of
+  // its own per call, so that a bit set by another stream between the read
+  // and the clear is never lost (it stays for the next call)
+  static std::atomic<unsigned> next_slot{0};
+  int* taken = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&taken), g_status_taken);
   if (e != cudaSuccess) return e;
+  int* slot = taken + next_slot.fetch_add(1u) % kStatusSlots;
+  status_take<<<1, 1, 0, s>>>(slot);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int v = 0;
-  if ((e = cudaMemcpyFromSymbol(&v, g_status, sizeof(int))) != cudaSuccess) return e;
-  const int zero = 0;
-  if ((e = cudaMemcpyToSymbol(g_status, &zero, sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(&v, slot, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   *out = v;
   return cudaSuccess;
 }

@@ -594,12 +594,11 @@ cudaError_t apply_t(const ApplyArgs& a, long V, cudaStream_t s) {
   const size_t stage = sizeof(float2) * 2 * ((size_t)a.n * a.n + (size_t)a.n * a.m);
   const size_t red = a.part ? sizeof(float) * 16 * 64 * 3 : 0;
   const size_t smem = stage > red ? stage : red;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr_once;
+  attr_once.run([&] {
     cudaFuncSetAttribute(stencil_apply_kernel<NR, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * (64 * 64 + 64 * 64) * (int)sizeof(float2));
-    attr = true;
-  }
+  });
   stencil_apply_kernel<NR, NQ><<<(unsigned)V, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -619,13 +618,12 @@ cudaError_t apply_dispatch(const ApplyArgs& a, long V, cudaStream_t s) {
     const size_t stage = sizeof(float2) * 2 * ((size_t)a.n * a.n + (size_t)a.n * a.m);
     const size_t red = a.part ? sizeof(float) * kThreads * 3 : 0;
     const size_t smem = stage > red ? stage : red;
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce attr_once;
+    attr_once.run([&] {
       cudaFuncSetAttribute(stencil_apply_small_kernel,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            2 * (64 * 64 + 64 * 4) * (int)sizeof(float2));
-      attr = true;
-    }
+    });
     stencil_apply_small_kernel<<<(unsigned)V, kThreads, smem, s>>>(a);
     return cudaGetLastError();
   }
@@ -739,12 +737,11 @@ cudaError_t launch_stencil_galerkin(const Geom& g, const float2* X, const float2
   const int n = 2 * a.nc;
   const size_t smem =
       sizeof(float2) * ((size_t)n * n + 4 * (size_t)a.nc * kKP + (size_t)n * 2 * kKP);
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr_once;
+  attr_once.run([&] {
     cudaFuncSetAttribute(stencil_galerkin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(float2) * (64 * 64 + 4 * 32 * kKP + 64 * 2 * kKP)));
-    attr = true;
-  }
+  });
   TimedScope ts("c_galerkin", s);
   stencil_galerkin_kernel<<<(unsigned)g.nblk, kThreads, smem, s>>>(a);
   return cudaGetLastError();

@@ -228,11 +228,10 @@ bool gram_tc_supported(const Geom& g) { return 2 * g.m <= kTcN; }
 
 cudaError_t launch_gram_tc(const Geom& g, const float2* psi, double2* G, int* status,
                            cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr_once;
+  attr_once.run([&] {
     cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    attr = true;
-  }
+  });
   TcGeom tg;
   for (int i = 0; i < 4; ++i) {
     tg.L[i] = g.L[i];

@@ -969,15 +969,14 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
   const size_t sm_chol = sizeof(double2) * (size_t)m * (m + 1) + sizeof(float2) * (size_t)m * m;
   const size_t sm_svd = sizeof(double2) * ((size_t)m * (m + 1) + (size_t)m * k);
   const size_t sm_uk = sm_gram1 + sizeof(float2) * ((size_t)m * k + (size_t)kChunkRows * k);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static PerDeviceOnce attr_once;
+  attr_once.run([&] {
     cudaFuncSetAttribute(gram_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
     cudaFuncSetAttribute(gram_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
     cudaFuncSetAttribute(chol_stage1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
     cudaFuncSetAttribute(svd_stage2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
     cudaFuncSetAttribute(form_uk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
-    attr_done = true;
-  }
+  });
   if (g.prec == MG_PREC_MIXED && g.rps == 6 && gram_tc_supported(g)) {
     // mixed precision: G1 on the tensor cores in BF16 (CholeskyQR2's second
     // pass, below, is FP32 and restores the orthonormality)

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_SHAPE", 3: "MG_ERR_N
                 7: "MG_ERR_UNSUPPORTED"}
 MG_PREC_FP32 = 0
 MG_PREC_MIXED = 1
+MG_ERR_TIMEOUT = 6
 MG_CALL_SMOOTH, MG_CALL_TRUNCATE, MG_CALL_COARSEN = 0, 1, 2
 
 # every symbol include/mg.h declares

@@ -46,6 +46,7 @@ class Request:
     t_done: float = math.nan
     gpu_ms: float = math.nan
     deferred: bool = False
+    failed: bool = False      # rejected: a bounded device wait timed out (see Server.run)
 
 
 def request_stream(n: int, rate: float, seed: int = 40, m0: float = -0.15,
@@ -162,6 +163,7 @@ class Server:
         self.used = 0
         self.high_water = 0
         self.results: Dict[int, tuple] = {}
+        self.late_timeout = False
 
     def _problem(self, r: Request) -> mg.Problem:
         return mg.Problem(dims=r.dims, block=r.block, m0=r.m0, n_vec=r.m, k=r.k,
@@ -229,6 +231,25 @@ class Server:
                 r, lv, s = a["r"], a["lv"], a["s"]
                 r.t_done = now()
                 r.gpu_ms = a["e_in"].elapsed_time(a["e_done"])
+                # The library's status word is per device: a bounded wait that
+                # timed out in any kernel since the last check shows up here.
+                # The request being completed and every request on the device
+                # with it are rejected (their results may be the invalid ones).
+                try:
+                    mg.mg_sync_status(s)
+                except mg.MgError as e:
+                    if e.status != mg.MG_ERR_TIMEOUT:
+                        raise
+                    for b in active:
+                        b["r"].failed = True
+                if r.failed:
+                    del lv
+                    a.clear()
+                    self.used -= need_bytes(self._problem(r))
+                    active.remove(a)
+                    done.append(r)
+                    progressed = True
+                    continue
                 if self.keep_results:
                     self.results[r.rid] = (lv.sigma.cpu(), lv.X.cpu(), lv.Y.cpu(), lv.psi.cpu())
                 # keep the hierarchy, drop the rest of the setup's memory
@@ -256,12 +277,21 @@ class Server:
             if not progressed:
                 time.sleep(2e-4)
         torch.cuda.synchronize()
-        mg.mg_sync_status()
+        try:
+            mg.mg_sync_status()
+        except mg.MgError as e:
+            if e.status != mg.MG_ERR_TIMEOUT:
+                raise
+            self.late_timeout = True  # a coarse apply timed out after its request completed
         resident.clear()
         return self._stats(done, realtime)
 
     def _stats(self, done: List[Request], realtime: bool) -> dict:
         import numpy as np
+        failed = sum(r.failed for r in done)
+        done = [r for r in done if not r.failed]
+        if not done:
+            return {"requests": 0, "failed": failed}
         lat = np.array([r.t_done - (r.arrival if realtime else 0.0) for r in done])
         span = max(r.t_done for r in done) - (min(r.arrival for r in done) if realtime else 0.0)
         gpu = np.array([r.gpu_ms for r in done])
@@ -271,4 +301,5 @@ class Server:
                 "admitted_at_arrival": int(sum(not r.deferred for r in done)),
                 "gpu_ms_p50": float(np.percentile(gpu, 50)),
                 "hbm_high_water_gb": self.high_water / 1e9,
-                "max_slots": self.max_slots}
+                "max_slots": self.max_slots, "failed": failed,
+                "late_timeout": self.late_timeout}

@@ -34,16 +34,23 @@ def _outputs(p):
     return Uk, sig, flags
 
 
-def test_static_scratch_matches_workspace_call_twice():
-    p = mg.Problem(dims=[8, 8, 8, 8], block=[4, 4, 4, 4], m0=-0.1, n_vec=48, k=24, mr_iters=1)
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_static_scratch_matches_workspace_call_twice(precision):
+    # the mixed-precision truncation runs its Grams on the tensor cores, which
+    # write into the same built-in array and report through the status word
+    prec = mg.MG_PREC_MIXED if precision == "mixed" else mg.MG_PREC_FP32
+    p = mg.Problem(dims=[8, 8, 8, 8], block=[4, 4, 4, 4], m0=-0.1, n_vec=48, k=24, mr_iters=1,
+                   precision=prec)
     assert mg.mg_workspace_size(p, mg.MG_CALL_TRUNCATE) <= 64 << 20
     ws = mg.workspace(p, mg.MG_CALL_TRUNCATE)
     for call, seed in enumerate((5, 6)):  # two calls in a row, different inputs
         psi = to_dev(G.psi0(p.dims, p.n_vec, seed))
         Uk_ref, s_ref, f_ref = _outputs(p)
         mg.mg_chiral_truncate(p, psi, Uk_ref, s_ref, None, f_ref, ws)
+        mg.mg_sync_status()  # raises on a device-side timeout
         Uk, s, f = _outputs(p)
         mg.mg_chiral_truncate_static(p, psi, Uk, s, None, f)
+        mg.mg_sync_status()
         torch.cuda.synchronize()
         assert np.all(f.cpu().numpy() == 0) and np.all(f_ref.cpu().numpy() == 0)
         np.testing.assert_allclose(s.cpu().numpy(), s_ref.cpu().numpy(), rtol=1e-5)
