@@ -81,20 +81,24 @@ def dslash_bytes(w, prec="fp32"):
     """One dslash pass: read 12 + write 12 complex numbers per site and
     right-hand side (192 B in complex64, 96 B in FP16), plus links (288 B) and
     clover (288 B) per site."""
-    per_site = (96 if prec == "mixed" else 192) * w["m"] + 288 + (288 if w["csw"] else 0)
+    per_site = (96 if prec == "mixed_fp16" else 192) * w["m"] + 288 + (288 if w["csw"] else 0)
     return vol(w["dims"]) * per_site
 
 
 def kernel_work(w, prec="fp32"):
     """{kernel: (bound, amount, unit)} -- bytes for HBM-bound kernels, flop for
-    arithmetic-bound ones (per launch).  prec "mixed": the smoother's fields
-    are FP16 (half the bytes of complex64)."""
+    arithmetic-bound ones (per launch).  prec "mixed_fp16": the smoother's
+    fields are FP16 (half the bytes of complex64).  The tensor-core kernels of
+    the mixed paths are counted by the bytes they must move (their arithmetic
+    runs far below the tensor pipe's rate)."""
     V, m, k = vol(w["dims"]), w["m"], w["k"]
     nb = vol(w["block"])
     nbc = 2 * V // nb
     K = 6 * nb
     abi = V * 96 * m  # one complex64 field [V][4][3][m] (the interface)
-    spinor = abi // 2 if prec == "mixed" else abi  # one smoother field
+    spinor = abi // 2 if prec == "mixed_fp16" else abi  # one smoother field
+    uk = V * 12 * k * 8  # U_k (and P): [V][2][6][k] complex64
+    xy = (V // nb) * 9 * (2 * k) ** 2 * 8  # X and Y
     return {
         "mr_input_norm": ("hbm", abi, "B"),
         "mr_to_slab": ("hbm", abi + spinor, "B"),
@@ -105,6 +109,10 @@ def kernel_work(w, prec="fp32"):
         "mr_scale": ("hbm", spinor + abi, "B"),
         "trunc_gram": ("hbm", abi, "B"),               # read every block once
         "trunc_gram_tc": ("hbm", abi, "B"),            # the same on BF16 tensor cores
+        "trunc_q1_tc": ("hbm", 2 * abi, "B"),          # read A, write Q1 = A R1^-1
+        "trunc_gram2_tc": ("hbm", abi, "B"),           # read Q1
+        "trunc_uk_tc": ("hbm", abi + uk, "B"),         # read Q1, write U_k
+        "coarsen_tc": ("hbm", uk + V * 288 + xy, "B"),  # read P and U once, write X, Y
         "trunc_gram_q1": ("fp32", nbc * (8 * K * m * m + 4 * K * m * m), "flop"),
         "trunc_form_uk": ("fp32", nbc * (4 * K * m * m + 8 * K * m * k), "flop"),
         "trunc_chol64": ("fp64", nbc * (8 * m ** 3 / 3 + 8 * m ** 3 / 3), "flop"),
@@ -112,7 +120,7 @@ def kernel_work(w, prec="fp32"):
                                             + 16 * m ** 3 / 3 + 8 * m * m * k), "flop"),
         "prolongator": ("hbm", 2 * V * 12 * k * 8, "B"),
         "coarsen": ("fp32", V * (4 * 8 * 6 * (2 * k) ** 2 + 8 * 12 * (2 * k) ** 2), "flop"),
-        "coarse_apply": ("hbm", (V // nb) * 9 * (2 * k) ** 2 * 8, "B"),
+        "coarse_apply": ("hbm", xy, "B"),
     }
 
 
@@ -279,10 +287,13 @@ def run_reference(args, w):
         dt, scale, threads, desc = oracle_sample(w)
         times.append(dt * scale)
     v = sum(times) / len(times)
-    cfg = config_of(w, args, "fp32" if getattr(args, "precision", "both") == "fp32" else "mixed")
+    cfg = config_of(w, args, "fp32" if getattr(args, "precision", "all") == "fp32" else "mixed")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        # every step is one run of the oracle on the sample sub-lattice:
+        # ms_per_step is that run's own time; value scales it to the workload
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v / scale * 1e3,
+        "sample_scale_to_workload": scale,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -292,10 +303,19 @@ def run_reference(args, w):
 
 
 PRECISION_NOTE = {
-    "fp32": "FP32 plain: complex64 storage and FP32 arithmetic; FP64 Cholesky and small eig",
-    "mixed": "mixed: FP16 storage of the smoother fields (FP32 arithmetic); truncation and "
-             "coarsening as the FP32 path; FP64 Cholesky and small eig",
+    "fp32": "FP32 plain: complex64 storage and FP32 arithmetic on the CUDA cores; FP64 "
+            "Cholesky and small eigenproblem",
+    "mixed": "mixed: smoother as FP32 plain; truncation Grams, Q1 = A R1^-1, U_k and the "
+             "Galerkin contractions on tcgen05 tensor cores with FP32 accumulation (first Gram "
+             "BF16, the rest FP16 hi/lo split, 3 products); FP64 Cholesky and small eigenproblem",
+    "mixed_fp16": "mixed with FP16 storage of the smoother fields (FP32 arithmetic); truncation "
+                  "and coarsening as mixed",
 }
+DTYPE = {"fp32": "f32",
+         "mixed": "f32 smoother; fp16x3+bf16 tensor-core contractions (f32 accum); f64 eig",
+         "mixed_fp16": "f16-stored smoother (f32 math); fp16x3+bf16 tensor-core contractions; "
+                       "f64 eig"}
+PREC_ID = {"fp32": 0, "mixed": 1, "mixed_fp16": 2}
 
 
 def config_of(w, args, prec="fp32"):
@@ -556,7 +576,7 @@ def _measure(args, w, prec, rep, U_host, psi0, level2=False):
 
     prob = mg.Problem(dims=w["dims"], block=w["block"], m0=w["m0"], n_vec=w["m"], k=w["k"],
                       mr_iters=w["N"], csw=w["csw"], xi=w["xi"],
-                      precision=mg.MG_PREC_MIXED if prec == "mixed" else mg.MG_PREC_FP32)
+                      precision=PREC_ID[prec])
     U = U_host.cuda()
     C = None
     if w["csw"]:
@@ -715,10 +735,10 @@ def accuracy_check(w):
     P = O.prolongator(d, b, Uk)
     lo = lowest16(*O.coarsen(d, b, w["m0"], w["xi"], U, C, P))
     out = {"lattice": "x".join(map(str, d)), "oracle_mean_abs_lowest16": float(lo.mean())}
-    for prec in ("fp32", "mixed"):
+    for prec in ("fp32", "mixed", "mixed_fp16"):
         prob = mg.Problem(dims=d, block=b, m0=w["m0"], n_vec=m, k=k, mr_iters=w["N"],
                           csw=w["csw"], xi=w["xi"],
-                          precision=mg.MG_PREC_MIXED if prec == "mixed" else mg.MG_PREC_FP32)
+                          precision=PREC_ID[prec])
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).cuda()
         Cd = dev(C.reshape(-1, 2, 6, 6)) if C is not None else None
         lv = mg.Level.allocate(prob, dev(U), Cd, dev(p0))
@@ -795,27 +815,37 @@ def batch_measure(args):
     return out
 
 
-def serving_measure(args, n_requests=200, rate=20.0):
+SERVING_RATES = ((2.0, 40), (4.0, 60), (8.0, 100), (20.0, 200))  # (arrivals/s, requests)
+
+
+def serving_measure(args):
     """Serving under the mixed-volume Poisson load: volumes uniform over
     {8^4, 12^3x24, 16^3x32, 24^3x48, 32^3x64}, (m', k) over {(48,24), (64,24),
-    (32,16)}, 4^4 aggregates, eps = 0.25, mean 20 arrivals/s (seed 40), each
-    hierarchy resident for 4 coarse applies (nrhs 8); mixed-precision path.
-    Warm-up: one request per volume, then n_requests timed in real time."""
+    (32,16)}, 4^4 aggregates, eps = 0.25, each hierarchy resident for 4
+    coarse applies (nrhs 8); mixed-precision path.  Warm-up: one request per
+    volume.  Then, per offered rate (Poisson, seed 40), a stream of requests
+    timed in real time: the low rates measure the serving loop's own latency,
+    20/s (the workload's rate) is above what one GPU completes, so its queue
+    grows over the run."""
     from paper_2502_03091_gb300 import serve
 
     m0 = _m0_table()["Wilson eps=0.25"]
     warm = [serve.Request(rid=10000 + i, arrival=0.0, dims=list(d), m=64, k=24, m0=m0,
                           seed=10000 + i) for i, d in enumerate(serve.VOLUMES)]
     serve.Server(max_slots=4).run(warm, realtime=False)
-    reqs = serve.request_stream(n_requests, rate, seed=40, m0=m0)
-    st = serve.Server(max_slots=4).run(reqs, realtime=True)
-    st.update({"config": f"{n_requests} requests, Poisson mean {rate:g}/s (seed 40); volumes "
-                         "8^4, 12^3x24, 16^3x32, 24^3x48, 32^3x64; (m',k) in {(48,24),(64,24),"
-                         "(32,16)}; 4^4 aggregates; eps 0.25; mixed precision; 4 coarse applies "
-                         "(nrhs 8) per hierarchy; inputs synthesised on the device per request",
-               "latency": "setup complete (host poll of the request's completion event) minus "
-                          "arrival, including input synthesis and queueing"})
-    return st
+    out = {"config": "Poisson arrivals (seed 40) at each offered rate; volumes 8^4, 12^3x24, "
+                     "16^3x32, 24^3x48, 32^3x64; (m',k) in {(48,24),(64,24),(32,16)}; 4^4 "
+                     "aggregates; eps 0.25; mixed precision; 4 coarse applies (nrhs 8) per "
+                     "hierarchy; inputs synthesised on the device per request",
+           "latency": "setup complete (host poll of the request's completion event) minus "
+                      "arrival, including input synthesis and queueing",
+           "rates": []}
+    for rate, n in SERVING_RATES:
+        reqs = serve.request_stream(n, rate, seed=40, m0=m0)
+        st = serve.Server(max_slots=4).run(reqs, realtime=True)
+        st["offered_per_s"] = rate
+        out["rates"].append(st)
+    return out
 
 
 def run_ours(args, w):
@@ -842,7 +872,7 @@ def run_ours(args, w):
     psi0 = torch.complex(torch.randn(shape, device="cuda", generator=gen),
                          torch.randn(shape, device="cuda", generator=gen))
 
-    precs = ["mixed", "fp32"] if args.precision == "both" else [args.precision]
+    precs = ["mixed", "fp32", "mixed_fp16"] if args.precision == "all" else [args.precision]
     res = {p: _measure(args, w, p, rep, U_host, psi0,
                        level2=(p == precs[0] and not args.no_level2)) for p in precs}
     if rank != 0:
@@ -864,7 +894,7 @@ def run_ours(args, w):
     out = {
         "metric": METRIC, "value": per_level(r["ms"], world), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[head],
         "data": "synthetic (seeded random SU(3) links, Gaussian starts)",
         "config": config_of(w, args, head),
         "roofline": roofline,
@@ -899,7 +929,7 @@ def run_ours(args, w):
         out["level2"] = r["level2"]
     if r.get("solve"):
         out["solve"] = r["solve"]
-    if world == 1 and not args.no_accuracy and len(precs) == 2:
+    if world == 1 and not args.no_accuracy and len(precs) == 3:
         out["accuracy"] = accuracy_check(w)
     if world == 1 and not args.no_batch:
         out["batch"] = batch_measure(args)
@@ -945,9 +975,9 @@ def main():
     ap.add_argument("--workload", default="32^3x64",
                     choices=["32^3x64", "16^3x32", "16^3x32-aniso"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="both", choices=["both", "fp32", "mixed"],
-                    help="both: the mixed path is the headline value, the FP32 plain path "
-                         "is reported beside it")
+    ap.add_argument("--precision", default="all", choices=["all", "fp32", "mixed", "mixed_fp16"],
+                    help="all: the mixed path (FP32-accurate) is the headline value; the FP32 "
+                         "plain path and the FP16-storage path are reported beside it")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the setup-serving measurement (p50/p99 under Poisson load)")
     ap.add_argument("--no-batch", action="store_true",

@@ -81,11 +81,21 @@ typedef enum {
 } mg_status;
 
 typedef enum {
-  MG_PREC_FP32 = 0,  /* complex64 storage, FP32 arithmetic; FP64 for the small
-                        Cholesky / R-factor eigen problems */
-  MG_PREC_MIXED = 1  /* FP16 storage of the smoother's fields (FP32 arithmetic);
-                        first Gram of the truncation on BF16 tensor cores (FP32
-                        accumulation); the rest as MG_PREC_FP32 */
+  MG_PREC_FP32 = 0,       /* complex64 storage, FP32 arithmetic on the CUDA cores; FP64
+                             for the small Cholesky / R-factor eigen problems */
+  MG_PREC_MIXED = 1,      /* the smoother as MG_PREC_FP32; the truncation's dense
+                             contractions on the tensor cores with FP32 accumulation:
+                             the first Gram (only the preconditioner of CholeskyQR2's
+                             second pass) in BF16, the second Gram, Q1 = A R1^-1 and
+                             U_k with FP16 operands split into hi + lo parts (three
+                             products, about FP32 accuracy, a power-of-two scale per
+                             block-chirality); FP64 Cholesky / R-factor eigen problem.
+                             Results agree with the FP64 reference as closely as the
+                             MG_PREC_FP32 path's do. */
+  MG_PREC_MIXED_FP16 = 2  /* as MG_PREC_MIXED, but the smoother's fields are stored
+                             in FP16 (FP32 arithmetic): half the smoother's memory
+                             traffic, at a test-vector error of about 1e-2 relative
+                             (the MR recurrence amplifies the storage rounding) */
 } mg_precision;
 
 typedef struct {
@@ -328,6 +338,17 @@ mg_status mg_solve(const mg_hierarchy* h, const void* b, void* x, int32_t nrhs, 
 mg_status mg_chiral_truncate_static(const mg_problem* prob, const void* psi, void* Uk,
                                     double* sigma, void* coarse_tv, int32_t* blk_flags,
                                     void* stream);
+
+/* Failure-detection self-test (no counterpart in the paper).  Enqueues on
+ * `stream` one kernel whose single thread waits on a shared-memory mbarrier
+ * that nothing ever arrives at, giving up after `polls` polls
+ * (1 <= polls <= 1048576, the limit the library's own waits use), exactly as
+ * the smoother's and the tensor-core kernels' bounded waits give up; it then
+ * records a timeout in the device status word.  No copy or matrix multiply
+ * is in flight when it gives up, so the device and the library stay usable:
+ * the next mg_sync_status(stream) returns MG_ERR_TIMEOUT, the one after that
+ * MG_OK.  Errors: MG_ERR_INVALID for polls out of range. */
+mg_status mg_selftest_timeout(int32_t polls, void* stream);
 
 /* Per-kernel timing (measurement aid; no counterpart in the paper).  While
  * enabled, every kernel the library launches is bracketed by two CUDA events

@@ -46,7 +46,8 @@ mg_status make_geom(const mg_problem* p, Geom* g) {
     nb *= p->block[i];
   }
   if (V > (1L << 30)) return fail(MG_ERR_SHAPE, "volume %ld too large", V);
-  if (p->precision != MG_PREC_FP32 && p->precision != MG_PREC_MIXED)
+  if (p->precision != MG_PREC_FP32 && p->precision != MG_PREC_MIXED &&
+      p->precision != MG_PREC_MIXED_FP16)
     return fail(MG_ERR_UNSUPPORTED, "precision %d not implemented", p->precision);
   if (p->n_vec < 4 || p->n_vec > kMaxM || p->n_vec % 4 != 0)
     return fail(MG_ERR_UNSUPPORTED, "n_vec must be a multiple of 4 in [4, %d], got %d", kMaxM,
@@ -137,7 +138,7 @@ mg_status make_cgeom(const mg_coarse_problem* p, StencilGeom* sg, Geom* g, bool 
 SmoothWs smooth_ws_layout(const Geom& g) {
   SmoothWs w{};
   // one spinor field: complex64 or, in the mixed-precision path, two FP16 per complex
-  const size_t field = (g.prec == MG_PREC_MIXED ? 4 : 8) * (size_t)g.V * 12 * g.m;
+  const size_t field = (g.prec == MG_PREC_MIXED_FP16 ? 4 : 8) * (size_t)g.V * 12 * g.m;
   size_t o = 0;
   w.ra = o; o = align256(o + field);
   w.wa = o; o = align256(o + field);
@@ -162,6 +163,13 @@ TruncWs trunc_ws_layout(const Geom& g) {
   w.w2 = o; o = align256(o + sizeof(float2) * nbc * g.m * g.k);
   w.hm = o; o = align256(o + sizeof(double2) * nbc * mm);
   w.flags = o; o = align256(o + sizeof(int32_t) * nbc);
+  w.q1 = w.qmax = 0;
+  if (g.prec != MG_PREC_FP32 && tc_supported(g)) {
+    // tensor-core path: Q1 = A R1^-1 of every block-chirality (as large as psi)
+    // and the largest entry of each
+    w.q1 = o; o = align256(o + sizeof(float2) * nbc * (size_t)g.cps * g.nb / 2 * g.m);
+    w.qmax = o; o = align256(o + sizeof(float) * nbc);
+  }
   w.bytes = o;
   return w;
 }
@@ -284,6 +292,13 @@ mg_status mg_sync_status(void* stream) {
                 "a tensor-core Gram gave up waiting for its matrix multiplies; the "
                 "truncation's outputs are not valid");
   return MG_OK;
+}
+
+mg_status mg_selftest_timeout(int32_t polls, void* stream) {
+  if (polls < 1 || polls > (1 << 20))
+    return fail(MG_ERR_INVALID, "mg_selftest_timeout: polls %d out of [1, 1048576]", polls);
+  return cuda_status(launch_selftest_timeout(polls, static_cast<cudaStream_t>(stream)),
+                     "mg_selftest_timeout");
 }
 
 const char* mg_last_error(void) { return g_err; }

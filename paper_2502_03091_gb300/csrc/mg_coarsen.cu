@@ -324,6 +324,12 @@ cudaError_t coarsen_t(const CoarsenArgs& a, int nblk, cudaStream_t s) {
 
 cudaError_t launch_coarsen(const Geom& g, const float2* U, const float2* C, const float2* P,
                            float2* X, float2* Y, cudaStream_t s) {
+  if (g.prec != MG_PREC_FP32 && tc_coarsen_supported(g)) {
+    // mixed precision: the contractions on the tensor cores (mg_tc.cu)
+    int* st = device_status_word();
+    if (!st) return cudaErrorInvalidSymbol;
+    return launch_tc_coarsen(g, U, C, P, X, Y, st, s);
+  }
   CoarsenArgs a;
   a.U = U;
   a.C = C;

@@ -43,7 +43,7 @@ struct SmoothWs {
   size_t ra, wa, ps, part, alpha, scale, bytes;
 };
 struct TruncWs {
-  size_t gram, r1, z1, w2, hm, flags, bytes;
+  size_t gram, r1, z1, w2, hm, flags, q1, qmax, bytes;  // q1, qmax: 0 unless tensor cores
 };
 
 // operator of a level l >= 1: a nearest-neighbour stencil (X, Y) with n = 2 nc
@@ -130,11 +130,24 @@ cudaError_t launch_smoother(const Geom& g, const float2* U, const float2* C,
 cudaError_t read_device_status(int* out, cudaStream_t s);
 // Device address of that word (nullptr on a CUDA error).
 int* device_status_word();
+// mg_selftest_timeout's kernel.
+cudaError_t launch_selftest_timeout(int polls, cudaStream_t s);
 
-// Tensor-core (tcgen05, BF16) first Gram of the truncation, mixed precision.
-bool gram_tc_supported(const Geom& g);
-cudaError_t launch_gram_tc(const Geom& g, const float2* psi, double2* G, int* status,
-                           cudaStream_t s);
+// Tensor-core (tcgen05) contractions of the truncation (mg_tc.cu), per
+// block-chirality bc: G[bc] = A^dag A (BF16 operands, or FP16 hi/lo split with
+// three products), and C[bc] = A B[bc] (FP16 hi/lo split).  A's rows are
+// gathered from psi by the block geometry (gather) or contiguous [bc][K][m'].
+bool tc_supported(const Geom& g);
+cudaError_t launch_tc_gram(const Geom& g, const float2* A, bool gather, bool fp16x3,
+                           const float* bound, double2* G, int* status, cudaStream_t s,
+                           const char* name);
+// Galerkin coarsening on the tensor cores (FP16 hi/lo operands, FP32 accumulation).
+bool tc_coarsen_supported(const Geom& g);
+cudaError_t launch_tc_coarsen(const Geom& g, const float2* U, const float2* C, const float2* P,
+                              float2* X, float2* Y, int* status, cudaStream_t s);
+cudaError_t launch_tc_gemm(const Geom& g, const float2* A, bool gather, const double2* gdiag,
+                           const float* abound, const float2* B, int n, float2* C, float* cmax,
+                           int* status, cudaStream_t s, const char* name);
 
 cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double* sigma,
                             float2* coarse_tv, int32_t* flags, char* ws, cudaStream_t s);

@@ -1,36 +1,63 @@
-// mg_tc.cu -- tensor-core (tcgen05) contractions of the mixed-precision path.
+// mg_tc.cu -- tensor-core (tcgen05) contractions of the chiral truncation.
 //
-// First Gram of the chiral truncation (Sec. 3, Eq. 4 via CholeskyQR2):
-// G1 = A^dag A for every block-chirality A (K = 6|Lambda| rows of m'
-// complex numbers).  With the rows stored as 2m' interleaved reals
-// (re_0, im_0, re_1, ...), A~ is a real K x 2m' matrix and
-//   (A~^T A~)[2i+a][2j+b],  a, b in {re, im},
-// gives G1[i][j] = (re.re + im.im) + i (re.im - im.re).  A~^T A~ is one real
-// 128 x 128 x K contraction (2m' padded to 128) on the 5th-generation tensor
-// cores: BF16 operands staged in shared memory in the K-major canonical
-// layout (8 x 16-byte core matrices, no swizzle), FP32 accumulation in TMEM,
-// one elected thread issuing tcgen05.mma (M = N = 128, K = 16 per
-// instruction) and tcgen05.commit to an mbarrier per staging buffer.  Both
-// MMA operands are the same shared-memory tile.
+// The per-block SVD of the truncation (paper Sec. 3, Eq. 4: the K x m' block
+// A = Psi^(alpha)(Lambda_j), K = 6|Lambda|, factored by CholeskyQR2 and the
+// SVD of its small R factor) needs two kinds of dense contraction per
+// block-chirality bc = 2j + alpha:
+//   Gram:  G = A^dag A                     (m' x m', Hermitian)
+//   GEMM:  C = A B                         (K x n; B an m' x n matrix of bc)
+// Both are taken over the reals.  A row of A is stored as 2m' interleaved
+// reals (re_0, im_0, re_1, ...), so A~ is K x 2m' and
+//   Gram: (A~^T A~)[2i+a][2j+b] gives G[i][j] = (rr + ii) + i (ri - ir);
+//   GEMM: C~ = A~ B~, with the 2m' x 2n real form of B
+//         B~[2i][2j] = re b, B~[2i][2j+1] = im b, B~[2i+1][2j] = -im b,
+//         B~[2i+1][2j+1] = re b,
+//         and C~[r][2j], C~[r][2j+1] the real and imaginary parts of C[r][j].
+// They run on the 5th-generation tensor cores: operands staged in shared
+// memory in the K-major canonical layout (core matrices of 8 rows x 16 bytes,
+// no swizzle), FP32 accumulators in TMEM, one thread issuing tcgen05.mma
+// (M = 128, K = 16 per instruction, kind::f16) and tcgen05.commit to one
+// mbarrier per staging buffer, tcgen05.ld epilogues.  The kernels are
+// persistent: a CTA walks the block-chiralities bc = blockIdx.x,
+// blockIdx.x + gridDim.x, ... in chunks of 128 rows of A.
 //
-// BF16 rounding of A perturbs G1 by about 2^-9 |A|^2 / sqrt(K) per entry;
-// CholeskyQR2's second pass (FP32 Gram of Q1 = A R1^-1) restores the
-// orthonormality, so only R1 (the preconditioner of the second pass) sees it.
+// Two operand precisions:
+//  * BF16, one product per pair of operands: about 2^-9 relative per product.
+//    Used for the first Gram G1 = A^dag A, which only yields the
+//    preconditioner R1 of CholeskyQR2's second pass.
+//  * FP16 hi/lo split, three products: a value v of a block-chirality is
+//    scaled by a power of two s (chosen per block-chirality so that
+//    |s v| <= 2^14: no overflow, and the typical entry stays far above the
+//    subnormal range), then split into h = fp16(s v) and l = fp16(s v - h).
+//    x y is taken as hh + hl + lh; the dropped ll term is below 2^-22 |x y|,
+//    so the contraction is accurate to about FP32 rounding.  The scales are
+//    undone exactly in the epilogue.
+//
+// Every wait on an mbarrier is bounded.  A CTA whose wait gives up stops
+// staging and issuing, waits (bounded) for the last matrix multiplies it
+// committed, writes nothing more, frees its TMEM and sets bit 1 of the status
+// word (mg_sync_status reports MG_ERR_TIMEOUT; the outputs of that call are
+// then undefined).
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "mg_common.cuh"
 
 namespace mg {
 namespace {
 
-constexpr int kTcN = 128;                    // padded 2m' = M = N of the MMA
-constexpr int kTcKC = 64;                    // rows of A per staged chunk
-constexpr int kTcTile = kTcN * kTcKC * 2;    // bytes of one BF16 chunk (16 KB)
-constexpr int kTcSmem = 48 * 1024;           // dynamic shared memory: caps the CTAs per
-                                             // SM at 4 = 512 TMEM columns / 128
+constexpr int kTcThreads = 256;
+constexpr int kTcRows = 128;                 // rows of A per staged chunk
+constexpr int kTcCols = 128;                 // reals per row of A~ (2m' padded)
+constexpr int kTcTile = kTcRows * kTcCols * 2;  // bytes of one 16-bit tile (32 KB)
+constexpr int kTcSbo = (kTcCols / 8) * 128;  // bytes between 8-row groups of a tile (2048)
+constexpr int kTcMaxSites = 1024;            // largest |Lambda| of a gathered block
 constexpr int kTcMaxPolls = 1 << 20;
+
+enum { TC_BF16 = 0, TC_FP16X3 = 1 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -48,7 +75,34 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
-__device__ __forceinline__ bool bar_wait(unsigned long long* bar, uint32_t parity) {
+// instruction descriptor of kind::f16 with FP32 accumulation, both operands
+// K-major, M = 128: operand type 0 = FP16, 1 = BF16
+__device__ __forceinline__ uint32_t idesc_f16(int n, int bf16) {
+  const uint32_t t = bf16 ? 1u : 0u;
+  return (1u << 4) | (t << 7) | (t << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t taddr, uint64_t da, uint64_t db, uint32_t idesc,
+                                    uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void commit(unsigned long long* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(bar))
+      : "memory");
+}
+
+// waits for completion `use` (0-based) of the barrier; false after a bounded
+// number of polls
+__device__ __forceinline__ bool bar_wait(unsigned long long* bar, int use) {
+  const uint32_t parity = (uint32_t)(use & 1);
   for (int i = 0; i < kTcMaxPolls; ++i) {
     uint32_t ok;
     asm volatile(
@@ -62,12 +116,92 @@ __device__ __forceinline__ bool bar_wait(unsigned long long* bar, uint32_t parit
   return false;
 }
 
-struct TcGeom {
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, int cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   su32(slot)),
+               "r"(cols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, int cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols)
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t a, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(a));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void sync_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void sync_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// generic-proxy writes to shared memory -> visible to the tensor core
+__device__ __forceinline__ void fence_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// operand conversion: 8 values -> one 16-byte row of a core matrix
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bf2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t hf2(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+// PREC == TC_BF16: hi = bf16(v); TC_FP16X3: hi = fp16(s v), lo = fp16(s v - hi)
+template <int PREC>
+__device__ __forceinline__ void split8(const float v[8], float s, uint4& hi, uint4& lo) {
+  if (PREC == TC_BF16) {
+    hi = make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
+  } else {
+    float x[8], r[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      x[i] = v[i] * s;
+      r[i] = x[i] - __half2float(__float2half_rn(x[i]));
+    }
+    hi = make_uint4(hf2(x[0], x[1]), hf2(x[2], x[3]), hf2(x[4], x[5]), hf2(x[6], x[7]));
+    lo = make_uint4(hf2(r[0], r[1]), hf2(r[2], r[3]), hf2(r[4], r[5]), hf2(r[6], r[7]));
+  }
+}
+
+// power of two s with s * bound <= 2^14 (1 for a zero or non-finite bound)
+__device__ __forceinline__ float scale_for(float bound) {
+  if (!(bound > 0.f) || !isfinite(bound)) return 1.f;
+  int e;
+  frexpf(bound, &e);  // bound <= 2^e
+  return ldexpf(1.f, 14 - e);
+}
+
+// ---------------------------------------------------------------------------
+// rows of A
+// ---------------------------------------------------------------------------
+struct TcRows {
+  const float* src;  // psi [V][12][m'] (gather) or contiguous rows [bc][K][m'], complex
+  int gather;
   int L[4], b[4], Lc[4];
-  int nb, m;
+  int nb, K, m, nbc;
 };
 
-__device__ __forceinline__ int tc_block_site(const TcGeom& g, int j, int loc) {
+// global site of local site `loc` of block `j`
+__device__ __forceinline__ int tc_block_site(const TcRows& g, int j, int loc) {
   int jc[4], lc[4];
   int t = j;
   jc[0] = t % g.Lc[0]; t /= g.Lc[0];
@@ -82,167 +216,916 @@ __device__ __forceinline__ int tc_block_site(const TcGeom& g, int j, int loc) {
                    g.L[1] * ((jc[2] * g.b[2] + lc[2]) + g.L[2] * (jc[3] * g.b[3] + lc[3])));
 }
 
-// One CTA (8 warps) per block-chirality.  Staging: warp w converts rows
-// 8w .. 8w+7 of the chunk, two rows at a time (a BF16 pair along K per
-// 4-byte store); lane l covers the reals 4l .. 4l+3 of a row.
-__global__ void __launch_bounds__(256) gram_tc_kernel(const float* __restrict__ psi,
-                                                      double2* __restrict__ G, TcGeom g,
-                                                      int* __restrict__ status) {
+// per-CTA table of the float offset of each site's chirality-0 rows (gather
+// mode), filled for block j; row r of chirality alpha starts at
+// table[r / 6] + (6 alpha + r % 6) * 2m'
+__device__ void fill_site_table(const TcRows& g, int j, long* table) {
+  for (int loc = threadIdx.x; loc < g.nb; loc += blockDim.x)
+    table[loc] = (long)tc_block_site(g, j, loc) * 12 * 2 * g.m;
+}
+
+__device__ __forceinline__ const float* row_ptr(const TcRows& g, const long* table, int bc,
+                                                int r) {
+  if (g.gather) return g.src + table[r / 6] + (long)(6 * (bc & 1) + r % 6) * 2 * g.m;
+  return g.src + ((long)bc * g.K + r) * 2 * g.m;
+}
+
+// Gram staging: chunk c of bc into the transposed K-major tiles (M = column of
+// A~, K = row): element (column q, row r) at (q>>3)*2048 + (r>>3)*128 +
+// (q&7)*16 + (r&7)*2.  Thread t covers the columns 2(t&63), 2(t&63)+1 and the
+// row groups (t>>6) + 4p; a warp reads 256 contiguous bytes of a row per load.
+template <int PREC>
+__device__ void stage_gram(const TcRows& g, const long* table, int bc, int c, float s,
+                           unsigned char* hi, unsigned char* lo) {
+  const int cp = threadIdx.x & 63, q0 = 2 * cp;
+  const int nreal = 2 * g.m;
+#pragma unroll 1
+  for (int p2 = 0; p2 < 4; p2 += 2) {
+    // two row groups' loads in flight at once (16 x 8 bytes)
+    float2 x[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = c * kTcRows + ((threadIdx.x >> 6) + 4 * (p2 + h)) * 8 + i;
+        x[h][i] = (r < g.K && q0 < nreal)
+                      ? __ldg(reinterpret_cast<const float2*>(row_ptr(g, table, bc, r) + q0))
+                      : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int rg = (threadIdx.x >> 6) + 4 * (p2 + h);
+    float v0[8], v1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      v0[i] = x[h][i].x;
+      v1[i] = x[h][i].y;
+    }
+    uint4 h0, l0, h1, l1;
+    split8<PREC>(v0, s, h0, l0);
+    split8<PREC>(v1, s, h1, l1);
+    const uint32_t o0 = (q0 >> 3) * kTcSbo + rg * 128 + (q0 & 7) * 16;
+    *reinterpret_cast<uint4*>(hi + o0) = h0;
+    *reinterpret_cast<uint4*>(hi + o0 + 16) = h1;
+    if (PREC == TC_FP16X3) {
+      *reinterpret_cast<uint4*>(lo + o0) = l0;
+      *reinterpret_cast<uint4*>(lo + o0 + 16) = l1;
+    }
+  }
+  }
+}
+
+// GEMM staging: chunk c of bc into K-major tiles (M = row, K = real column):
+// element (row r, column q) at (r>>3)*2048 + (q>>3)*128 + (r&7)*16 + (q&7)*2.
+// Thread t covers row t&127 and the column groups (t>>7) + 2p.
+__device__ void stage_gemm_rows(const TcRows& g, const long* table, int bc, int c, float s,
+                                unsigned char* hi, unsigned char* lo) {
+  const int rl = threadIdx.x & 127;
+  const int r = c * kTcRows + rl;
+  const int nreal = 2 * g.m;
+  const float* rp = r < g.K ? row_ptr(g, table, bc, r) : nullptr;
+  // all of the thread's loads in flight at once (16 x 16 bytes)
+  float4 ld[16];
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const int cg = (threadIdx.x >> 7) + 2 * p;
+    const bool ok = rp && 8 * cg < nreal;
+    ld[2 * p] = ok ? __ldg(reinterpret_cast<const float4*>(rp + 8 * cg)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    ld[2 * p + 1] =
+        ok ? __ldg(reinterpret_cast<const float4*>(rp + 8 * cg + 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const int cg = (threadIdx.x >> 7) + 2 * p;
+    const float4 a = ld[2 * p], b = ld[2 * p + 1];
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint4 h, l;
+    split8<TC_FP16X3>(v, s, h, l);
+    const uint32_t o = (rl >> 3) * kTcSbo + cg * 128 + (rl & 7) * 16;
+    *reinterpret_cast<uint4*>(hi + o) = h;
+    *reinterpret_cast<uint4*>(lo + o) = l;
+  }
+}
+
+// block-wide maximum of a non-negative float (all threads get it)
+__device__ float block_max(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = 0.f;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = fmaxf(r, red[i]);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Gram kernel: G[bc] = A^dag A (FP64 output [bc][m'][m']).
+//
+// The tensor core's FP32 accumulation is not round-to-nearest: on a long
+// chain of accumulating MMAs (3072 rows x 3 products here) it drifts by
+// about 1e-5 relative, systematically.  So the FP16X3 form keeps every TMEM
+// accumulation short: per chunk of 128 rows, D1 = sum of the hi*hi products
+// (8 MMAs) and D2 = sum of the hi*lo + lo*hi products (16 MMAs, 2^-11 smaller)
+// start from zero, and the chunk sums D1 + D2 are added on the CUDA cores
+// (round to nearest) in the registers of the epilogue warps: thread (warp w
+// < 4, lane) owns row 32w + lane of the 128 x 128 result.  TMEM holds two
+// slots (D1, D2) so the epilogue of chunk c-1 overlaps the MMAs of chunk c.
+// The BF16 form (the preconditioner Gram) accumulates all chunks in TMEM.
+// bound (FP16X3 only): per-bc bound on |entries of A| for the scale.
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(kTcThreads, PREC == TC_BF16 ? 3 : 1)
+    tc_gram_kernel(TcRows g, const float* bound,
+                                                                double2* __restrict__ G,
+                                                                int* __restrict__ status) {
+  constexpr bool X3 = PREC == TC_FP16X3;
+  constexpr int NP = X3 ? 2 : 1;
+  constexpr int TCOLS = X3 ? 4 * kTcCols : kTcCols;  // (D1, D2) x 2 slots, or one D
   extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* tiles = tc_smem;                                      // [2][NP][kTcTile]
+  long* table = reinterpret_cast<long*>(tc_smem + 2 * NP * kTcTile);  // [kTcMaxSites]
   __shared__ __align__(8) unsigned long long bar[2];
   __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int bc = blockIdx.x, j = bc >> 1, al = bc & 1;
-  const int m = g.m, K = 6 * g.nb, nreal = 2 * m;
-  unsigned char* tile0 = tc_smem;
-  unsigned char* tile1 = tc_smem + kTcTile;
-  // zero both tiles: rows >= 2m' (padding) are never written again
-  for (int i = tid; i < 2 * kTcTile / 16; i += blockDim.x)
-    reinterpret_cast<uint4*>(tc_smem)[i] = make_uint4(0u, 0u, 0u, 0u);
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     su32(&tmem_base)),
-                 "r"(kTcN)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (tid == 0) {
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) tmem_alloc(&tmem_base, TCOLS);
+  if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  sync_before();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  sync_after();
   const uint32_t taddr = tmem_base;
-  // instruction descriptor: D FP32, A and B BF16, both K-major, N = 128, M = 128
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                         ((uint32_t)(128 >> 4) << 24);
-  const int nchunk = (K + kTcKC - 1) / kTcKC;
-  bool ok = true;
-  for (int c = 0; c < nchunk; ++c) {
-    const int b = c & 1;
-    unsigned char* tile = b ? tile1 : tile0;
-    // the MMAs that read this buffer two chunks ago must have completed
-    if (c >= 2 && !bar_wait(&bar[b], ((c - 2) >> 1) & 1)) ok = false;
-    for (int rr = 0; rr < 8; rr += 2) {
-      const int kk = warp * 8 + rr;
-      const int r0 = c * kTcKC + kk;
-      float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-      if (4 * lane < nreal) {
-        if (r0 < K) {
-          const int x = tc_block_site(g, j, r0 / 6);
-          v0 = __ldg(reinterpret_cast<const float4*>(psi + ((long)x * 12 + 6 * al + r0 % 6) * nreal) +
-                     lane);
-        }
-        if (r0 + 1 < K) {
-          const int x = tc_block_site(g, j, (r0 + 1) / 6);
-          v1 = __ldg(reinterpret_cast<const float4*>(
-                         psi + ((long)x * 12 + 6 * al + (r0 + 1) % 6) * nreal) +
-                     lane);
-        }
-        const float a0[4] = {v0.x, v0.y, v0.z, v0.w}, a1[4] = {v1.x, v1.y, v1.z, v1.w};
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t idesc = idesc_f16(kTcCols, PREC == TC_BF16);
+  const int nchunk = (g.K + kTcRows - 1) / kTcRows;
+  const int m = g.m;
+  int gidx = 0;  // chunks this CTA has committed
+  int last_j = -1;
+  float acc[X3 ? kTcCols : 1];  // FP16X3: this thread's row of the sum of chunk results
+
+  // FP16X3: add the chunk in TMEM slot d to acc (warps 0-3)
+  auto add_chunk = [&](int d) {
+    if (!X3 || warp >= 4) return;
+    sync_after();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int mr = 4 * lane + q;  // real column of A~ = row of the K-major operand
-          const uint32_t off = (mr >> 3) * 1024 + (kk >> 3) * 128 + (mr & 7) * 16 + (kk & 7) * 2;
-          *reinterpret_cast<__nv_bfloat162*>(tile + off) = __floats2bfloat162_rn(a0[q], a1[q]);
-        }
-      }
+    for (int cb = 0; cb < kTcCols / 16; ++cb) {
+      float v1[16], v2[16];
+      tmem_ld16(taddr + lane_base + d * 2 * kTcCols + cb * 16, v1);
+      tmem_ld16(taddr + lane_base + d * 2 * kTcCols + kTcCols + cb * 16, v2);
+#pragma unroll
+      for (int t = 0; t < 16; ++t) acc[cb * 16 + t] += v1[t] + v2[t];
     }
-    // generic-proxy writes -> visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  };
+
+  for (int bc = blockIdx.x; bc < g.nbc && !s_abort; bc += gridDim.x) {
+    if (g.gather && (bc >> 1) != last_j) {
+      last_j = bc >> 1;
+      fill_site_table(g, last_j, table);
+      __syncthreads();
+    }
+    const float s = X3 ? scale_for(bound ? bound[bc] : 1.f) : 1.f;
+    if (X3) {
+#pragma unroll
+      for (int i = 0; i < kTcCols; ++i) acc[i] = 0.f;
+    }
+    for (int c = 0; c < nchunk; ++c, ++gidx) {
+      const int b = gidx & 1;
+      unsigned char* hi = tiles + b * NP * kTcTile;
+      unsigned char* lo = hi + kTcTile;  // (FP16X3 only)
+      // the MMAs that read this buffer (and TMEM slot) two chunks ago are done
+      if (gidx >= 2 && !bar_wait(&bar[b], (gidx - 2) >> 1)) s_abort = 1;
+      __syncthreads();
+      if (s_abort) break;
+      stage_gram<PREC>(g, table, bc, c, s, hi, lo);
+      fence_async();
+      sync_before();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        sync_after();
+        const uint32_t d1 = taddr + (X3 ? b * 2 * kTcCols : 0), d2 = d1 + kTcCols;
+#pragma unroll 1
+        for (int k = 0; k < kTcRows / 16; ++k) {
+          const uint64_t dh = smem_desc(su32(hi) + k * 256, 128, kTcSbo);
+          if (X3) {
+            const uint64_t dl = smem_desc(su32(lo) + k * 256, 128, kTcSbo);
+            mma(d1, dh, dh, idesc, k > 0 ? 1u : 0u);
+            mma(d2, dh, dl, idesc, k > 0 ? 1u : 0u);
+            mma(d2, dl, dh, idesc, 1u);
+          } else {
+            mma(d1, dh, dh, idesc, (c > 0 || k > 0) ? 1u : 0u);
+          }
+        }
+        commit(&bar[b]);
+      }
+      if (X3 && c > 0) {
+        // chunk c-1 (committed as gidx-1) while chunk c multiplies
+        if (warp < 4 && !bar_wait(&bar[(gidx - 1) & 1], (gidx - 1) >> 1)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) break;
+        add_chunk((gidx - 1) & 1);
+      }
+      sync_before();
+      __syncthreads();
+    }
+    if (s_abort) break;
+    // the last commit covers every MMA of this bc
+    if (!bar_wait(&bar[(gidx - 1) & 1], (gidx - 1) >> 1)) s_abort = 1;
     __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (s_abort) break;
+    sync_after();
+    if (warp < 4) {
+      // lane = row rho = 32 warp + lane; rows 2i, 2i+1 (re, im of column i of
+      // A) are neighbouring lanes
+      const int rho = warp * 32 + lane, i = rho >> 1;
+      const double inv = 1.0 / ((double)s * (double)s);
+      double2* Gb = G + (long)bc * m * m;
+      if (X3) add_chunk((gidx - 1) & 1);
 #pragma unroll
-      for (int s = 0; s < kTcKC / 16; ++s) {
-        // K step s: core-matrix columns 2s, 2s+1 (LBO 128 B), row groups every 1024 B
-        const uint64_t d = smem_desc(su32(tile) + s * 256, 128, 1024);
-        const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
-            "l"(d), "l"(d), "r"(idesc), "r"(acc)
-            : "memory");
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              su32(&bar[b]))
-          : "memory");
-    }
-  }
-  // the last two chunks' MMAs (every earlier one was waited for in the loop)
-  if (!bar_wait(&bar[(nchunk - 1) & 1], ((nchunk - 1) >> 1) & 1)) ok = false;
-  if (nchunk >= 2 && !bar_wait(&bar[(nchunk - 2) & 1], ((nchunk - 2) >> 1) & 1)) ok = false;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncthreads();
-  // epilogue: warp w (< 4) holds D rows 32w + lane; rows 2i and 2i+1 (real and
-  // imaginary parts of column i of A) sit in neighbouring lanes
-  if (warp < 4) {
-    const int rho = warp * 32 + lane;
-    const int i = rho >> 1;
-    double2* Gb = G + (long)bc * m * m;
-    for (int cb = 0; cb < kTcN / 32; ++cb) {
-      uint32_t r[32];
-      const uint32_t a = taddr + ((uint32_t)(warp * 32) << 16) + cb * 32;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-            "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-            "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-            "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-            "=r"(r[31])
-          : "r"(a));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int cb = 0; cb < kTcCols / 16; ++cb) {
+        float v[16];
+        if (X3) {
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        // D[2i][2jj], D[2i][2jj+1] here; D[2i+1][2jj], D[2i+1][2jj+1] in lane + 1
-        const float re_re = __uint_as_float(r[2 * t]), re_im = __uint_as_float(r[2 * t + 1]);
-        const float im_re = __shfl_down_sync(0xffffffffu, re_re, 1);
-        const float im_im = __shfl_down_sync(0xffffffffu, re_im, 1);
-        const int jj = cb * 16 + t;
-        if ((lane & 1) == 0 && i < m && jj < m)
-          Gb[(long)i * m + jj] =
-              make_double2((double)re_re + (double)im_im, (double)re_im - (double)im_re);
+          for (int t = 0; t < 16; ++t) v[t] = acc[cb * 16 + t];
+        } else {
+          tmem_ld16(taddr + lane_base + cb * 16, v);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const float re_re = v[2 * t], re_im = v[2 * t + 1];
+          const float im_re = __shfl_down_sync(0xffffffffu, re_re, 1);
+          const float im_im = __shfl_down_sync(0xffffffffu, re_im, 1);
+          const int jj = cb * 8 + t;
+          if ((lane & 1) == 0 && i < m && jj < m)
+            Gb[(long)i * m + jj] = make_double2(((double)re_re + (double)im_im) * inv,
+                                                ((double)re_im - (double)im_re) * inv);
+        }
       }
     }
+    sync_before();
+    __syncthreads();
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  // on a timeout: let the MMAs already committed finish before TMEM is freed
+  if (s_abort && threadIdx.x == 0 && gidx > 0) (void)bar_wait(&bar[(gidx - 1) & 1], (gidx - 1) >> 1);
+  sync_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcN)
-                 : "memory");
+    sync_after();
+    tmem_dealloc(taddr, TCOLS);
   }
-  if (!ok && tid == 0) atomicOr(status, 2);
+  if (s_abort && threadIdx.x == 0) atomicOr(status, 2);
+}
+
+// ---------------------------------------------------------------------------
+// GEMM kernel: C[bc] = A B[bc] with FP16X3 operands.  B: [bc][m'][n] complex
+// (row-major); C: rows [bc][K][n] complex.  Scale of A from gdiag (the
+// diagonal of a Gram of A bounds every entry: |a_ri|^2 <= G_ii), else from
+// abound[bc], else 1; scale of B from its largest entry.  cmax (optional):
+// per-bc largest |re| or |im| of C.  As in the Gram kernel, every TMEM
+// accumulation is short: per chunk, D1 = sum over the 2m'/16 K steps of the
+// hi*hi products and D2 of the hi*lo + lo*hi products, added on the CUDA
+// cores in the epilogue.  (D1, D2) are double buffered in TMEM, so the
+// epilogue of chunk c-1 overlaps the MMAs of chunk c.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_gemm_kernel(TcRows g, const double2* __restrict__ gdiag, const float* __restrict__ abound,
+                   const float2* __restrict__ B, int n, float2* __restrict__ C,
+                   float* __restrict__ cmax, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  const int npad = ((2 * n + 15) / 16) * 16;
+  // (D1, D2) x 2 slots of npad columns, rounded up to a power of two
+  const int tcols = npad <= 16 ? 64 : (npad <= 32 ? 128 : (npad <= 64 ? 256 : 512));
+  unsigned char* atiles = tc_smem;                    // [2 buffers][hi, lo][kTcTile]
+  unsigned char* bhi = tc_smem + 4 * kTcTile;         // [npad / 8][2048]
+  unsigned char* blo = bhi + (npad / 8) * kTcSbo;
+  long* table = reinterpret_cast<long*>(blo + (npad / 8) * kTcSbo);
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  __shared__ float red[kTcThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) tmem_alloc(&tmem_base, tcols);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  sync_before();
+  __syncthreads();
+  sync_after();
+  const uint32_t taddr = tmem_base;
+  const uint32_t idesc = idesc_f16(npad, 0);
+  const int m = g.m, nreal = 2 * m;
+  const int ksteps = (nreal + 15) / 16;
+  const int nchunk = (g.K + kTcRows - 1) / kTcRows;
+  int gidx = 0;
+  int last_j = -1;
+  float inv = 1.f;
+  float cm = 0.f;  // this thread's largest |C| entry of the current bc
+
+  // epilogue of chunk cc of bc from TMEM slot d: warp w reads TMEM lanes
+  // 32 (w & 3) .. + 31 (rows of the chunk) and the column blocks cb = w >> 2,
+  // w >> 2 + 2, ...
+  auto epilogue = [&](int bc, int cc, int d) {
+    sync_after();
+    const int rl = (warp & 3) * 32 + lane, r = cc * kTcRows + rl;
+    float2* out = C + ((long)bc * g.K + r) * n;
+#pragma unroll 1
+    for (int cb = warp >> 2; cb < npad / 16; cb += 2) {
+      float v[16], w[16];
+      const uint32_t a = taddr + ((uint32_t)((warp & 3) * 32) << 16) + d * 2 * npad + cb * 16;
+      tmem_ld16(a, v);
+      tmem_ld16(a + npad, w);
+      if (r < g.K) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int jj = cb * 8 + t;
+          if (jj < n) {
+            const float2 z = make_float2((v[2 * t] + w[2 * t]) * inv,
+                                         (v[2 * t + 1] + w[2 * t + 1]) * inv);
+            out[jj] = z;
+            cm = fmaxf(cm, fmaxf(fabsf(z.x), fabsf(z.y)));
+          }
+        }
+      }
+    }
+  };
+
+  for (int bc = blockIdx.x; bc < g.nbc; bc += gridDim.x) {
+    if (g.gather && (bc >> 1) != last_j) {
+      last_j = bc >> 1;
+      fill_site_table(g, last_j, table);
+    }
+    // scales of A and B
+    float abnd = 1.f;
+    if (gdiag) {
+      const double2* Gb = gdiag + (long)bc * m * m;
+      double mx = 0;
+      for (int i = 0; i < m; ++i) mx = fmax(mx, Gb[(long)i * m + i].x);
+      abnd = (float)sqrt(mx);
+    } else if (abound) {
+      abnd = abound[bc];
+    }
+    const float sa = scale_for(abnd);
+    const float2* Bb = B + (long)bc * m * n;
+    float bm = 0.f;
+    for (int i = threadIdx.x; i < m * n; i += blockDim.x) {
+      const float2 z = __ldg(Bb + i);
+      bm = fmaxf(bm, fmaxf(fabsf(z.x), fabsf(z.y)));
+    }
+    const float sb = scale_for(block_max(bm, red));
+    inv = 1.f / (sa * sb);
+    // B~^T tiles: row n' = 2jj + bb (output real column), K column k' = 2ii + a
+    for (int idx = threadIdx.x; idx < npad * (kTcCols / 8); idx += blockDim.x) {
+      const int np_ = idx % npad, kg = idx / npad;
+      const int jj = np_ >> 1, bb = np_ & 1;
+      float v[8];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int ii = 4 * kg + t;
+        float2 z = make_float2(0.f, 0.f);
+        if (ii < m && jj < n) z = __ldg(Bb + (long)ii * n + jj);
+        // a = 0 (re a_ii): re b / im b;  a = 1 (im a_ii): -im b / re b
+        v[2 * t] = bb ? z.y : z.x;
+        v[2 * t + 1] = bb ? z.x : -z.y;
+      }
+      uint4 h, l;
+      split8<TC_FP16X3>(v, sb, h, l);
+      const uint32_t o = (np_ >> 3) * kTcSbo + kg * 128 + (np_ & 7) * 16;
+      *reinterpret_cast<uint4*>(bhi + o) = h;
+      *reinterpret_cast<uint4*>(blo + o) = l;
+    }
+    cm = 0.f;
+    __syncthreads();
+    for (int c = 0; c < nchunk; ++c, ++gidx) {
+      const int b = gidx & 1;
+      unsigned char* ahi = atiles + 2 * b * kTcTile;
+      unsigned char* alo = ahi + kTcTile;
+      // the MMAs that read this buffer (and TMEM slot) two chunks ago are done
+      if (gidx >= 2 && !bar_wait(&bar[b], (gidx - 2) >> 1)) s_abort = 1;
+      __syncthreads();
+      if (s_abort) break;
+      stage_gemm_rows(g, table, bc, c, sa, ahi, alo);
+      fence_async();
+      sync_before();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        sync_after();
+        const uint32_t d1 = taddr + b * 2 * npad, d2 = d1 + npad;
+#pragma unroll 1
+        for (int k = 0; k < ksteps; ++k) {
+          const uint64_t dah = smem_desc(su32(ahi) + k * 256, 128, kTcSbo);
+          const uint64_t dal = smem_desc(su32(alo) + k * 256, 128, kTcSbo);
+          const uint64_t dbh = smem_desc(su32(bhi) + k * 256, 128, kTcSbo);
+          const uint64_t dbl = smem_desc(su32(blo) + k * 256, 128, kTcSbo);
+          mma(d1, dah, dbh, idesc, k > 0 ? 1u : 0u);
+          mma(d2, dah, dbl, idesc, k > 0 ? 1u : 0u);
+          mma(d2, dal, dbh, idesc, 1u);
+        }
+        commit(&bar[b]);
+      }
+      if (c > 0) {
+        // chunk c-1 (committed as gidx-1) while chunk c multiplies
+        if (!bar_wait(&bar[(gidx - 1) & 1], (gidx - 1) >> 1)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) break;
+        epilogue(bc, c - 1, (gidx - 1) & 1);
+      }
+      sync_before();
+      __syncthreads();
+    }
+    if (s_abort) break;
+    // the last chunk of this bc
+    if (!bar_wait(&bar[(gidx - 1) & 1], (gidx - 1) >> 1)) s_abort = 1;
+    __syncthreads();
+    if (s_abort) break;
+    epilogue(bc, nchunk - 1, (gidx - 1) & 1);
+    sync_before();
+    const float bcm = block_max(cm, red);  // (synchronises)
+    if (cmax && threadIdx.x == 0) cmax[bc] = bcm;
+  }
+  if (s_abort && threadIdx.x == 0 && gidx > 0) (void)bar_wait(&bar[(gidx - 1) & 1], (gidx - 1) >> 1);
+  sync_before();
+  __syncthreads();
+  if (warp == 0) {
+    sync_after();
+    tmem_dealloc(taddr, tcols);
+  }
+  if (s_abort && threadIdx.x == 0) atomicOr(status, 2);
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin coarsening D_c = P^dag D P (paper Sec. 2, Eq. 3) on the tensor
+// cores.  The spin projection of the hop gives, per site x and chirality
+// columns (alpha, i) of the prolongator P(x) = diag(P_0(x), P_1(x)):
+//   P(x)^dag (1 - gamma_mu) U P(y) = Pi_mu(x)^dag (1_2 x U) Pi_mu(y),
+//   Pi_mu = [P_0, -B_mu P_1]                (6 x 2k: 2 spins x 3 colours),
+// so every term is a depth-6 product conj(L_x)^T R_x of two 6 x 2k matrices.
+// Six passes per block j (as the CUDA-core coarsen_kernel):
+//   passes 0, 1 (chirality alpha): L = P_alpha(x), R = 1/2 (m0 + sum w + C_alpha(x)) P_alpha(x)
+//   passes 2..5 (mu = 0..3):       L = Pi_mu(x), R = hw_mu U_mu(x) Pi_mu(x + mu)
+// summed over the block's sites into S (site term and hops that stay in the
+// block) or, for the sites on the block's +mu face, into Y_{+mu}; then
+// X = S + sigma_3 S^dag sigma_3 and Y_{-mu}(j + mu) = sigma_3 Y_{+mu}(j)^dag sigma_3.
+// Over the reals, with 8 rows per site (the 6 of L or R and two zero rows)
+// and chunks of 8 sites, a chunk is D = L~^T R~ with M = 4k real columns of
+// L~ (padded to 128), N = 4k padded to a multiple of 32, K = 64, operands
+// FP16 hi/lo (P and L scaled by 2^14: every entry of a block-orthonormal P
+// is at most 1 in modulus; R by 2^8: |R| <= 64).  Per chunk D1 (hi*hi) and
+// D2 (hi*lo + lo*hi) accumulate in TMEM from zero and are added on the CUDA
+// cores into registers: warp w owns TMEM lanes 32 (w & 3) .. + 31 (rows of
+// D) and column half w >> 2; S and Y are kept per thread.
+// ---------------------------------------------------------------------------
+struct TcCoarsen {
+  const float2* U;
+  const float2* C;
+  const float2* P;
+  float2* X;
+  float2* Y;
+  int L[4], b[4], Lc[4];
+  int nb, k, nblk;
+  float hw[4];
+  float diag;
+};
+
+constexpr int kCsSites = 8;                    // sites per chunk
+constexpr int kCsSbo = kCsSites * 128;         // bytes between 8-row groups (K = 64)
+constexpr int kCsTileL = (kTcCols / 8) * kCsSbo;  // L~^T tile: M = 128 (16 KB)
+constexpr float kCsScaleL = 16384.f;           // 2^14
+constexpr float kCsScaleR = 256.f;             // 2^8
+
+// Pi_mu's lower-chirality columns: row sp of -B_mu has a single non-zero
+// entry -B_mu[sp][t] = g
+__device__ __forceinline__ void tc_pi_entry(int mu, int sp, int& t, float2& g) {
+  if (mu == 0) { t = 1 - sp; g = make_float2(0.f, 1.f); }
+  else if (mu == 1) { t = 1 - sp; g = make_float2(sp == 0 ? 1.f : -1.f, 0.f); }
+  else if (mu == 2) { t = sp; g = make_float2(0.f, sp == 0 ? 1.f : -1.f); }
+  else { t = sp; g = make_float2(-1.f, 0.f); }
+}
+
+// site t of the pass's group: group 0 = all sites (mu < 0) or the sites off
+// the +mu face, group 1 = the +mu face; returns the global site and, for
+// mu >= 0, its +mu neighbour
+__device__ __forceinline__ int cs_site(const TcCoarsen& a, int j, int mu, int grp, int t,
+                                       int* nbr) {
+  int jc[4], ext[4], off[4] = {0, 0, 0, 0};
+  int u = j;
+  jc[0] = u % a.Lc[0]; u /= a.Lc[0];
+  jc[1] = u % a.Lc[1]; u /= a.Lc[1];
+  jc[2] = u % a.Lc[2]; jc[3] = u / a.Lc[2];
+  for (int d = 0; d < 4; ++d) ext[d] = a.b[d];
+  if (mu >= 0) {
+    if (grp == 0) ext[mu] = a.b[mu] - 1;
+    else { ext[mu] = 1; off[mu] = a.b[mu] - 1; }
+  }
+  int xo[4];
+  for (int d = 0; d < 4; ++d) {
+    xo[d] = jc[d] * a.b[d] + off[d] + t % ext[d];
+    t /= ext[d];
+  }
+  const int x = xo[0] + a.L[0] * (xo[1] + a.L[1] * (xo[2] + a.L[2] * xo[3]));
+  if (mu >= 0) {
+    xo[mu] = (xo[mu] + 1) % a.L[mu];
+    *nbr = xo[0] + a.L[0] * (xo[1] + a.L[1] * (xo[2] + a.L[2] * xo[3]));
+  }
+  return x;
+}
+
+// stage chunk: L~^T and R~^T tiles (element (real column q, row 8s + e) at
+// (q>>3)*1024 + s*128 + (q&7)*16 + e*2)
+__device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const int* s_nbr,
+                         unsigned char* lhi, unsigned char* llo, unsigned char* rhi,
+                         unsigned char* rlo) {
+  const int k = a.k, n2 = 2 * k;
+  const int mu = pass - 2;
+  for (int it = threadIdx.x; it < kCsSites * n2; it += blockDim.x) {
+    const int s = it / n2, col = it % n2;
+    const int x = s_site[s];
+    float2 Lv[6], Rv[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) Lv[e] = Rv[e] = make_float2(0.f, 0.f);
+    const int al = col / k, i = col % k;
+    if (x >= 0) {
+      const float2* Px = a.P + (long)x * 12 * k;  // [2][6][k]
+      if (mu < 0) {
+        if (al == pass) {
+#pragma unroll
+          for (int e = 0; e < 6; ++e) Lv[e] = __ldg(Px + (al * 6 + e) * k + i);
+#pragma unroll
+          for (int e = 0; e < 6; ++e) {
+            float2 r = cscale(Lv[e], 0.5f * a.diag);
+            if (a.C) {
+              const float2* cl = a.C + (long)x * 72 + al * 36 + e * 6;
+#pragma unroll
+              for (int f = 0; f < 6; ++f) cfma(r, cscale(__ldg(cl + f), 0.5f), Lv[f]);
+            }
+            Rv[e] = r;
+          }
+        }
+      } else {
+        const float2* Py = a.P + (long)s_nbr[s] * 12 * k;
+        const float2* u = a.U + ((long)x * 4 + mu) * 9;
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+          int tt;
+          float2 ph;
+          tc_pi_entry(mu, sp, tt, ph);
+          const int o = al == 0 ? (sp * 3) * k + i : (6 + tt * 3) * k + i;
+          float2 py[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const float2 vx = __ldg(Px + o + d * k), vy = __ldg(Py + o + d * k);
+            Lv[sp * 3 + d] = al == 0 ? vx : cmul(ph, vx);
+            py[d] = al == 0 ? vy : cmul(ph, vy);
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cfma(acc, __ldg(u + c * 3 + d), py[d]);
+            Rv[sp * 3 + c] = cscale(acc, a.hw[mu]);
+          }
+        }
+      }
+    }
+    float lre[8], lim[8], rre[8], rim[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      lre[e] = e < 6 ? Lv[e < 6 ? e : 0].x : 0.f;
+      lim[e] = e < 6 ? Lv[e < 6 ? e : 0].y : 0.f;
+      rre[e] = e < 6 ? Rv[e < 6 ? e : 0].x : 0.f;
+      rim[e] = e < 6 ? Rv[e < 6 ? e : 0].y : 0.f;
+    }
+    uint4 h, l;
+    const int q = 2 * col;
+    const uint32_t o0 = (q >> 3) * kCsSbo + s * 128 + (q & 7) * 16;
+    split8<TC_FP16X3>(lre, kCsScaleL, h, l);
+    *reinterpret_cast<uint4*>(lhi + o0) = h;
+    *reinterpret_cast<uint4*>(llo + o0) = l;
+    split8<TC_FP16X3>(lim, kCsScaleL, h, l);
+    *reinterpret_cast<uint4*>(lhi + o0 + 16) = h;
+    *reinterpret_cast<uint4*>(llo + o0 + 16) = l;
+    split8<TC_FP16X3>(rre, kCsScaleR, h, l);
+    *reinterpret_cast<uint4*>(rhi + o0) = h;
+    *reinterpret_cast<uint4*>(rlo + o0) = l;
+    split8<TC_FP16X3>(rim, kCsScaleR, h, l);
+    *reinterpret_cast<uint4*>(rhi + o0 + 16) = h;
+    *reinterpret_cast<uint4*>(rlo + o0 + 16) = l;
+  }
+}
+
+template <int NPAD>
+__global__ void __launch_bounds__(kTcThreads, 1) tc_coarsen_kernel(TcCoarsen a,
+                                                                   int* __restrict__ status) {
+  constexpr int NH = NPAD / 2;                        // columns per thread
+  constexpr int TCOLS = 4 * NPAD <= 256 ? 256 : 512;  // (D1, D2) x 2 slots
+  constexpr int kTileR = (NPAD / 8) * kCsSbo;
+  constexpr int kBuf = 2 * kCsTileL + 2 * kTileR;     // one staging buffer
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  float2* Ms = reinterpret_cast<float2*>(tc_smem + 2 * kBuf);  // [2k][2k + 1]
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  __shared__ int s_site[2][kCsSites], s_nbr[2][kCsSites];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = a.k, n2 = 2 * k;
+  const int half = warp >> 2;
+  // zero both staging buffers once: padding rows (real columns >= 4k) are never written
+  for (int i = threadIdx.x; i < 2 * kBuf / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(tc_smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) tmem_alloc(&tmem_base, TCOLS);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  sync_before();
+  __syncthreads();
+  sync_after();
+  const uint32_t taddr = tmem_base;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t idesc = idesc_f16(NPAD, 0);
+  const float inv = 1.f / (kCsScaleL * kCsScaleR);
+  float Sr[NH], Yr[NH];
+  int gidx = 0;
+
+  // add the chunk in TMEM slot d to Sr (to_y = 0) or Yr
+  auto add_chunk = [&](int d, int to_y) {
+    sync_after();
+#pragma unroll
+    for (int cb = 0; cb < NH / 16; ++cb) {
+      float v1[16], v2[16];
+      const uint32_t ad = taddr + lane_base + d * 2 * NPAD + half * NH + cb * 16;
+      tmem_ld16(ad, v1);
+      tmem_ld16(ad + NPAD, v2);
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        if (to_y) Yr[cb * 16 + t] += v1[t] + v2[t];
+        else Sr[cb * 16 + t] += v1[t] + v2[t];
+      }
+    }
+  };
+  // the complex 2k x 2k matrix of the real accumulator R (this thread's row
+  // and column half) into Ms
+  auto to_ms = [&](const float* R) {
+    const int rho = (warp & 3) * 32 + lane, c1 = rho >> 1;
+#pragma unroll
+    for (int t = 0; t < NH / 2; ++t) {
+      const float re_re = R[2 * t], re_im = R[2 * t + 1];
+      const float im_re = __shfl_down_sync(0xffffffffu, re_re, 1);
+      const float im_im = __shfl_down_sync(0xffffffffu, re_im, 1);
+      const int c2 = (half * NH) / 2 + t;
+      if ((lane & 1) == 0 && c1 < n2 && c2 < n2)
+        Ms[c1 * (n2 + 1) + c2] = make_float2((re_re + im_im) * inv, (re_im - im_re) * inv);
+    }
+  };
+
+  for (int j = blockIdx.x; j < a.nblk && !s_abort; j += gridDim.x) {
+#pragma unroll
+    for (int t = 0; t < NH; ++t) Sr[t] = 0.f;
+    int pend = -1, pend_y = 0;  // TMEM slot awaiting its epilogue, and its target
+    for (int pass = 0; pass < 6 && !s_abort; ++pass) {
+      const int mu = pass - 2;
+#pragma unroll
+      for (int t = 0; t < NH; ++t) Yr[t] = 0.f;
+      for (int grp = 0; grp < (mu < 0 ? 1 : 2) && !s_abort; ++grp) {
+        const int cnt = mu < 0 ? a.nb : (grp == 0 ? a.nb - a.nb / a.b[mu] : a.nb / a.b[mu]);
+        for (int c0 = 0; c0 < cnt; c0 += kCsSites, ++gidx) {
+          const int b = gidx & 1;
+          unsigned char* lhi = tc_smem + b * kBuf;
+          unsigned char* llo = lhi + kCsTileL;
+          unsigned char* rhi = llo + kCsTileL;
+          unsigned char* rlo = rhi + kTileR;
+          if (gidx >= 2 && !bar_wait(&bar[b], (gidx - 2) >> 1)) s_abort = 1;
+          if (threadIdx.x < kCsSites) {
+            const int t = c0 + threadIdx.x;
+            int nb_ = -1;
+            s_site[b][threadIdx.x] = t < cnt ? cs_site(a, j, mu, grp, t, &nb_) : -1;
+            s_nbr[b][threadIdx.x] = nb_;
+          }
+          __syncthreads();
+          if (s_abort) break;
+          cs_stage(a, pass, s_site[b], s_nbr[b], lhi, llo, rhi, rlo);
+          fence_async();
+          sync_before();
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            sync_after();
+            const uint32_t d1 = taddr + b * 2 * NPAD, d2 = d1 + NPAD;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t dlh = smem_desc(su32(lhi) + kk * 256, 128, kCsSbo);
+              const uint64_t dll = smem_desc(su32(llo) + kk * 256, 128, kCsSbo);
+              const uint64_t drh = smem_desc(su32(rhi) + kk * 256, 128, kCsSbo);
+              const uint64_t drl = smem_desc(su32(rlo) + kk * 256, 128, kCsSbo);
+              mma(d1, dlh, drh, idesc, kk > 0 ? 1u : 0u);
+              mma(d2, dlh, drl, idesc, kk > 0 ? 1u : 0u);
+              mma(d2, dll, drh, idesc, 1u);
+            }
+            commit(&bar[b]);
+          }
+          if (pend >= 0) {
+            if (!bar_wait(&bar[pend], (gidx - 1) >> 1)) s_abort = 1;
+            __syncthreads();
+            if (s_abort) break;
+            add_chunk(pend, pend_y);
+          }
+          pend = b;
+          pend_y = mu >= 0 && grp == 1;
+          sync_before();
+          __syncthreads();
+        }
+      }
+      if (s_abort) break;
+      if (mu >= 0) {
+        // drain, then Y_{+mu}(j) and Y_{-mu}(j + mu) = sigma_3 Y_{+mu}(j)^dag sigma_3
+        if (pend >= 0) {
+          if (!bar_wait(&bar[pend], (gidx - 1) >> 1)) s_abort = 1;
+          __syncthreads();
+          if (s_abort) break;
+          add_chunk(pend, pend_y);
+          pend = -1;
+        }
+        to_ms(Yr);
+        __syncthreads();
+        int jc[4];
+        {
+          int u = j;
+          jc[0] = u % a.Lc[0]; u /= a.Lc[0];
+          jc[1] = u % a.Lc[1]; u /= a.Lc[1];
+          jc[2] = u % a.Lc[2]; jc[3] = u / a.Lc[2];
+        }
+        jc[mu] = (jc[mu] + 1) % a.Lc[mu];
+        const int jn = jc[0] + a.Lc[0] * (jc[1] + a.Lc[1] * (jc[2] + a.Lc[2] * jc[3]));
+        for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
+          const int r = idx / n2, c = idx % n2;
+          a.Y[(((long)j * 8 + mu) * n2 + r) * n2 + c] = Ms[r * (n2 + 1) + c];
+          float2 v = cconj(Ms[c * (n2 + 1) + r]);
+          if ((r < k) != (c < k)) v = make_float2(-v.x, -v.y);
+          a.Y[(((long)jn * 8 + 4 + mu) * n2 + r) * n2 + c] = v;
+        }
+        sync_before();
+        __syncthreads();
+      }
+    }
+    if (s_abort) break;
+    if (pend >= 0) {
+      if (!bar_wait(&bar[pend], (gidx - 1) >> 1)) s_abort = 1;
+      __syncthreads();
+      if (s_abort) break;
+      add_chunk(pend, pend_y);
+    }
+    // X = S + sigma_3 S^dag sigma_3
+    to_ms(Sr);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
+      const int r = idx / n2, c = idx % n2;
+      float2 v = cconj(Ms[c * (n2 + 1) + r]);
+      if ((r < k) != (c < k)) v = make_float2(-v.x, -v.y);
+      a.X[((long)j * n2 + r) * n2 + c] = cadd(Ms[r * (n2 + 1) + c], v);
+    }
+    sync_before();
+    __syncthreads();
+  }
+  if (s_abort && threadIdx.x == 0 && gidx > 0) (void)bar_wait(&bar[(gidx - 1) & 1], (gidx - 1) >> 1);
+  sync_before();
+  __syncthreads();
+  if (warp == 0) {
+    sync_after();
+    tmem_dealloc(taddr, TCOLS);
+  }
+  if (s_abort && threadIdx.x == 0) atomicOr(status, 2);
+}
+
+template <int NPAD>
+size_t cs_smem(int k) {
+  return (size_t)2 * (2 * kCsTileL + 2 * (NPAD / 8) * kCsSbo) +
+         sizeof(float2) * (size_t)(2 * k) * (2 * k + 1);
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    return 148;
+  return n;
+}
+
+TcRows tc_rows(const Geom& g, const float2* src, bool gather) {
+  TcRows r;
+  r.src = reinterpret_cast<const float*>(src);
+  r.gather = gather ? 1 : 0;
+  for (int i = 0; i < 4; ++i) {
+    r.L[i] = g.L[i];
+    r.b[i] = g.b[i];
+    r.Lc[i] = g.Lc[i];
+  }
+  r.nb = g.nb;
+  r.K = 6 * g.nb;
+  r.m = g.m;
+  r.nbc = (int)(2 * g.nblk);
+  return r;
+}
+
+size_t gram_smem(int prec) {
+  return (size_t)2 * (prec == TC_FP16X3 ? 2 : 1) * kTcTile + sizeof(long) * kTcMaxSites;
+}
+size_t gemm_smem(int n) {
+  const int npad = ((2 * n + 15) / 16) * 16;
+  return (size_t)4 * kTcTile + (size_t)2 * (npad / 8) * kTcSbo + sizeof(long) * kTcMaxSites;
 }
 
 }  // namespace
 
-bool gram_tc_supported(const Geom& g) { return 2 * g.m <= kTcN; }
+bool tc_supported(const Geom& g) {
+  return g.rps == 6 && 2 * g.m <= kTcCols && g.nb <= kTcMaxSites && 2 * g.k <= kTcCols;
+}
 
-cudaError_t launch_gram_tc(const Geom& g, const float2* psi, double2* G, int* status,
-                           cudaStream_t s) {
+cudaError_t launch_tc_gram(const Geom& g, const float2* A, bool gather, bool fp16x3,
+                           const float* bound, double2* G, int* status, cudaStream_t s,
+                           const char* name) {
   static PerDeviceOnce attr_once;
   attr_once.run([&] {
-    cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(tc_gram_kernel<TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)gram_smem(TC_BF16));
+    cudaFuncSetAttribute(tc_gram_kernel<TC_FP16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)gram_smem(TC_FP16X3));
   });
-  TcGeom tg;
+  const TcRows r = tc_rows(g, A, gather);
+  // BF16: three CTAs per SM fit (shared memory; 3 x 128 TMEM columns)
+  const int per_sm = fp16x3 ? 1 : 3;
+  const int grid = (int)std::min<long>(r.nbc, (long)num_sms() * per_sm);
+  TimedScope ts(name, s);
+  if (fp16x3)
+    tc_gram_kernel<TC_FP16X3><<<grid, kTcThreads, gram_smem(TC_FP16X3), s>>>(r, bound, G, status);
+  else
+    tc_gram_kernel<TC_BF16><<<grid, kTcThreads, gram_smem(TC_BF16), s>>>(r, bound, G, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm(const Geom& g, const float2* A, bool gather, const double2* gdiag,
+                           const float* abound, const float2* B, int n, float2* C, float* cmax,
+                           int* status, cudaStream_t s, const char* name) {
+  static PerDeviceOnce attr_once;
+  attr_once.run([&] {
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)gemm_smem(kTcCols / 2));
+  });
+  const TcRows r = tc_rows(g, A, gather);
+  const int grid = (int)std::min<long>(r.nbc, (long)num_sms());
+  TimedScope ts(name, s);
+  tc_gemm_kernel<<<grid, kTcThreads, gemm_smem(n), s>>>(r, gdiag, abound, B, n, C, cmax,
+                                                        status);
+  return cudaGetLastError();
+}
+
+bool tc_coarsen_supported(const Geom& g) { return g.rps == 6 && g.k <= 32; }
+
+cudaError_t launch_tc_coarsen(const Geom& g, const float2* U, const float2* C, const float2* P,
+                              float2* X, float2* Y, int* status, cudaStream_t s) {
+  TcCoarsen a;
+  a.U = U;
+  a.C = C;
+  a.P = P;
+  a.X = X;
+  a.Y = Y;
   for (int i = 0; i < 4; ++i) {
-    tg.L[i] = g.L[i];
-    tg.b[i] = g.b[i];
-    tg.Lc[i] = g.Lc[i];
+    a.L[i] = g.L[i];
+    a.b[i] = g.b[i];
+    a.Lc[i] = g.Lc[i];
+    a.hw[i] = g.hw[i];
   }
-  tg.nb = g.nb;
-  tg.m = g.m;
-  TimedScope ts("trunc_gram_tc", s);
-  gram_tc_kernel<<<(int)(2 * g.nblk), 256, kTcSmem, s>>>(reinterpret_cast<const float*>(psi), G,
-                                                         tg, status);
+  a.nb = g.nb;
+  a.k = g.k;
+  a.nblk = (int)g.nblk;
+  a.diag = g.diag;
+  const int npad = ((4 * g.k + 31) / 32) * 32;
+  const int grid = (int)std::min<long>(g.nblk, (long)num_sms());
+  TimedScope ts("coarsen_tc", s);
+  switch (npad) {
+#define MG_CS_CASE(NP)                                                                       \
+  case NP: {                                                                                 \
+    static PerDeviceOnce attr_once;                                                          \
+    attr_once.run([&] {                                                                      \
+      cudaFuncSetAttribute(tc_coarsen_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           (int)cs_smem<NP>(NP / 4));                                        \
+    });                                                                                      \
+    tc_coarsen_kernel<NP><<<grid, kTcThreads, cs_smem<NP>(g.k), s>>>(a, status);             \
+    break;                                                                                   \
+  }
+    MG_CS_CASE(32)
+    MG_CS_CASE(64)
+    MG_CS_CASE(96)
+    MG_CS_CASE(128)
+#undef MG_CS_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

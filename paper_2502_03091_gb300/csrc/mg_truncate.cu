@@ -2,8 +2,7 @@
 // Sec. 3 Eq. 4).  For every block Lambda_j and chirality alpha the
 // K x m' matrix A = Psi^(alpha)(Lambda_j), K = 6 |Lambda_j| (rows: site,
 // spin in chirality, colour), is factored as
-//   G1 = A^dag A                  (FP32 products, FP64 across row chunks; BF16
-//                                  tensor cores in the mixed-precision path)
+//   G1 = A^dag A                  (FP32 products, FP64 across row chunks)
 //   R1 = chol(G1)                 (FP64)
 //   Q1 = A R1^{-1}, G2 = Q1^dag Q1 (FP32, Q1 never stored)
 //   R2 = chol(G2), R = R2 R1      (FP32 on the deviations from 1; R in FP64)
@@ -15,6 +14,8 @@
 // so U_k are the k leading left singular vectors of A (A = Q R, R = U~ S V~^dag),
 // the best rank-k basis of Eq. (4).  The chiral split itself is only the
 // choice of rows: chirality 0 is spins {0,1}, chirality 1 spins {2,3}.
+// In the mixed-precision paths G1, Q1 (then stored), G2 and U_k = Q1 (R2^-1 U~_k)
+// are tensor-core contractions (mg_tc.cu); the small FP64 stages are shared.
 #include "mg_common.cuh"
 
 namespace mg {
@@ -977,14 +978,37 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
     cudaFuncSetAttribute(svd_stage2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
     cudaFuncSetAttribute(form_uk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
   });
-  if (g.prec == MG_PREC_MIXED && g.rps == 6 && gram_tc_supported(g)) {
-    // mixed precision: G1 on the tensor cores in BF16 (CholeskyQR2's second
-    // pass, below, is FP32 and restores the orthonormality)
+  if (g.prec != MG_PREC_FP32 && tc_supported(g) && lay.q1) {
+    // mixed precision: the dense contractions on the tensor cores
+    //   G1 = A^dag A (BF16: it only preconditions the second pass)
+    //   R1 = chol(G1), Z1 = R1^-1 (FP64 / FP32, CUDA cores)
+    //   Q1 = A Z1 (FP16 hi/lo), stored, and its largest entry
+    //   G2 = Q1^dag Q1 (FP16 hi/lo)
+    //   R2 = chol(G2), R = R2 R1, eigen-decomposition of R R^dag (as FP32 path)
+    //   U_k = Q1 W2 with W2 = R2^-1 U~_k (FP16 hi/lo), straight into Uk
     int* st = device_status_word();
     if (!st) return cudaErrorInvalidSymbol;
-    cudaError_t e = launch_gram_tc(g, psi, G, st, s);
+    float2* Q1 = reinterpret_cast<float2*>(ws + lay.q1);
+    float* qmax = reinterpret_cast<float*>(ws + lay.qmax);
+    cudaError_t e = launch_tc_gram(g, psi, true, false, nullptr, G, st, s, "trunc_gram_tc");
     if (e != cudaSuccess) return e;
-  } else {
+    {
+      TimedScope ts("trunc_chol64", s);
+      chol_stage1<<<nbc, kThreads, sm_chol, s>>>(G, R1, Z1, flags, m);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_tc_gemm(g, psi, true, G, nullptr, Z1, m, Q1, qmax, st, s, "trunc_q1_tc");
+    if (e != cudaSuccess) return e;
+    e = launch_tc_gram(g, Q1, false, true, qmax, G, st, s, "trunc_gram2_tc");
+    if (e != cudaSuccess) return e;
+    {
+      TimedScope ts("trunc_chol_eig64", s);
+      svd_stage2<<<nbc, kThreads, sm_svd, s>>>(G, R1, Hm, W2, sigma, coarse_tv, flags, m, k);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_tc_gemm(g, Q1, false, nullptr, qmax, W2, k, Uk, nullptr, st, s, "trunc_uk_tc");
+  }
+  {
     TimedScope ts("trunc_gram", s);
     gram_kernel<false><<<nbc, kThreads, sm_gram0, s>>>(psi, nullptr, G, bg);
   }

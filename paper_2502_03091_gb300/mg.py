@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_SHAPE", 3: "MG_ERR_N
                 7: "MG_ERR_UNSUPPORTED"}
 MG_PREC_FP32 = 0
 MG_PREC_MIXED = 1
+MG_PREC_MIXED_FP16 = 2
 MG_ERR_TIMEOUT = 6
 MG_CALL_SMOOTH, MG_CALL_TRUNCATE, MG_CALL_COARSEN = 0, 1, 2
 
@@ -31,6 +32,7 @@ EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_apply_dirac", "mg_smooth_
            "mg_timing_enable",
            "mg_timing_read", "mg_batch_create", "mg_batch_launch", "mg_batch_streams",
            "mg_batch_destroy", "mg_tuned_pairs", "mg_sync_status", "mg_last_error", "mg_version",
+           "mg_selftest_timeout",
            "mg_coarse_workspace_size", "mg_coarse_op_apply", "mg_coarse_smooth_testvecs",
            "mg_coarse_chiral_truncate", "mg_coarse_build_prolongator", "mg_coarse_coarsen",
            "mg_solve_workspace_size", "mg_solve")
@@ -215,6 +217,8 @@ def library(path: str = LIB_PATH):
     lib.mg_tuned_pairs.restype = ctypes.c_int
     lib.mg_sync_status.argtypes = [P]
     lib.mg_sync_status.restype = ctypes.c_int
+    lib.mg_selftest_timeout.argtypes = [ctypes.c_int32, P]
+    lib.mg_selftest_timeout.restype = ctypes.c_int
     lib.mg_last_error.restype = ctypes.c_char_p
     lib.mg_version.restype = ctypes.c_char_p
     _lib = lib
@@ -273,6 +277,12 @@ def mg_sync_status(stream=None):
     operator pass enqueued since the previous call gave up waiting for its
     staged input."""
     _check(library().mg_sync_status(_stream(stream)))
+
+
+def mg_selftest_timeout(polls: int, stream=None):
+    """Enqueues the failure-detection self-test: one bounded device wait that
+    runs out after `polls` polls and records a timeout (see include/mg.h)."""
+    _check(library().mg_selftest_timeout(int(polls), _stream(stream)))
 
 
 def mg_workspace_size(prob: Problem, which: int) -> int:

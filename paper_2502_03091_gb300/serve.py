@@ -10,10 +10,11 @@ requests' completion events, keeps each built hierarchy (P, X, Y_mu) resident
 for its follow-up coarse applies, and reports latency (setup complete minus
 arrival) percentiles beside throughput.
 
-Inputs are synthesised on the device per request from a per-request seed
-(torch's generator: links exp(i eps H) with H = sum_a h_a lambda_a / 2,
-h_a ~ N(0, 1), by a Taylor series projected onto SU(3), and complex Gaussian
-starts), as part of handling the request.
+Inputs are synthesised on the device per request from a per-request seed,
+as part of handling the request, by the device form of the seeded input
+generator (mg_inputs.device: the counter-based SplitMix64 / Box-Muller numbers
+of mg_inputs, so a request's links exp(i eps H), H = sum_a h_a lambda_a / 2,
+and complex Gaussian starts are those the host generator gives for that seed).
 """
 from __future__ import annotations
 
@@ -65,64 +66,16 @@ def request_stream(n: int, rate: float, seed: int = 40, m0: float = -0.15,
     return out
 
 
-def _gell_mann_half(torch, device):
-    l = torch.zeros((8, 3, 3), dtype=torch.complex128, device=device)
-    s3 = 1.0 / math.sqrt(3.0)
-    l[0, 0, 1] = l[0, 1, 0] = 1
-    l[1, 0, 1], l[1, 1, 0] = -1j, 1j
-    l[2, 0, 0], l[2, 1, 1] = 1, -1
-    l[3, 0, 2] = l[3, 2, 0] = 1
-    l[4, 0, 2], l[4, 2, 0] = -1j, 1j
-    l[5, 1, 2] = l[5, 2, 1] = 1
-    l[6, 1, 2], l[6, 2, 1] = -1j, 1j
-    l[7, 0, 0] = l[7, 1, 1] = s3
-    l[7, 2, 2] = -2 * s3
-    return l / 2
-
-
-def _mm3(a, b):
-    """Batched 3x3 products with elementwise kernels (no batched GEMM calls)."""
-    return (a[..., :, :, None] * b[..., None, :, :]).sum(-2)
-
-
-def _su3_near(H, eps: float, order: int = 12):
-    """exp(i eps H) by its Taylor series (|eps H| <= ~1.5 here: the truncation
-    error is below 1e-9), then projected onto SU(3) exactly: rows 0 and 1
-    orthonormalised, row 2 = conj(row0 x row1)."""
-    torch = __import__("torch")
-    X = 1j * eps * H
-    term = torch.eye(3, dtype=H.dtype, device=H.device).expand_as(H).clone()
-    U = term.clone()
-    for j in range(1, order + 1):
-        term = _mm3(term, X) / j
-        U = U + term
-    r0 = U[:, 0]
-    r0 = r0 / torch.linalg.vector_norm(r0, dim=-1, keepdim=True)
-    r1 = U[:, 1] - (r0.conj() * U[:, 1]).sum(-1, keepdim=True) * r0
-    r1 = r1 / torch.linalg.vector_norm(r1, dim=-1, keepdim=True)
-    r2 = torch.stack([r0[:, 1] * r1[:, 2] - r0[:, 2] * r1[:, 1],
-                      r0[:, 2] * r1[:, 0] - r0[:, 0] * r1[:, 2],
-                      r0[:, 0] * r1[:, 1] - r0[:, 1] * r1[:, 0]], dim=-1).conj()
-    return torch.stack([r0, r1, r2], dim=1)
-
-
 def synth_inputs(prob: mg.Problem, eps: float, seed: int, device="cuda"):
-    """(U, psi0) complex64 on the device for one request (current stream)."""
+    """(U, psi0) complex64 on the device for one request (current stream):
+    mg_inputs.gauge_field(dims, eps, seed) and mg_inputs.psi0(dims, m', seed),
+    drawn on the device."""
     import torch
-    gen = torch.Generator(device=device).manual_seed(seed)
-    V = prob.volume
-    lam = _gell_mann_half(torch, device)
-    U = torch.empty((V * 4, 3, 3), dtype=torch.complex64, device=device)
-    chunk = 1 << 20
-    for lo in range(0, V * 4, chunk):
-        hi = min(V * 4, lo + chunk)
-        h = torch.randn((hi - lo, 8), dtype=torch.float64, device=device, generator=gen)
-        H = (h.to(torch.complex128)[:, :, None, None] * lam[None]).sum(1)
-        U[lo:hi] = _su3_near(H, eps).to(torch.complex64)
-    shape = mg.shape_psi(prob)
-    psi0 = torch.complex(torch.randn(shape, device=device, generator=gen),
-                         torch.randn(shape, device=device, generator=gen))
-    return U.reshape(V, 4, 3, 3), psi0
+
+    from mg_inputs import device as D
+    U = D.gauge_field_t(prob.dims, eps, seed, device).to(torch.complex64)
+    psi0 = D.psi0_t(prob.dims, prob.n_vec, seed, device, dtype=torch.complex64)
+    return U, psi0
 
 
 def need_bytes(prob: mg.Problem) -> int:

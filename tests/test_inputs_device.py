@@ -1,0 +1,41 @@
+"""The device form of the seeded input generator (mg_inputs.device, used by the
+setup server to draw a request's links and starts on the GPU) against the host
+generator mg_inputs: uniforms bit for bit, normals, links and starts to within
+a few ulps.  Runs on the CPU device here and on cuda:0 with -m gpu."""
+import numpy as np
+import pytest
+
+import mg_inputs as G
+
+torch = pytest.importorskip("torch")
+from mg_inputs import device as D  # noqa: E402
+
+
+def _devices():
+    out = [pytest.param("cpu")]
+    out.append(pytest.param("cuda", marks=pytest.mark.gpu))
+    return out
+
+
+@pytest.mark.parametrize("device", _devices())
+def test_uniforms_bit_identical(device):
+    if device == "cuda" and not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    for seed, stream, start in ((0, 1, 0), (400, 2, 12345), (2 ** 40 + 7, 5, 3 * 10 ** 9)):
+        u = D.uniforms_t(seed, stream, start, 4096, device).cpu().numpy()
+        np.testing.assert_array_equal(u, G.uniforms(seed, stream, start, 4096))
+
+
+@pytest.mark.parametrize("device", _devices())
+def test_normals_links_and_starts_agree(device):
+    if device == "cuda" and not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = D.normals_t(401, G.STREAM_PSI0, 77, 5000, device).cpu().numpy()
+    ref = G.normals(401, G.STREAM_PSI0, 77, 5000)
+    np.testing.assert_allclose(g, ref, rtol=1e-14, atol=1e-14)
+    dims = [4, 4, 2, 6]
+    U = D.gauge_field_t(dims, 0.25, 402, device).cpu().numpy()
+    Uh = G.gauge_field(dims, 0.25, 402)
+    assert np.abs(U - Uh).max() <= 1e-13
+    p = D.psi0_t(dims, 8, 403, device).cpu().numpy()
+    np.testing.assert_allclose(p, G.psi0(dims, 8, 403), rtol=1e-14, atol=1e-14)
