@@ -140,14 +140,15 @@ __device__ __forceinline__ long slab_index(int q, int V, int x, int e, int PAIRS
 // global slab); u at the 9 entries of the link.
 // ---------------------------------------------------------------------------
 // the 9 entries of one link at u (u is 8-byte aligned; u16 says whether u
-// itself is 16-byte aligned): four 16-byte loads and one 8-byte load
-__device__ __forceinline__ void load_link(const float2* __restrict__ u, bool u16, float2 L[9]) {
+// itself is 16-byte aligned): four 16-byte loads and one 8-byte load.  u
+// points into the shared-memory link ring or into global memory.
+__device__ __forceinline__ void load_link(const float2* u, bool u16, float2 L[9]) {
   // the 16-byte aligned run of 8 entries starts at u or at u + 1
   const float4* a4 = reinterpret_cast<const float4*>(u16 ? u : u + 1);
   float4 v[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = __ldg(a4 + i);
-  const float2 last = __ldg(u16 ? u + 8 : u);
+  for (int i = 0; i < 4; ++i) v[i] = a4[i];
+  const float2 last = u16 ? u[8] : u[0];
   if (u16) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -167,7 +168,7 @@ __device__ __forceinline__ void load_link(const float2* __restrict__ u, bool u16
 
 template <int MU, int S, int PAIRS, typename T>
 __device__ __forceinline__ void hop(CP zu[3], CP zl[3], int hf, const T* src,
-                                    const float2* __restrict__ u, float hw) {
+                                    const float2* u, float hw) {
   float2 L[9];
   load_link(u, (reinterpret_cast<uintptr_t>(u) & 15) == 0, L);
   // (B chi_l)_hf uses lower spin 2 + lo
@@ -255,21 +256,28 @@ __device__ __forceinline__ void cmul_acc(CP& acc, float2 c, const CP& v) {
 //
 // One CTA owns a patch of kSPC consecutive sites of a timeslice (spatial
 // lexicographic index p0 .. p0+kSPC-1) for one slab, and marches t = 0..Lt-1.
-// A ring of kRing rows of the input lives in shared memory: hops that stay in
-// the patch (x, and y when a patch spans several x-rows) and both t-hops read
-// the ring; the other hops read global memory (L2).  A ring row is one bulk
-// copy of the patch's contiguous slab row (24.6 KB for P = 4) that completes
-// on the slot's mbarrier: at step t thread 0 issues row t+2 into the slot of row t-2
-// (free since the previous step's barrier) and every thread waits for row
-// t+1, so each row has a whole step to arrive.  Row r (-1 <= r <= Lt) uses
-// slot (r+1) & 3 for the ((r+1)/4)-th time: phase parity ((r+1)/4) & 1.
+// A ring of kRing = 3 rows lives in shared memory.  Row r (time r mod Lt) is
+// two bulk copies completing on the slot's mbarrier: the patch's contiguous
+// slab row of the input (24.6 KB for P = 4 in FP32) and the patch's
+// contiguous row of links U[r][p0 .. p0+kSPC-1][4][3][3] (9.2 KB).  Hops that
+// stay in the patch (x, and y when a patch spans several x-rows) and both
+// t-hops read their neighbour from the ring; every forward link, the
+// backward t link (row t-1) and the backward links of in-patch hops come from
+// the ring; the remaining neighbours and backward links are read from global
+// memory (L2).
+// Step t uses rows t-1, t and t+1.  It starts with the -t hop, the only read
+// of row t-1; after one barrier thread 0 reuses that slot for row t+2, which
+// then has the rest of step t to arrive.  Row r (-1 <= r <= Lt) uses slot
+// (r+1) % 3 for the ((r+1)/3)-th time: phase parity ((r+1)/3) & 1.
 //
 // MODE_NEG_D: out = -D in.  MODE_D_DOT: out = D in, plus per-patch partial
-// sums <out, in> and |out|^2 per right-hand side.
+// sums <out, in> and |out|^2 per right-hand side (per lane in FP32 over 8
+// steps, then reduced over the warp in FP64 into shared memory).
 // Lanes: threadIdx = (site * P + pair) * 2 + hf.
 // ---------------------------------------------------------------------------
 constexpr int kSPC = 32;
-constexpr int kRing = 4;
+constexpr int kRing = 3;
+constexpr int kLinkSite = 36;  // float2 per site in a link row
 
 struct MarchArgs {
   const void* in;     // input s (slab, storage type of the pass)
@@ -291,19 +299,26 @@ constexpr int march_threads() {
   return 2 * kSPC * PAIRS;
 }
 
+template <int PAIRS, typename T>
+constexpr size_t march_smem() {
+  return sizeof(T) * (size_t)kRing * kSPC * 12 * PAIRS +
+         sizeof(float2) * (size_t)kRing * kSPC * kLinkSite;
+}
+
 template <int PAIRS, int MODE, typename T>
 __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchArgs a) {
   constexpr int NC = 2 * kSPC * PAIRS;
   constexpr int SS = 12 * PAIRS;  // ring site stride (elements): a row is a copy of the slab row
   constexpr int NW = NC / 32;
   constexpr uint32_t kSiteBytes = 12 * PAIRS * sizeof(T);
+  constexpr uint32_t kLinkBytes = kLinkSite * sizeof(float2);
   extern __shared__ __align__(128) unsigned char ring_raw[];
   T* ring = reinterpret_cast<T*>(ring_raw);  // [kRing][kSPC][SS]
+  float2* lring = reinterpret_cast<float2*>(ring_raw + sizeof(T) * kRing * kSPC * SS);
   const T* in = static_cast<const T*>(a.in);
   T* out = static_cast<T*>(a.out);
   __shared__ __align__(8) unsigned long long bar[kRing];
-  __shared__ double red[NW][PAIRS][6];
-  __shared__ double pr_s[MODE == MODE_D_DOT ? NC : 1][6];  // per-lane FP64 partial sums
+  __shared__ double red[MODE == MODE_D_DOT ? NW : 1][PAIRS][6];  // FP64 partial sums per warp
   __shared__ int s_abort;
   const int q = blockIdx.x / a.npatch, patch = blockIdx.x % a.npatch;
   const int p0 = patch * kSPC;
@@ -312,6 +327,7 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
   const int hf = threadIdx.x & 1;
   const int sp_idx = threadIdx.x >> 1;
   const int s_loc = sp_idx / PAIRS, p = sp_idx % PAIRS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int xyz = p0 + s_loc;
   const bool valid = xyz < a.Vs;
   int nf[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
@@ -332,17 +348,21 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
     mbar_fence_init();
     s_abort = 0;
   }
+  if (MODE == MODE_D_DOT)
+    for (int i = threadIdx.x; i < NW * PAIRS * 6; i += blockDim.x) (&red[0][0][0])[i] = 0.0;
   __syncthreads();
-  // thread 0: one bulk copy of ring row r (the patch's sites are contiguous in the slab)
+  // thread 0: the two bulk copies of ring row r (the patch's sites are
+  // contiguous in the slab and in the link array)
   auto issue = [&](int r) {
-    const int slot = (r + 1) & 3;
-    const uint32_t bytes = (uint32_t)nvalid * kSiteBytes;
-    mbar_expect_tx(&bar[slot], bytes);
+    const int slot = (r + 1) % kRing;
+    const uint32_t bytes = (uint32_t)nvalid * kSiteBytes, lbytes = (uint32_t)nvalid * kLinkBytes;
+    mbar_expect_tx(&bar[slot], bytes + lbytes);
     const int x = ((r + Lt) % Lt) * a.Vs + p0;
     bulk_g2s(ring + slot * kSPC * SS, in + slab_index(q, a.V, x, 0, PAIRS, 0), bytes, &bar[slot]);
+    bulk_g2s(lring + slot * kSPC * kLinkSite, a.U + (long)x * kLinkSite, lbytes, &bar[slot]);
   };
   auto wait_row = [&](int r) -> bool {
-    return mbar_wait(&bar[(r + 1) & 3], (uint32_t)(((r + 1) >> 2) & 1));
+    return mbar_wait(&bar[(r + 1) % kRing], (uint32_t)(((r + 1) / kRing) & 1));
   };
   auto give_up = [&]() {
     s_abort = 1;
@@ -353,131 +373,129 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), 2) march_kernel(MarchA
     issue(0);
     issue(1);
   }
-  if (!wait_row(-1) || !wait_row(0)) give_up();
+  // rows <= waited have all landed; last_issued is the newest row in flight
+  int last_issued = 1, waited = -2;
+  if (wait_row(-1)) {
+    waited = -1;
+    if (wait_row(0)) waited = 0;
+  }
+  if (waited < 0) give_up();
 
-  // partial sums: FP32 pairs in registers over 8 steps, then added into the
-  // lane's FP64 slots in shared memory (keeps registers for the hops)
   float2 sre = make_float2(0.f, 0.f), sim = sre, snn = sre;
-  if (MODE == MODE_D_DOT)
-#pragma unroll
-    for (int i = 0; i < 6; ++i) pr_s[threadIdx.x][i] = 0.0;
-  int last_issued = 1;
+  // lanes of a site beyond the lattice compute on site p0 and discard it
+  const int xyzc = valid ? xyz : p0;
+  const int sl = xyzc - p0;
   for (int t = 0; t < Lt; ++t) {
+    if (waited == t && wait_row(t + 1)) waited = t + 1;
+    else give_up();
+    const T* ring_t = ring + ((t + 1) % kRing) * kSPC * SS;
+    const T* ring_f = ring + ((t + 2) % kRing) * kSPC * SS;
+    const T* ring_b = ring + (t % kRing) * kSPC * SS;
+    const float2* lk_t = lring + ((t + 1) % kRing) * kSPC * kLinkSite;  // links of time t
+    const float2* lk_b = lring + (t % kRing) * kSPC * kLinkSite;        // links of time t-1
+    CP zu[3], zl[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) zu[c] = zl[c] = CP{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    // the -t hop first: the only read of row t-1, whose slot is refilled next
+    hop<3, -1, PAIRS, T>(zu, zl, hf, ring_b + sl * SS + p, lk_b + sl * kLinkSite + 27, a.hw[3]);
+    __syncthreads();
+    if (s_abort) break;
     if (t + 2 <= Lt) {
       if (threadIdx.x == 0) issue(t + 2);
       last_issued = t + 2;
     }
-    if (!wait_row(t + 1)) give_up();
-    {
-      // lanes of a site beyond the lattice compute on site p0 and discard it
-      const int xyzc = valid ? xyz : p0;
-      const int sl = xyzc - p0;
-      const T* ring_t = ring + ((t + 1) & 3) * kSPC * SS;
-      const T* ring_f = ring + ((t + 2) & 3) * kSPC * SS;
-      const T* ring_b = ring + (t & 3) * kSPC * SS;
-      const int x = t * a.Vs + xyzc;
-      const int tb = (t - 1 + Lt) % Lt;
-      const T* cen = ring_t + sl * SS + p;
-      CP zu[3], zl[3];
+    const int x = t * a.Vs + xyzc;
+    const T* cen = ring_t + sl * SS + p;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const CP u = cp_ld(cen + (hf * 3 + c) * PAIRS), l = cp_ld(cen + ((2 + hf) * 3 + c) * PAIRS);
-        zu[c] = CP{pmul(dup(a.diag), u.re), pmul(dup(a.diag), u.im)};
-        zl[c] = CP{pmul(dup(a.diag), l.re), pmul(dup(a.diag), l.im)};
-      }
-      if (a.C) {
-        // row (spin hf, colour c) of each chirality's 6x6 block
-        const float2* cl = a.C + (long)x * 72;
+    for (int c = 0; c < 3; ++c) {
+      const CP u = cp_ld(cen + (hf * 3 + c) * PAIRS), l = cp_ld(cen + ((2 + hf) * 3 + c) * PAIRS);
+      zu[c].re = pfma(dup(a.diag), u.re, zu[c].re);
+      zu[c].im = pfma(dup(a.diag), u.im, zu[c].im);
+      zl[c].re = pfma(dup(a.diag), l.re, zl[c].re);
+      zl[c].im = pfma(dup(a.diag), l.im, zl[c].im);
+    }
+    if (a.C) {
+      // row (spin hf, colour c) of each chirality's 6x6 block
+      const float2* cl = a.C + (long)x * 72;
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int j = 0; j < 6; ++j) {
-            cmul_acc(zu[c], __ldg(cl + (hf * 3 + c) * 6 + j), cp_ld(cen + j * PAIRS));
-            cmul_acc(zl[c], __ldg(cl + 36 + (hf * 3 + c) * 6 + j), cp_ld(cen + (6 + j) * PAIRS));
-          }
-      }
-      const float2* Ux = a.U + (long)x * 36;
-      const long tV = (long)t * a.Vs;
-#pragma unroll
-      for (int mu = 0; mu < 3; ++mu) {
-        // neighbours: ring if inside the patch, else global (same component stride)
-        const int f = valid ? nf[mu] : p0, b = valid ? nb[mu] : p0;
-        const int lf = f - p0, lb = b - p0;
-        const bool rf = lf >= 0 && lf < kSPC && f < a.Vs, rb = lb >= 0 && lb < kSPC && b < a.Vs;
-        const T* pf = rf ? ring_t + lf * SS + p : in + slab_index(q, a.V, tV + f, 0, PAIRS, p);
-        const T* pb = rb ? ring_t + lb * SS + p : in + slab_index(q, a.V, tV + b, 0, PAIRS, p);
-        const float2* ub = a.U + (tV + b) * 36 + mu * 9;
-        if (mu == 0) {
-          hop<0, +1, PAIRS, T>(zu, zl, hf, pf, Ux, a.hw[0]);
-          hop<0, -1, PAIRS, T>(zu, zl, hf, pb, ub, a.hw[0]);
-        } else if (mu == 1) {
-          hop<1, +1, PAIRS, T>(zu, zl, hf, pf, Ux + 9, a.hw[1]);
-          hop<1, -1, PAIRS, T>(zu, zl, hf, pb, ub, a.hw[1]);
-        } else {
-          hop<2, +1, PAIRS, T>(zu, zl, hf, pf, Ux + 18, a.hw[2]);
-          hop<2, -1, PAIRS, T>(zu, zl, hf, pb, ub, a.hw[2]);
+        for (int j = 0; j < 6; ++j) {
+          cmul_acc(zu[c], __ldg(cl + (hf * 3 + c) * 6 + j), cp_ld(cen + j * PAIRS));
+          cmul_acc(zl[c], __ldg(cl + 36 + (hf * 3 + c) * 6 + j), cp_ld(cen + (6 + j) * PAIRS));
         }
-      }
-      hop<3, +1, PAIRS, T>(zu, zl, hf, ring_f + sl * SS + p, Ux + 27, a.hw[3]);
-      hop<3, -1, PAIRS, T>(zu, zl, hf, ring_b + sl * SS + p,
-                        a.U + ((long)tb * a.Vs + xyzc) * 36 + 27, a.hw[3]);
-      if (valid) {
-        const long so = slab_index(q, a.V, x, 0, PAIRS, p);
-        if (MODE == MODE_NEG_D) {
+    }
+    const float2* Ux = lk_t + sl * kLinkSite;
+    const long tV = (long)t * a.Vs;
 #pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
-            const CP w = k < 3 ? zu[k] : zl[k - 3];
-            __stcs(out + so + e * PAIRS, cp_pack<T>(cp_neg(w)));
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
-            const CP w = k < 3 ? zu[k] : zl[k - 3];
-            const CP r = cp_ld(cen + e * PAIRS);
-            // <w, r> = sum conj(w) r
-            sre = pfma(w.re, r.re, sre);
-            sre = pfma(w.im, r.im, sre);
-            sim = pfma(w.re, r.im, sim);
-            sim = pfma(pmul(dup(-1.f), w.im), r.re, sim);
-            snn = pfma(w.re, w.re, snn);
-            snn = pfma(w.im, w.im, snn);
-            __stcs(out + so + e * PAIRS, cp_pack<T>(w));
-          }
-        }
-      }
-      if (MODE == MODE_D_DOT && ((t & 7) == 7 || t == Lt - 1)) {
-        double* ps_ = pr_s[threadIdx.x];
-        ps_[0] += (double)sre.x; ps_[1] += (double)sim.x; ps_[2] += (double)snn.x;
-        ps_[3] += (double)sre.y; ps_[4] += (double)sim.y; ps_[5] += (double)snn.y;
-        sre = sim = snn = make_float2(0.f, 0.f);
+    for (int mu = 0; mu < 3; ++mu) {
+      // neighbours: ring if inside the patch, else global (same component stride)
+      const int f = valid ? nf[mu] : p0, b = valid ? nb[mu] : p0;
+      const int lf = f - p0, lb = b - p0;
+      const bool rf = lf >= 0 && lf < kSPC && f < a.Vs, rb = lb >= 0 && lb < kSPC && b < a.Vs;
+      const T* pf = rf ? ring_t + lf * SS + p : in + slab_index(q, a.V, tV + f, 0, PAIRS, p);
+      const T* pb = rb ? ring_t + lb * SS + p : in + slab_index(q, a.V, tV + b, 0, PAIRS, p);
+      const float2* ub = rb ? lk_t + lb * kLinkSite + mu * 9 : a.U + (tV + b) * 36 + mu * 9;
+      if (mu == 0) {
+        hop<0, +1, PAIRS, T>(zu, zl, hf, pf, Ux, a.hw[0]);
+        hop<0, -1, PAIRS, T>(zu, zl, hf, pb, ub, a.hw[0]);
+      } else if (mu == 1) {
+        hop<1, +1, PAIRS, T>(zu, zl, hf, pf, Ux + 9, a.hw[1]);
+        hop<1, -1, PAIRS, T>(zu, zl, hf, pb, ub, a.hw[1]);
+      } else {
+        hop<2, +1, PAIRS, T>(zu, zl, hf, pf, Ux + 18, a.hw[2]);
+        hop<2, -1, PAIRS, T>(zu, zl, hf, pb, ub, a.hw[2]);
       }
     }
-    // the slot of row t-1 is refilled at the next step
-    __syncthreads();
-    if (s_abort) break;
+    hop<3, +1, PAIRS, T>(zu, zl, hf, ring_f + sl * SS + p, Ux + 27, a.hw[3]);
+    if (valid) {
+      const long so = slab_index(q, a.V, x, 0, PAIRS, p);
+      if (MODE == MODE_NEG_D) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
+          const CP w = k < 3 ? zu[k] : zl[k - 3];
+          __stcs(out + so + e * PAIRS, cp_pack<T>(cp_neg(w)));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const int e = k < 3 ? hf * 3 + k : (2 + hf) * 3 + k - 3;
+          const CP w = k < 3 ? zu[k] : zl[k - 3];
+          const CP r = cp_ld(cen + e * PAIRS);
+          // <w, r> = sum conj(w) r
+          sre = pfma(w.re, r.re, sre);
+          sre = pfma(w.im, r.im, sre);
+          sim = pfma(w.re, r.im, sim);
+          sim = pfma(pmul(dup(-1.f), w.im), r.re, sim);
+          snn = pfma(w.re, w.re, snn);
+          snn = pfma(w.im, w.im, snn);
+          __stcs(out + so + e * PAIRS, cp_pack<T>(w));
+        }
+      }
+    }
+    if (MODE == MODE_D_DOT && ((t & 7) == 7 || t == Lt - 1)) {
+      // lane = 2 * (s * PAIRS + p) + hf: FP64 sum over hf and the warp's sites, per pair
+      double pr[6] = {(double)sre.x, (double)sim.x, (double)snn.x,
+                      (double)sre.y, (double)sim.y, (double)snn.y};
+#pragma unroll
+      for (int i = 0; i < 6; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], 1);
+#pragma unroll
+      for (int off = 16; off >= 2 * PAIRS; off >>= 1)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], off);
+      if (lane < 2 * PAIRS && (lane & 1) == 0)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) red[warp][lane >> 1][i] += pr[i];
+      sre = sim = snn = make_float2(0.f, 0.f);
+    }
   }
   if (s_abort) {
     // let the copies still in flight land before the CTA's shared memory is released
-    if (last_issued >= 1) (void)wait_row(last_issued);
+    for (int r = waited + 1; r <= last_issued; ++r) (void)wait_row(r);
     return;
   }
   if (MODE != MODE_NEG_D) {
-    double pr[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) pr[i] = pr_s[threadIdx.x][i];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // lane = 2 * (s * PAIRS + p) + hf: sum over hf and s, keep p
-#pragma unroll
-    for (int i = 0; i < 6; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], 1);
-#pragma unroll
-    for (int off = 16; off >= 2 * PAIRS; off >>= 1)
-#pragma unroll
-      for (int i = 0; i < 6; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], off);
-    if (lane < 2 * PAIRS && (lane & 1) == 0)
-#pragma unroll
-      for (int i = 0; i < 6; ++i) red[warp][lane >> 1][i] = pr[i];
     __syncthreads();
     if (threadIdx.x < PAIRS) {
       double tt[6];
@@ -817,7 +835,7 @@ __global__ void clover_kernel(int L0, int L1, int L2, int L3, float csw,
 template <int PAIRS, int MODE, typename T>
 cudaError_t run_march(const MarchArgs& a, int nsl, cudaStream_t s) {
   static const char* names[2] = {"mr_neg_dslash", "mr_dslash_dot"};
-  const size_t smem = sizeof(T) * (size_t)kRing * kSPC * 12 * PAIRS;
+  const size_t smem = march_smem<PAIRS, T>();
   static PerDeviceOnce attr_once;
   attr_once.run([&] {
     cudaFuncSetAttribute(march_kernel<PAIRS, MODE, T>,

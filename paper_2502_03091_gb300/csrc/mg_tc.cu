@@ -527,31 +527,40 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   float inv = 1.f;
   float cm = 0.f;  // this thread's largest |C| entry of the current bc
 
-  // epilogue of chunk cc of bc from TMEM slot d: warp w reads TMEM lanes
-  // 32 (w & 3) .. + 31 (rows of the chunk) and the column blocks cb = w >> 2,
-  // w >> 2 + 2, ...
+  // epilogue of chunk cc of bc from TMEM slot d.  Its A tiles (buffer d) are
+  // free once the chunk's MMAs are done, so they stage the output: warp w
+  // reads TMEM lanes 32 (w & 3) .. + 31 (rows of the chunk) and the column
+  // blocks cb = w >> 2, w >> 2 + 2, ..., writes them to shared memory (row
+  // stride n + 1, or for n = 64 a 64-wide row with the columns XOR-swizzled
+  // by the row), then every warp writes whole rows to global memory.
   auto epilogue = [&](int bc, int cc, int d) {
     sync_after();
+    float2* stg = reinterpret_cast<float2*>(atiles + 2 * d * kTcTile);
+    const int ld = n < 64 ? n + 1 : 64;
     const int rl = (warp & 3) * 32 + lane, r = cc * kTcRows + rl;
-    float2* out = C + ((long)bc * g.K + r) * n;
 #pragma unroll 1
     for (int cb = warp >> 2; cb < npad / 16; cb += 2) {
       float v[16], w[16];
       const uint32_t a = taddr + ((uint32_t)((warp & 3) * 32) << 16) + d * 2 * npad + cb * 16;
       tmem_ld16(a, v);
       tmem_ld16(a + npad, w);
-      if (r < g.K) {
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int jj = cb * 8 + t;
-          if (jj < n) {
-            const float2 z = make_float2((v[2 * t] + w[2 * t]) * inv,
-                                         (v[2 * t + 1] + w[2 * t + 1]) * inv);
-            out[jj] = z;
-            cm = fmaxf(cm, fmaxf(fabsf(z.x), fabsf(z.y)));
-          }
+      for (int t = 0; t < 8; ++t) {
+        const int jj = cb * 8 + t;
+        if (jj < n) {
+          const float2 z = make_float2((v[2 * t] + w[2 * t]) * inv,
+                                       (v[2 * t + 1] + w[2 * t + 1]) * inv);
+          stg[rl * ld + (n < 64 ? jj : (jj ^ (rl & 31)))] = z;
+          if (r < g.K) cm = fmaxf(cm, fmaxf(fabsf(z.x), fabsf(z.y)));
         }
       }
+    }
+    __syncthreads();
+    const int rows = min(kTcRows, g.K - cc * kTcRows);
+    for (int row = warp; row < rows; row += kTcThreads / 32) {
+      float2* out = C + ((long)bc * g.K + cc * kTcRows + row) * n;
+      for (int jj = lane; jj < n; jj += 32)
+        out[jj] = stg[row * ld + (n < 64 ? jj : (jj ^ (row & 31)))];
     }
   };
 
