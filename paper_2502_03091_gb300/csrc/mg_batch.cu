@@ -3,7 +3,8 @@
 //
 // mg_batch_create validates the level descriptors, tunes the smoother's slab
 // width (2 or 4 pairs of right-hand sides per CTA) once per distinct problem
-// shape by timing both variants, then captures every level's four setup calls
+// shape by timing both variants, runs every level once (so every kernel is
+// loaded and configured before the capture), then captures every level's four setup calls
 // into one CUDA graph that forks over S streams from the caller's stream and
 // joins back: small levels run side by side and fill the GPU, and one
 // cudaGraphLaunch replaces a few thousand kernel launches.  With
@@ -205,6 +206,15 @@ mg_status mg_batch_create(const mg_level_desc* levels, int n, int n_streams, voi
       }
     }
     set_tuned_pairs(g, best_p);
+  }
+  // one short run of every level before the capture: each kernel the graph
+  // will hold is loaded and configured (function attributes) outside it
+  for (int i = 0; i < n; ++i) {
+    mg_level_desc d = lv[i];
+    d.prob.mr_iters = 1;
+    SuspendTiming no_timing;
+    const mg_status st = run_level(d, s);
+    if (st != MG_OK) return st;
   }
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return batch_fail(MG_ERR_CUDA, "tuning", e);

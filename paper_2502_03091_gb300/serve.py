@@ -48,6 +48,7 @@ class Request:
     gpu_ms: float = math.nan
     deferred: bool = False
     failed: bool = False      # rejected: a bounded device wait timed out (see Server.run)
+    too_large: bool = False   # rejected: needs more device memory than the budget
 
 
 def request_stream(n: int, rate: float, seed: int = 40, m0: float = -0.15,
@@ -157,8 +158,13 @@ class Server:
                 evict_until(need)
                 if self.used + need > self.budget:
                     if not active and not applying:
-                        raise RuntimeError(f"request {r.rid} needs {need} bytes, more than the "
-                                           f"budget of {self.budget}")
+                        # too large even for an idle device: rejected, not queued forever
+                        waiting.popleft()
+                        r.failed = r.too_large = True
+                        r.t_admit = r.t_done = now()
+                        done.append(r)
+                        progressed = True
+                        continue
                     break
                 waiting.popleft()
                 r.t_admit = now()
@@ -241,10 +247,11 @@ class Server:
 
     def _stats(self, done: List[Request], realtime: bool) -> dict:
         import numpy as np
-        failed = sum(r.failed for r in done)
+        failed = sum(r.failed and not r.too_large for r in done)
+        too_large = sum(r.too_large for r in done)
         done = [r for r in done if not r.failed]
         if not done:
-            return {"requests": 0, "failed": failed}
+            return {"requests": 0, "failed": failed, "rejected_too_large": too_large}
         lat = np.array([r.t_done - (r.arrival if realtime else 0.0) for r in done])
         span = max(r.t_done for r in done) - (min(r.arrival for r in done) if realtime else 0.0)
         gpu = np.array([r.gpu_ms for r in done])
@@ -255,4 +262,5 @@ class Server:
                 "gpu_ms_p50": float(np.percentile(gpu, 50)),
                 "hbm_high_water_gb": self.high_water / 1e9,
                 "max_slots": self.max_slots, "failed": failed,
+                "rejected_too_large": too_large, "budget_gb": self.budget / 1e9,
                 "late_timeout": self.late_timeout}

@@ -3,7 +3,8 @@
 4^4, eps in [0.15, 0.35], drawn from batch seed 30) built by one graph launch
 must give every level bit for bit what the level gives when it is built
 alone with the single calls (the kernels are deterministic and the levels
-share nothing), and the smallest levels must match the FP64 oracle."""
+share nothing), and the smallest levels must match the FP64 oracle; in the
+FP32 path and in the mixed path (tensor-core contractions)."""
 import json
 import os
 
@@ -50,8 +51,9 @@ def _snapshot(lv):
     return [t.clone() for t in (lv.psi, lv.sigma, lv.flags, lv.P, lv.X, lv.Y)]
 
 
-def test_batch_equals_solo_and_oracle():
-    levels = _levels()
+@pytest.mark.parametrize("precision", [mg.MG_PREC_FP32, mg.MG_PREC_MIXED])
+def test_batch_equals_solo_and_oracle(precision):
+    levels = _levels(precision)
     batch = mg.Batch([lv for _, _, _, lv in levels], n_streams=0)
     assert batch.n_streams in (1, 2, 4, 8)
     for _, _, _, lv in levels:   # poison the outputs the batch must write

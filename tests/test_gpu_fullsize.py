@@ -16,7 +16,9 @@ parameters), on outputs the FP64 oracle can compute one at a time:
 
 Workloads: 16^3x32 Wilson-clover (c_sw = 1, eps = 0.25, m' = 48, k = 24,
 4^4 aggregates: 512 blocks) and 32^3x64 anisotropic Wilson (xi = 3.5,
-eps = 0.2, m' = 64, k = 24, 4^3x8 aggregates: 4096 blocks).
+eps = 0.2, m' = 64, k = 24, 4^3x8 aggregates: 4096 blocks), each in the FP32
+plain path and in the mixed path (tensor-core contractions), which is held to
+the same tolerances.
 """
 import concurrent.futures as cf
 
@@ -85,31 +87,40 @@ def _block_sites(dims, block, j):
     return xs[0] + dims[0] * (xs[1] + dims[1] * (xs[2] + dims[2] * xs[3]))
 
 
+_inputs = {}
 _runs = {}
+PRECISIONS = {"fp32": mg.MG_PREC_FP32, "mixed": mg.MG_PREC_MIXED}
 
 
-def _run(name):
-    if name in _runs:
-        return _runs[name]
+def _run(name, precision="fp32"):
+    key = (name, precision)
+    if key in _runs:
+        return _runs[key]
     dims, block, eps, csw, xi, m0, m, k, N, gs, ps, cols, blocks = WORKLOADS[name]
-    U = G.round_to_c64(G.gauge_field(dims, eps, gs, threads=_POOL))
-    C = G.round_to_c64(O.clover(dims, U, csw)) if csw else None
-    prob = mg.Problem(dims=dims, block=block, m0=m0, n_vec=m, k=k, mr_iters=N, csw=csw, xi=xi)
-    Ud = torch.from_numpy(U.astype(np.complex64)).cuda()
-    Cd = torch.from_numpy(C.astype(np.complex64).reshape(-1, 2, 6, 6)).cuda() if csw else None
-    p0 = _psi0_device(dims, m, ps)
+    if name not in _inputs:
+        U = G.round_to_c64(G.gauge_field(dims, eps, gs, threads=_POOL))
+        C = G.round_to_c64(O.clover(dims, U, csw)) if csw else None
+        Ud = torch.from_numpy(U.astype(np.complex64)).cuda()
+        Cd = torch.from_numpy(C.astype(np.complex64).reshape(-1, 2, 6, 6)).cuda() if csw else None
+        _inputs[name] = (U, C, Ud, Cd, _psi0_device(dims, m, ps))
+    U, C, Ud, Cd, p0 = _inputs[name]
+    prob = mg.Problem(dims=dims, block=block, m0=m0, n_vec=m, k=k, mr_iters=N, csw=csw, xi=xi,
+                      precision=PRECISIONS[precision])
     lv = mg.Level.allocate(prob, Ud, Cd, p0)
     lv.run()
     torch.cuda.synchronize()
     mg.mg_sync_status()
-    _runs[name] = dict(prob=prob, U=U, C=C, lv=lv, dims=dims, block=block, m0=m0, xi=xi,
-                       m=m, k=k, N=N, ps=ps, cols=cols, blocks=blocks, csw=csw)
-    return _runs[name]
+    lv.ws_smooth = lv.ws_trunc = None  # the tests read only the level's outputs
+    torch.cuda.empty_cache()
+    _runs[key] = dict(prob=prob, U=U, C=C, lv=lv, dims=dims, block=block, m0=m0, xi=xi,
+                      m=m, k=k, N=N, ps=ps, cols=cols, blocks=blocks, csw=csw)
+    return _runs[key]
 
 
+@pytest.mark.parametrize("precision", list(PRECISIONS))
 @pytest.mark.parametrize("name", list(WORKLOADS))
-def test_fullsize_smoother_sampled_vectors(name):
-    r = _run(name)
+def test_fullsize_smoother_sampled_vectors(name, precision):
+    r = _run(name, precision)
     cols = r["cols"]
     p0 = G.round_to_c64(G.psi0_columns(r["dims"], r["m"], r["ps"], cols))
     want = O.mr(r["dims"], r["m0"], r["xi"], r["U"], r["C"], p0, r["N"])
@@ -119,9 +130,10 @@ def test_fullsize_smoother_sampled_vectors(name):
         assert err <= 2e-5, (cols[i], err)
 
 
+@pytest.mark.parametrize("precision", list(PRECISIONS))
 @pytest.mark.parametrize("name", list(WORKLOADS))
-def test_fullsize_truncation_sampled_blocks(name):
-    r = _run(name)
+def test_fullsize_truncation_sampled_blocks(name, precision):
+    r = _run(name, precision)
     lv, k = r["lv"], r["k"]
     flags = lv.flags.cpu().numpy()
     assert np.all(flags == 0)
@@ -139,9 +151,10 @@ def test_fullsize_truncation_sampled_blocks(name):
             assert e <= max(1e-5, float(dk_bound(so, k))), (j, al, e)
 
 
+@pytest.mark.parametrize("precision", list(PRECISIONS))
 @pytest.mark.parametrize("name", list(WORKLOADS))
-def test_fullsize_galerkin_identity(name):
-    r = _run(name)
+def test_fullsize_galerkin_identity(name, precision):
+    r = _run(name, precision)
     lv, prob, k = r["lv"], r["prob"], r["k"]
     dims, block = r["dims"], r["block"]
     nc = prob.n_blocks
