@@ -108,7 +108,7 @@ typedef struct {
   int32_t k;          /* kept per chirality, 1 <= k <= m' */
   int32_t mr_iters;   /* smoother iterations N >= 1 */
   int32_t precision;  /* mg_precision */
-  uint64_t seed;      /* reserved (inputs are always passed in) */
+  uint64_t seed;      /* read only by mg_random_starts */
 } mg_problem;
 
 /* Which call a workspace size is asked for. */
@@ -338,6 +338,17 @@ mg_status mg_solve(const mg_hierarchy* h, const void* b, void* x, int32_t nrhs, 
 mg_status mg_chiral_truncate_static(const mg_problem* prob, const void* psi, void* Uk,
                                     double* sigma, void* coarse_tv, int32_t* blk_flags,
                                     void* stream);
+
+/* Random starting vectors for the smoother (the "m random initial guesses" of
+ * Sec. 2, Eq. 1), for callers that do not bring their own (a setup server,
+ * say): psi0 [V][4][3][n_vec] complex64 on the device, element e (flat index)
+ * = normal 2e + i normal 2e+1 of the counter-based generator of prob->seed
+ * (SplitMix64 of counter + key(seed, stream 2), 53-bit uniforms, Box-Muller's
+ * cosine branch), the definition the library's tests draw their inputs from;
+ * uniforms bit-identical, the transcendental functions in FP32 (within a
+ * few 1e-6 of the FP64 definition).  Only dims and n_vec of prob are used besides the seed.  Out:
+ * psi0 (caller-owned device memory).  Asynchronous on `stream`. */
+mg_status mg_random_starts(const mg_problem* prob, void* psi0, void* stream);
 
 /* Failure-detection self-test (no counterpart in the paper).  Enqueues on
  * `stream` one kernel whose single thread waits on a shared-memory mbarrier

@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmg.so")
 SOURCES = ["mg_abi.cu", "mg_dslash.cu", "mg_truncate.cu", "mg_coarsen.cu", "mg_static.cu",
-           "mg_batch.cu", "mg_tc.cu", "mg_level2.cu", "mg_solve.cu"]
+           "mg_batch.cu", "mg_tc.cu", "mg_level2.cu", "mg_solve.cu",
+           "mg_starts.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -294,6 +294,16 @@ mg_status mg_sync_status(void* stream) {
   return MG_OK;
 }
 
+mg_status mg_random_starts(const mg_problem* prob, void* psi0, void* stream) {
+  Geom g;
+  mg_status st = make_geom(prob, &g);
+  if (st != MG_OK) return st;
+  if (!psi0) return fail(MG_ERR_INVALID, "mg_random_starts: NULL array");
+  return cuda_status(launch_random_starts(g, prob->seed, static_cast<float2*>(psi0),
+                                          static_cast<cudaStream_t>(stream)),
+                     "mg_random_starts");
+}
+
 mg_status mg_selftest_timeout(int32_t polls, void* stream) {
   if (polls < 1 || polls > (1 << 20))
     return fail(MG_ERR_INVALID, "mg_selftest_timeout: polls %d out of [1, 1048576]", polls);

@@ -264,12 +264,23 @@ __device__ void stage_gram(const TcRows& g, const long* table, int bc, int c, fl
     uint4 h0, l0, h1, l1;
     split8<PREC>(v0, s, h0, l0);
     split8<PREC>(v1, s, h1, l1);
+    // the bank group of a 16-byte store is q & 7: lanes 4..7 of each 8-lane
+    // phase store their second column first, so a phase covers all 8 groups
     const uint32_t o0 = (q0 >> 3) * kTcSbo + rg * 128 + (q0 & 7) * 16;
-    *reinterpret_cast<uint4*>(hi + o0) = h0;
-    *reinterpret_cast<uint4*>(hi + o0 + 16) = h1;
-    if (PREC == TC_FP16X3) {
-      *reinterpret_cast<uint4*>(lo + o0) = l0;
-      *reinterpret_cast<uint4*>(lo + o0 + 16) = l1;
+    if ((threadIdx.x >> 2) & 1) {
+      *reinterpret_cast<uint4*>(hi + o0 + 16) = h1;
+      *reinterpret_cast<uint4*>(hi + o0) = h0;
+      if (PREC == TC_FP16X3) {
+        *reinterpret_cast<uint4*>(lo + o0 + 16) = l1;
+        *reinterpret_cast<uint4*>(lo + o0) = l0;
+      }
+    } else {
+      *reinterpret_cast<uint4*>(hi + o0) = h0;
+      *reinterpret_cast<uint4*>(hi + o0 + 16) = h1;
+      if (PREC == TC_FP16X3) {
+        *reinterpret_cast<uint4*>(lo + o0) = l0;
+        *reinterpret_cast<uint4*>(lo + o0 + 16) = l1;
+      }
     }
   }
   }
@@ -759,25 +770,26 @@ __device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const 
     for (int e = 0; e < 6; ++e) Lv[e] = Rv[e] = make_float2(0.f, 0.f);
     const int al = col / k, i = col % k;
     if (x >= 0) {
-      const float2* Px = a.P + (long)x * 12 * k;  // [2][6][k]
+      const int rowc = 12 * k;  // complex per site of P: [2][6][k]
+      const float2* Px = a.P + (long)x * rowc;
       if (mu < 0) {
         if (al == pass) {
 #pragma unroll
-          for (int e = 0; e < 6; ++e) Lv[e] = __ldg(Px + (al * 6 + e) * k + i);
+          for (int e = 0; e < 6; ++e) Lv[e] = Px[(al * 6 + e) * k + i];
 #pragma unroll
           for (int e = 0; e < 6; ++e) {
             float2 r = cscale(Lv[e], 0.5f * a.diag);
             if (a.C) {
               const float2* cl = a.C + (long)x * 72 + al * 36 + e * 6;
 #pragma unroll
-              for (int f = 0; f < 6; ++f) cfma(r, cscale(__ldg(cl + f), 0.5f), Lv[f]);
+              for (int f = 0; f < 6; ++f) cfma(r, cscale(cl[f], 0.5f), Lv[f]);
             }
             Rv[e] = r;
           }
         }
       } else {
-        const float2* Py = a.P + (long)s_nbr[s] * 12 * k;
-        const float2* u = a.U + ((long)x * 4 + mu) * 9;
+        const float2* Py = a.P + (long)s_nbr[s] * rowc;
+        const float2* u = a.U + (long)x * 36 + mu * 9;
 #pragma unroll
         for (int sp = 0; sp < 2; ++sp) {
           int tt;
@@ -787,7 +799,7 @@ __device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const 
           float2 py[3];
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            const float2 vx = __ldg(Px + o + d * k), vy = __ldg(Py + o + d * k);
+            const float2 vx = Px[o + d * k], vy = Py[o + d * k];
             Lv[sp * 3 + d] = al == 0 ? vx : cmul(ph, vx);
             py[d] = al == 0 ? vy : cmul(ph, vy);
           }
@@ -795,7 +807,7 @@ __device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const 
           for (int c = 0; c < 3; ++c) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) cfma(acc, __ldg(u + c * 3 + d), py[d]);
+            for (int d = 0; d < 3; ++d) cfma(acc, u[c * 3 + d], py[d]);
             Rv[sp * 3 + c] = cscale(acc, a.hw[mu]);
           }
         }
@@ -809,21 +821,25 @@ __device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const 
       rre[e] = e < 6 ? Rv[e < 6 ? e : 0].x : 0.f;
       rim[e] = e < 6 ? Rv[e < 6 ? e : 0].y : 0.f;
     }
-    uint4 h, l;
+    uint4 lhr, llr, lhm, llm, rhr, rlr, rhm, rlm;
     const int q = 2 * col;
     const uint32_t o0 = (q >> 3) * kCsSbo + s * 128 + (q & 7) * 16;
-    split8<TC_FP16X3>(lre, kCsScaleL, h, l);
-    *reinterpret_cast<uint4*>(lhi + o0) = h;
-    *reinterpret_cast<uint4*>(llo + o0) = l;
-    split8<TC_FP16X3>(lim, kCsScaleL, h, l);
-    *reinterpret_cast<uint4*>(lhi + o0 + 16) = h;
-    *reinterpret_cast<uint4*>(llo + o0 + 16) = l;
-    split8<TC_FP16X3>(rre, kCsScaleR, h, l);
-    *reinterpret_cast<uint4*>(rhi + o0) = h;
-    *reinterpret_cast<uint4*>(rlo + o0) = l;
-    split8<TC_FP16X3>(rim, kCsScaleR, h, l);
-    *reinterpret_cast<uint4*>(rhi + o0 + 16) = h;
-    *reinterpret_cast<uint4*>(rlo + o0 + 16) = l;
+    split8<TC_FP16X3>(lre, kCsScaleL, lhr, llr);
+    split8<TC_FP16X3>(lim, kCsScaleL, lhm, llm);
+    split8<TC_FP16X3>(rre, kCsScaleR, rhr, rlr);
+    split8<TC_FP16X3>(rim, kCsScaleR, rhm, rlm);
+    // the bank group of a 16-byte store is q & 7: lanes 4..7 of each 8-lane
+    // phase store their imaginary column first, so a phase covers all 8 groups
+    const uint32_t a0 = ((threadIdx.x >> 2) & 1) ? o0 + 16 : o0, a1 = o0 + 16 - (a0 - o0);
+    const bool sw = (threadIdx.x >> 2) & 1;
+    *reinterpret_cast<uint4*>(lhi + a0) = sw ? lhm : lhr;
+    *reinterpret_cast<uint4*>(llo + a0) = sw ? llm : llr;
+    *reinterpret_cast<uint4*>(rhi + a0) = sw ? rhm : rhr;
+    *reinterpret_cast<uint4*>(rlo + a0) = sw ? rlm : rlr;
+    *reinterpret_cast<uint4*>(lhi + a1) = sw ? lhr : lhm;
+    *reinterpret_cast<uint4*>(llo + a1) = sw ? llr : llm;
+    *reinterpret_cast<uint4*>(rhi + a1) = sw ? rhr : rhm;
+    *reinterpret_cast<uint4*>(rlo + a1) = sw ? rlr : rlm;
   }
 }
 
@@ -881,11 +897,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_coarsen_kernel(TcCoarsen a,
   };
   // the complex 2k x 2k matrix of the real accumulator R (this thread's row
   // and column half) into Ms
-  auto to_ms = [&](const float* R) {
+  auto to_ms = [&](bool from_y) {
     const int rho = (warp & 3) * 32 + lane, c1 = rho >> 1;
 #pragma unroll
     for (int t = 0; t < NH / 2; ++t) {
-      const float re_re = R[2 * t], re_im = R[2 * t + 1];
+      const float re_re = from_y ? Yr[2 * t] : Sr[2 * t];
+      const float re_im = from_y ? Yr[2 * t + 1] : Sr[2 * t + 1];
       const float im_re = __shfl_down_sync(0xffffffffu, re_re, 1);
       const float im_im = __shfl_down_sync(0xffffffffu, re_im, 1);
       const int c2 = (half * NH) / 2 + t;
@@ -960,7 +977,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_coarsen_kernel(TcCoarsen a,
           add_chunk(pend, pend_y);
           pend = -1;
         }
-        to_ms(Yr);
+        to_ms(true);
         __syncthreads();
         int jc[4];
         {
@@ -990,7 +1007,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_coarsen_kernel(TcCoarsen a,
       add_chunk(pend, pend_y);
     }
     // X = S + sigma_3 S^dag sigma_3
-    to_ms(Sr);
+    to_ms(false);
     __syncthreads();
     for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
       const int r = idx / n2, c = idx % n2;

@@ -11,10 +11,11 @@ for its follow-up coarse applies, and reports latency (setup complete minus
 arrival) percentiles beside throughput.
 
 Inputs are synthesised on the device per request from a per-request seed,
-as part of handling the request, by the device form of the seeded input
-generator (mg_inputs.device: the counter-based SplitMix64 / Box-Muller numbers
-of mg_inputs, so a request's links exp(i eps H), H = sum_a h_a lambda_a / 2,
-and complex Gaussian starts are those the host generator gives for that seed).
+as part of handling the request, with the counter-based SplitMix64 /
+Box-Muller numbers of mg_inputs: the links exp(i eps H), H = sum_a h_a
+lambda_a / 2, by the torch form of that generator (mg_inputs.device), the
+complex Gaussian starts by the library's mg_random_starts, so a request's
+inputs are those the host generator gives for that seed.
 """
 from __future__ import annotations
 
@@ -69,13 +70,18 @@ def request_stream(n: int, rate: float, seed: int = 40, m0: float = -0.15,
 
 def synth_inputs(prob: mg.Problem, eps: float, seed: int, device="cuda"):
     """(U, psi0) complex64 on the device for one request (current stream):
-    mg_inputs.gauge_field(dims, eps, seed) and mg_inputs.psi0(dims, m', seed),
-    drawn on the device."""
+    mg_inputs.gauge_field(dims, eps, seed), drawn on the device in torch, and
+    mg_inputs.psi0(dims, m', seed), drawn by the library (mg_random_starts,
+    the same counter-based numbers to FP32 rounding)."""
+    import dataclasses
+
     import torch
 
     from mg_inputs import device as D
     U = D.gauge_field_t(prob.dims, eps, seed, device).to(torch.complex64)
-    psi0 = D.psi0_t(prob.dims, prob.n_vec, seed, device, dtype=torch.complex64)
+    psi0 = torch.empty(mg.shape_psi(prob), dtype=torch.complex64, device=device)
+    mg.mg_random_starts(dataclasses.replace(prob, seed=seed), psi0,
+                        torch.cuda.current_stream())
     return U, psi0
 
 
@@ -112,6 +118,9 @@ class Server:
         self.nrhs = nrhs
         self.keep_results = keep_results
         self.device = device
+        # the device's free memory, counting blocks torch keeps cached but unused
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
         free, _ = torch.cuda.mem_get_info()
         self.budget = free - reserve_bytes
         self.used = 0
@@ -243,6 +252,7 @@ class Server:
                 raise
             self.late_timeout = True  # a coarse apply timed out after its request completed
         resident.clear()
+        torch.cuda.empty_cache()
         return self._stats(done, realtime)
 
     def _stats(self, done: List[Request], realtime: bool) -> dict:

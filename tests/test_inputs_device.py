@@ -39,3 +39,24 @@ def test_normals_links_and_starts_agree(device):
     assert np.abs(U - Uh).max() <= 1e-13
     p = D.psi0_t(dims, 8, 403, device).cpu().numpy()
     np.testing.assert_allclose(p, G.psi0(dims, 8, 403), rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.gpu
+def test_library_random_starts_match_host_generator():
+    """mg_random_starts draws the same counter-based starts as mg_inputs.psi0
+    (uniforms bit for bit; log, sqrt and cos in FP32: the argument of the
+    cosine carries the FP32 rounding of u, about 6e-8, times the radius
+    sqrt(-2 ln u) <= 9, so within 5e-6)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_03091_gb300 import build as _build
+    from paper_2502_03091_gb300 import mg
+    _build.build()
+    for dims, m, seed in (([4, 4, 2, 6], 8, 405), ([6, 4, 4, 4], 12, 2 ** 40 + 3)):
+        p = mg.Problem(dims=dims, block=[2, 2, 2, 2], m0=0.0, n_vec=m, k=4, mr_iters=1,
+                       seed=seed)
+        psi0 = torch.empty(mg.shape_psi(p), dtype=torch.complex64, device="cuda")
+        mg.mg_random_starts(p, psi0)
+        torch.cuda.synchronize()
+        got = psi0.cpu().numpy().astype(np.complex128)
+        np.testing.assert_allclose(got, G.psi0(dims, m, seed), rtol=1e-6, atol=5e-6)
