@@ -350,6 +350,16 @@ mg_status mg_chiral_truncate_static(const mg_problem* prob, const void* psi, voi
  * psi0 (caller-owned device memory).  Asynchronous on `stream`. */
 mg_status mg_random_starts(const mg_problem* prob, void* psi0, void* stream);
 
+/* Random SU(3) gauge links for synthetic inputs (input synthesis, not part of
+ * the method; the ensembles of Sec. 4 are not available): U [V][4][3][3]
+ * complex64, U_mu(x) = exp(i eps H), H = sum_a h_a lambda_a / 2, h_a the
+ * normals 8j .. 8j+7 (j = 4x + mu) of stream 1 of the counter-based generator
+ * of prob->seed, lambda_a the Gell-Mann matrices; the exponential by its
+ * Taylor series in FP32 (within a few 1e-7 of the exact exponential).
+ * 0 <= eps <= 1, else MG_ERR_INVALID.  Out: U
+ * (caller-owned device memory).  Asynchronous on `stream`. */
+mg_status mg_random_links(const mg_problem* prob, double eps, void* U, void* stream);
+
 /* Failure-detection self-test (no counterpart in the paper).  Enqueues on
  * `stream` one kernel whose single thread waits on a shared-memory mbarrier
  * that nothing ever arrives at, giving up after `polls` polls

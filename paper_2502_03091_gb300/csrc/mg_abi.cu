@@ -304,6 +304,18 @@ mg_status mg_random_starts(const mg_problem* prob, void* psi0, void* stream) {
                      "mg_random_starts");
 }
 
+mg_status mg_random_links(const mg_problem* prob, double eps, void* U, void* stream) {
+  Geom g;
+  mg_status st = make_geom(prob, &g);
+  if (st != MG_OK) return st;
+  if (!U) return fail(MG_ERR_INVALID, "mg_random_links: NULL array");
+  if (!(eps >= 0.0 && eps <= 1.0))
+    return fail(MG_ERR_INVALID, "mg_random_links: eps %g outside [0, 1]", eps);
+  return cuda_status(launch_random_links(g, prob->seed, eps, static_cast<float2*>(U),
+                                         static_cast<cudaStream_t>(stream)),
+                     "mg_random_links");
+}
+
 mg_status mg_selftest_timeout(int32_t polls, void* stream) {
   if (polls < 1 || polls > (1 << 20))
     return fail(MG_ERR_INVALID, "mg_selftest_timeout: polls %d out of [1, 1048576]", polls);

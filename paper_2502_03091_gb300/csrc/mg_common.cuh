@@ -149,8 +149,11 @@ cudaError_t launch_tc_gemm(const Geom& g, const float2* A, bool gather, const do
                            const float* abound, const float2* B, int n, float2* C, float* cmax,
                            int* status, cudaStream_t s, const char* name);
 
-// psi0 [V][4][3][m] from the counter-based generator of seed (mg_starts.cu).
+// psi0 [V][4][3][m] and links U [V][4][3][3] = exp(i eps H) from the
+// counter-based generator of seed (mg_starts.cu).
 cudaError_t launch_random_starts(const Geom& g, uint64_t seed, float2* psi0, cudaStream_t s);
+cudaError_t launch_random_links(const Geom& g, uint64_t seed, double eps, float2* U,
+                                cudaStream_t s);
 
 cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double* sigma,
                             float2* coarse_tv, int32_t* flags, char* ws, cudaStream_t s);

@@ -32,7 +32,7 @@ EXPORTS = ("mg_workspace_size", "mg_clover_field", "mg_apply_dirac", "mg_smooth_
            "mg_timing_enable",
            "mg_timing_read", "mg_batch_create", "mg_batch_launch", "mg_batch_streams",
            "mg_batch_destroy", "mg_tuned_pairs", "mg_sync_status", "mg_last_error", "mg_version",
-           "mg_selftest_timeout", "mg_random_starts",
+           "mg_selftest_timeout", "mg_random_starts", "mg_random_links",
            "mg_coarse_workspace_size", "mg_coarse_op_apply", "mg_coarse_smooth_testvecs",
            "mg_coarse_chiral_truncate", "mg_coarse_build_prolongator", "mg_coarse_coarsen",
            "mg_solve_workspace_size", "mg_solve")
@@ -221,6 +221,8 @@ def library(path: str = LIB_PATH):
     lib.mg_selftest_timeout.restype = ctypes.c_int
     lib.mg_random_starts.argtypes = [Pp, P, P]
     lib.mg_random_starts.restype = ctypes.c_int
+    lib.mg_random_links.argtypes = [Pp, ctypes.c_double, P, P]
+    lib.mg_random_links.restype = ctypes.c_int
     lib.mg_last_error.restype = ctypes.c_char_p
     lib.mg_version.restype = ctypes.c_char_p
     _lib = lib
@@ -287,6 +289,14 @@ def mg_random_starts(prob: Problem, psi0, stream=None):
     _expect(psi0, shape_psi(prob), torch.complex64, "psi0")
     pc = prob.c()
     _check(library().mg_random_starts(ctypes.byref(pc), _ptr(psi0), _stream(stream)))
+
+
+def mg_random_links(prob: Problem, eps: float, U, stream=None):
+    """U <- exp(i eps H) links of the counter-based generator of prob.seed."""
+    import torch
+    _expect(U, shape_U(prob), torch.complex64, "U")
+    pc = prob.c()
+    _check(library().mg_random_links(ctypes.byref(pc), float(eps), _ptr(U), _stream(stream)))
 
 
 def mg_selftest_timeout(polls: int, stream=None):

@@ -12,10 +12,10 @@ arrival) percentiles beside throughput.
 
 Inputs are synthesised on the device per request from a per-request seed,
 as part of handling the request, with the counter-based SplitMix64 /
-Box-Muller numbers of mg_inputs: the links exp(i eps H), H = sum_a h_a
-lambda_a / 2, by the torch form of that generator (mg_inputs.device), the
-complex Gaussian starts by the library's mg_random_starts, so a request's
-inputs are those the host generator gives for that seed.
+Box-Muller numbers of mg_inputs, by the library (mg_random_links: links
+exp(i eps H), H = sum_a h_a lambda_a / 2; mg_random_starts: complex Gaussian
+starts), so a request's inputs are those the host generator gives for that
+seed, to complex64 rounding.
 """
 from __future__ import annotations
 
@@ -70,18 +70,18 @@ def request_stream(n: int, rate: float, seed: int = 40, m0: float = -0.15,
 
 def synth_inputs(prob: mg.Problem, eps: float, seed: int, device="cuda"):
     """(U, psi0) complex64 on the device for one request (current stream):
-    mg_inputs.gauge_field(dims, eps, seed), drawn on the device in torch, and
-    mg_inputs.psi0(dims, m', seed), drawn by the library (mg_random_starts,
-    the same counter-based numbers to FP32 rounding)."""
+    mg_inputs.gauge_field(dims, eps, seed) and mg_inputs.psi0(dims, m', seed),
+    drawn by the library (mg_random_links, mg_random_starts: the same
+    counter-based numbers, to complex64 rounding)."""
     import dataclasses
 
     import torch
-
-    from mg_inputs import device as D
-    U = D.gauge_field_t(prob.dims, eps, seed, device).to(torch.complex64)
+    p = dataclasses.replace(prob, seed=seed)
+    s = torch.cuda.current_stream()
+    U = torch.empty(mg.shape_U(prob), dtype=torch.complex64, device=device)
+    mg.mg_random_links(p, eps, U, s)
     psi0 = torch.empty(mg.shape_psi(prob), dtype=torch.complex64, device=device)
-    mg.mg_random_starts(dataclasses.replace(prob, seed=seed), psi0,
-                        torch.cuda.current_stream())
+    mg.mg_random_starts(p, psi0, s)
     return U, psi0
 
 

@@ -60,3 +60,26 @@ def test_library_random_starts_match_host_generator():
         torch.cuda.synchronize()
         got = psi0.cpu().numpy().astype(np.complex128)
         np.testing.assert_allclose(got, G.psi0(dims, m, seed), rtol=1e-6, atol=5e-6)
+
+
+@pytest.mark.gpu
+def test_library_random_links_match_host_generator():
+    """mg_random_links draws mg_inputs.gauge_field's links exp(i eps H) (normals
+    in FP64, the exponential's Taylor series in FP32: within 1e-6), and they
+    are SU(3) to FP32 rounding."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_03091_gb300 import build as _build
+    from paper_2502_03091_gb300 import mg
+    _build.build()
+    for dims, eps, seed in (([4, 4, 2, 6], 0.25, 406), ([4, 2, 2, 4], 0.35, 2 ** 33 + 1)):
+        p = mg.Problem(dims=dims, block=[2, 2, 2, 2], m0=0.0, n_vec=8, k=4, mr_iters=1,
+                       seed=seed)
+        U = torch.empty(mg.shape_U(p), dtype=torch.complex64, device="cuda")
+        mg.mg_random_links(p, eps, U)
+        torch.cuda.synchronize()
+        got = U.cpu().numpy().astype(np.complex128)
+        np.testing.assert_allclose(got, G.gauge_field(dims, eps, seed), rtol=0, atol=1e-6)
+        g = got.reshape(-1, 3, 3)
+        np.testing.assert_allclose(np.einsum("nij,nkj->nik", g, g.conj()),
+                                   np.broadcast_to(np.eye(3), g.shape), atol=1e-6)
