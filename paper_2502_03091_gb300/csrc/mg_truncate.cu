@@ -16,6 +16,8 @@
 // choice of rows: chirality 0 is spins {0,1}, chirality 1 spins {2,3}.
 // In the mixed-precision paths G1, Q1 (then stored), G2 and U_k = Q1 (R2^-1 U~_k)
 // are tensor-core contractions (mg_tc.cu); the small FP64 stages are shared.
+#include <algorithm>
+
 #include "mg_common.cuh"
 
 namespace mg {
@@ -208,183 +210,14 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const float2* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// FP64 dense helpers on shared memory (one CTA, m <= 64).  Matrices use the
-// leading dimension ld = m + 1: the padding keeps column accesses free of
-// bank conflicts.
-// ---------------------------------------------------------------------------
-
-__device__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  return s;
-}
-
-// In-place upper Cholesky G = R^dag R on the upper triangle of Gs (m x m,
-// leading dimension ld).  Returns false if a pivot is <= tol; the lower
-// triangle is zeroed on exit.
-__device__ bool chol_upper(double2* Gs, int m, int ld, double tol, int* s_fail) {
-  if (threadIdx.x == 0) *s_fail = 0;
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = Gs[j * ld + j].x;
-      if (!(d > tol)) *s_fail = 1;
-      Gs[j * ld + j] = make_double2(d > tol ? sqrt(d) : 1.0, 0.0);
-    }
-    __syncthreads();
-    const double inv = 1.0 / Gs[j * ld + j].x;
-    for (int l = j + 1 + threadIdx.x; l < m; l += blockDim.x)
-      Gs[j * ld + l] = zscale(Gs[j * ld + l], inv);
-    __syncthreads();
-    const int n = m - j - 1;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int r = j + 1 + idx / n, c = j + 1 + idx % n;
-      if (c >= r) Gs[r * ld + c] = zsub(Gs[r * ld + c], zmulc(Gs[j * ld + r], Gs[j * ld + c]));
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x)
-    if (idx / m > idx % m) Gs[(idx / m) * ld + idx % m] = make_double2(0.0, 0.0);
-  __syncthreads();
-  return *s_fail == 0;
-}
-
-// Cholesky of a Hermitian matrix close to the identity, G = 1 + E, in
-// deviations: R = 1 + F with F upper triangular.  Every update acts on the
-// small quantities only (the diagonal is kept as delta_jj = a_jj - 1 and
-// r_jj - 1 = delta_jj / (1 + sqrt(1 + delta_jj)) has no cancellation), so FP32
-// gives F to FP32 relative accuracy, i.e. R to ~1e-7 |E| absolute.  Gs (FP64,
-// leading dimension ld) holds G on entry and R (upper, 1 + F) on exit; the
-// FP32 deviations live in the first 8 bytes of each 16-byte entry meanwhile.
-// Returns false if a pivot 1 + delta_jj is not positive (it is then set to 1).
-__device__ bool chol_upper_near1(double2* Gs, int m, int ld, int* s_fail) {
-  float2* Ef = reinterpret_cast<float2*>(Gs);  // entry e at Ef[2 e]
-  if (threadIdx.x == 0) *s_fail = 0;
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    const int i = idx / m, c = idx % m;
-    const double2 v = Gs[i * ld + c];
-    Ef[2 * (i * ld + c)] = make_float2((float)(v.x - (i == c ? 1.0 : 0.0)), (float)v.y);
-  }
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    if (threadIdx.x == 0) {
-      float dj = Ef[2 * (j * ld + j)].x;
-      if (!(1.0f + dj > 1e-6f)) {
-        *s_fail = 1;
-        dj = 0.f;
-      }
-      Ef[2 * (j * ld + j)] = make_float2(dj / (1.0f + sqrtf(1.0f + dj)), 0.f);
-    }
-    __syncthreads();
-    const float inv = 1.0f / (1.0f + Ef[2 * (j * ld + j)].x);
-    for (int l = j + 1 + threadIdx.x; l < m; l += blockDim.x) {
-      float2& r = Ef[2 * (j * ld + l)];
-      r = make_float2(r.x * inv, r.y * inv);
-    }
-    __syncthreads();
-    const int n = m - j - 1;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int r = j + 1 + idx / n, c = j + 1 + idx % n;
-      if (c >= r) {
-        const float2 a = Ef[2 * (j * ld + r)], b = Ef[2 * (j * ld + c)];
-        float2& e = Ef[2 * (r * ld + c)];
-        // e -= conj(a) b
-        e = make_float2(e.x - (a.x * b.x + a.y * b.y), e.y - (a.x * b.y - a.y * b.x));
-      }
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    const int i = idx / m, c = idx % m;
-    const float2 f = Ef[2 * (i * ld + c)];
-    Gs[i * ld + c] = c < i ? make_double2(0.0, 0.0)
-                           : make_double2((i == c ? 1.0 : 0.0) + (double)f.x, (double)f.y);
-  }
-  __syncthreads();
-  return *s_fail == 0;
-}
-
-// Stage 1: R1 = chol(G1) (with a diagonal shift if a pivot fails), store R1
-// (FP64) and Z1 = R1^{-1} (FP32).  The inverse is formed row by row from the
-// bottom: z_ic = (delta_ic - sum_{i<l<=c} R_il z_lc) / R_ii, four threads per
-// column sharing the sum.
-__global__ void __launch_bounds__(kThreads, 2) chol_stage1(const double2* __restrict__ G,
-                                                           double2* __restrict__ R1,
-                                                           float2* __restrict__ Z1,
-                                                           int32_t* __restrict__ flags, int m) {
-  extern __shared__ double2 dsm[];
-  const int ld = m + 1;
-  double2* Gs = dsm;                                    // [m][ld] FP64
-  float2* Zs = reinterpret_cast<float2*>(Gs + m * ld);  // [m][m] FP32
-  __shared__ int s_fail;
-  __shared__ double red[32];
-  const int bc = blockIdx.x;
-  const double2* Gb = G + (long)bc * m * m;
-  double mx = 0;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    const double2 v = Gb[i];
-    Gs[(i / m) * ld + i % m] = v;
-    if (i / m == i % m) mx = fmax(mx, v.x);
-  }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  double maxd = 0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) maxd = fmax(maxd, red[i]);
-  int32_t flag = 0;
-  if (!chol_upper(Gs, m, ld, 1e-13 * maxd, &s_fail)) {
-    flag |= 1;
-    for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-      double2 v = Gb[i];
-      if (i / m == i % m) v.x += 1e-5 * maxd;
-      Gs[(i / m) * ld + i % m] = v;
-    }
-    __syncthreads();
-    if (!chol_upper(Gs, m, ld, 1e-13 * maxd, &s_fail)) flag |= 2;
-  }
-  double2* Rb = R1 + (long)bc * m * m;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    Rb[i] = Gs[(i / m) * ld + i % m];
-    Zs[i] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  // Z1 is an FP32 output and R1 is well conditioned: the substitution runs in
-  // FP32 arithmetic on the FP64 factor rounded to FP32
-  const int c = threadIdx.x >> 2, part = threadIdx.x & 3;
-  for (int i = m - 1; i >= 0; --i) {
-    float2 acc = make_float2(0.f, 0.f);
-    if (c < m && c >= i)
-      for (int l = i + 1 + part; l <= c; l += 4) {
-        const double2 r = Gs[i * ld + l];
-        cfma(acc, make_float2((float)r.x, (float)r.y), Zs[l * m + c]);
-      }
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-    if (c < m && c >= i && part == 0) {
-      const float inv = (float)(1.0 / Gs[i * ld + i].x);
-      Zs[i * m + c] = make_float2(((i == c ? 1.f : 0.f) - acc.x) * inv, -acc.y * inv);
-    }
-    __syncthreads();
-  }
-  float2* Zb = Z1 + (long)bc * m * m;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) Zb[i] = Zs[i];
-  if (threadIdx.x == 0) flags[bc] = flag;
-}
-
-// ---------------------------------------------------------------------------
 // Double-float numbers: value = hi + lo, two FP32 with |lo| <= ulp(hi) / 2.
 // Sums by Knuth's TwoSum and products by the FMA form of Dekker's TwoProduct
 // (error-free transformations; cf. Hida, Li, Bailey, "Algorithms for quad-double
 // precision", 2001) give about 2^-44 relative accuracy on the FP32 pipe, which
 // on this GPU issues 64 times the FP64 rate.  The _rn intrinsics keep the
-// compiler from fusing the operations the transformations rely on.
+// compiler from fusing the operations the transformations rely on.  The
+// small dense stages below run on these numbers; FP64 is left to O(m) scalar
+// work per block-chirality (the tridiagonal eigenvectors).
 // ---------------------------------------------------------------------------
 struct df {
   float hi, lo;
@@ -424,9 +257,33 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return quick_two_sum(p, e);
 }
+__device__ __forceinline__ df df_mulf(df a, float b) {  // a b, b an FP32 number
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_half(df a) { return df{0.5f * a.hi, 0.5f * a.lo}; }
+// 1 / a: the FP32 reciprocal q and one Newton step q + q (1 - a q); the
+// residual 1 - a q is exact in double-float, so the result has ~2^-46 error
+__device__ __forceinline__ df df_recip(df a) {
+  const float q = __frcp_rn(a.hi);
+  const df r = df_sub(df{1.f, 0.f}, df_mulf(a, q));
+  return df_add(df{q, 0.f}, df_mulf(r, q));
+}
+// sqrt(a) for a > 0: y = sqrt(a.hi) and one Newton step y + (a - y^2) / (2 y)
+__device__ __forceinline__ df df_sqrt(df a) {
+  const float y = __fsqrt_rn(a.hi);
+  const float p = __fmul_rn(y, y);
+  const df r = df_sub(a, df{p, __fmaf_rn(y, y, -p)});
+  return quick_two_sum(y, __fdiv_rn(r.hi, 2.f * y));
+}
 
 __device__ __forceinline__ dz dz_from(double2 v) { return dz{df_from(v.x), df_from(v.y)}; }
 __device__ __forceinline__ double2 dz_to(dz a) { return make_double2(df_to(a.re), df_to(a.im)); }
+__device__ __forceinline__ float2 dz_to_f(dz a) {
+  return make_float2(__fadd_rn(a.re.hi, a.re.lo), __fadd_rn(a.im.hi, a.im.lo));
+}
 __device__ __forceinline__ dz dz_zero() { return dz{df{0.f, 0.f}, df{0.f, 0.f}}; }
 __device__ __forceinline__ dz dz_add(dz a, dz b) { return dz{df_add(a.re, b.re), df_add(a.im, b.im)}; }
 __device__ __forceinline__ dz dz_sub(dz a, dz b) { return dz{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
@@ -440,93 +297,169 @@ __device__ __forceinline__ dz dz_mulc(dz a, dz b) {  // conj(a) b
 }
 __device__ __forceinline__ dz dz_conj(dz a) { return dz{a.re, df_neg(a.im)}; }
 __device__ __forceinline__ dz dz_scale(dz a, df s) { return dz{df_mul(a.re, s), df_mul(a.im, s)}; }
+__device__ __forceinline__ df dz_abs2(dz a) { return df_add(df_mul(a.re, a.re), df_mul(a.im, a.im)); }
 __device__ __forceinline__ df df_shfl_xor(df a, int o) {
   return df{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
-__device__ __forceinline__ dz dz_warp_sum(dz a) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a.re = df_add(a.re, df_shfl_xor(a.re, o));
-    a.im = df_add(a.im, df_shfl_xor(a.im, o));
-  }
+__device__ __forceinline__ dz dz_shfl_xor(dz a, int o) {
+  return dz{df_shfl_xor(a.re, o), df_shfl_xor(a.im, o)};
+}
+__device__ __forceinline__ dz dz_shfl(dz a, int src) {
+  return dz{df{__shfl_sync(0xffffffffu, a.re.hi, src), __shfl_sync(0xffffffffu, a.re.lo, src)},
+            df{__shfl_sync(0xffffffffu, a.im.hi, src), __shfl_sync(0xffffffffu, a.im.lo, src)}};
+}
+__device__ __forceinline__ df df_warp_sum(df a) {
+  for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_xor(a, o));
   return a;
 }
 
-// ---------------------------------------------------------------------------
-// Top-k eigenpairs of a Hermitian m x m matrix in shared memory: Householder
-// tridiagonalisation (double-float), Sturm multisection (FP32), inverse
-// iteration and Rayleigh quotients (FP64).
-// ---------------------------------------------------------------------------
-
-// Hs: Hermitian (full, leading dimension ld), double-float.  On exit:
-// d[0..m), e[0..m-1) complex subdiagonal T[j+1][j], reflector j stored in
-// column j of Hs rows j+1.. (u_j), tau[j].  H = Q T Q^dag with
-// Q = H_0 H_1 ... H_{m-3}, H_j = I - tau_j u_j u_j^dag.  The scalars of each
-// reflector (norms, tau, beta) are formed in FP64.
-__device__ void tridiagonalise(dz* Hs, int m, int ld, double* d, double2* e, double* tau,
-                               dz* uv, dz* pv, double* red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = 0; j + 2 < m; ++j) {
-    const int n = m - j - 1;  // length of x = H[j+1.., j]
-    double tail = 0;
-    for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) tail += zabs2(dz_to(Hs[i * ld + j]));
-    tail = block_sum(tail, red);
-    const double2 x0 = dz_to(Hs[(j + 1) * ld + j]);
-    double t = 0.0;
-    double2 beta = x0;
-    if (tail > 0.0) {
-      const double ax0 = sqrt(zabs2(x0));
-      const double nx = sqrt(zabs2(x0) + tail);
-      const double2 ph = ax0 > 0 ? zscale(x0, 1.0 / ax0) : make_double2(1.0, 0.0);
-      beta = zscale(ph, -nx);
-      const double2 u0 = zsub(x0, beta);
-      t = 2.0 / (zabs2(u0) + tail);
-      const df tdf = df_from(t);
-      // u (contiguous copy) and its column copy for the back-transform
-      for (int a = threadIdx.x; a < n; a += blockDim.x)
-        uv[a] = a == 0 ? dz_from(u0) : Hs[(j + 1 + a) * ld + j];
-      __syncthreads();
-      if (threadIdx.x == 0) Hs[(j + 1) * ld + j] = dz_from(u0);
-      // p = t A u over the trailing block A = H[j+1.., j+1..], one warp per row
-      for (int a = w; a < n; a += nw) {
-        dz sacc = dz_zero();
-        const dz* row = Hs + (j + 1 + a) * ld + j + 1;
-        for (int b = lane; b < n; b += 32) sacc = dz_add(sacc, dz_mul(row[b], uv[b]));
-        sacc = dz_warp_sum(sacc);
-        if (lane == 0) pv[a] = dz_scale(sacc, tdf);
-      }
-      __syncthreads();
-      // K = t/2 u^dag p (real); w = p - K u (stored over p)
-      double kr = 0;
-      for (int a = threadIdx.x; a < n; a += blockDim.x) kr += zmulc(dz_to(uv[a]), dz_to(pv[a])).x;
-      kr = 0.5 * t * block_sum(kr, red);
-      const df krdf = df_from(kr);
-      for (int a = threadIdx.x; a < n; a += blockDim.x)
-        pv[a] = dz_sub(pv[a], dz_scale(uv[a], krdf));
-      __syncthreads();
-      // A -= u w^dag + w u^dag
-      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int ra = idx / n, cb = idx % n;
-        dz v = Hs[(j + 1 + ra) * ld + j + 1 + cb];
-        v = dz_sub(v, dz_mul(uv[ra], dz_conj(pv[cb])));
-        v = dz_sub(v, dz_mul(pv[ra], dz_conj(uv[cb])));
-        Hs[(j + 1 + ra) * ld + j + 1 + cb] = v;
-      }
-    }
-    if (threadIdx.x == 0) {
-      e[j] = beta;
-      tau[j] = t;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    if (m >= 2) {
-      e[m - 2] = dz_to(Hs[(m - 1) * ld + m - 2]);
-      tau[m - 2] = 0.0;
-    }
-  }
-  for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = df_to(Hs[i * ld + i].re);
-  __syncthreads();
+// (r, c) of entry idx of a lower triangle stored row by row (idx = r (r+1)/2 + c,
+// c <= r); the FP32 square root is within one of the row, fixed up exactly
+__device__ __forceinline__ void tri_index(int idx, int& r, int& c) {
+  int a = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+  if ((a + 1) * (a + 2) / 2 <= idx) ++a;
+  if (a * (a + 1) / 2 > idx) --a;
+  r = a;
+  c = idx - a * (a + 1) / 2;
 }
+
+__device__ __forceinline__ float block_max(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float s = 0.f;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s = fmaxf(s, red[i]);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Stage 1: R1 = chol(G1), with a diagonal shift if a pivot fails; R1 is stored
+// in FP64 and Z1 = R1^{-1} in FP32.  The elimination runs in double-float as
+// G1 = L D L^dag (no square roots inside it), R1 = D^(1/2) L^dag at the end:
+// each step reads the pivot d_j, and the trailing upper triangle takes
+// g_rc -= conj(g_jr) g_jc / d_j, one barrier per step.  R1 only preconditions
+// the second pass of CholeskyQR2, for which ~2^-44 relative accuracy is ample.
+// Matrices in shared memory use the leading dimension m + 1.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 2) chol_stage1(const double2* __restrict__ G,
+                                                           double2* __restrict__ R1,
+                                                           float2* __restrict__ Z1,
+                                                           int32_t* __restrict__ flags, int m) {
+  extern __shared__ double2 dsm[];
+  const int ld = m + 1, ldz = m + 4, tid = threadIdx.x;
+  constexpr int nt = kThreads;
+  dz* Gz = reinterpret_cast<dz*>(dsm);          // [m][ld] during the elimination
+  float2* Rf = reinterpret_cast<float2*>(dsm);  // [m][ld] R1 (FP32) afterwards
+  float2* Zt = Rf + m * ld;                     // [m][ldz]: column c of Z1 in row c
+  __shared__ double piv[kMaxM];
+  __shared__ df rs[kMaxM];
+  __shared__ float rinv[kMaxM], redf[kThreads / 32];
+  __shared__ int s_fail;
+  const int bc = blockIdx.x;
+  const double2* Gb = G + (long)bc * m * m;
+  float mx = 0.f;
+  for (int i = tid; i < m; i += nt) mx = fmaxf(mx, (float)Gb[i * m + i].x);
+  const float maxd = block_max(mx, redf);
+  const float tol = 1e-13f * maxd;
+  int32_t flag = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const double shift = attempt ? 1e-5 * (double)maxd : 0.0;
+    for (int i = tid; i < m * m; i += nt) {
+      const int r = i / m, c = i % m;
+      if (c >= r) {
+        double2 v = Gb[i];
+        if (r == c) v.x += shift;
+        Gz[r * ld + c] = dz_from(v);
+      }
+    }
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+      df dj = Gz[j * ld + j].re;
+      const bool bad = !(dj.hi > tol);
+      if (bad) dj = df{1.f, 0.f};
+      if (tid == 0) {
+        piv[j] = df_to(dj);
+        if (bad) s_fail = 1;
+      }
+      const df inv = df_recip(dj);
+      const int n = m - j - 1;
+      for (int idx = tid; idx < n * (n + 1) / 2; idx += nt) {
+        int a, b;
+        tri_index(idx, a, b);
+        const int r = j + 1 + b, c = j + 1 + a;  // r <= c
+        const dz x = Gz[j * ld + r], y = dz_scale(Gz[j * ld + c], inv);
+        Gz[r * ld + c] = dz_sub(Gz[r * ld + c], dz_mulc(x, y));
+      }
+      __syncthreads();
+    }
+    const bool failed = s_fail != 0;
+    __syncthreads();  // s_fail is read by all before the next attempt resets it
+    if (!failed) break;
+    flag |= attempt ? 2 : 1;
+  }
+  // R1 = D^(1/2) L^dag
+  for (int i = tid; i < m; i += nt) rs[i] = df_recip(df_sqrt(df_from(piv[i])));
+  __syncthreads();
+  double2* Rb = R1 + (long)bc * m * m;
+  constexpr int kSlots = kMaxM * kMaxM / kThreads;
+  float2 rf[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const int i = tid + s * nt;
+    float2 v = make_float2(0.f, 0.f);
+    if (i < m * m) {
+      const int r = i / m, c = i % m;
+      double2 o = make_double2(0.0, 0.0);
+      if (c > r)
+        o = dz_to(dz_scale(Gz[r * ld + c], rs[r]));
+      else if (c == r)
+        o = make_double2(sqrt(piv[r]), 0.0);
+      Rb[i] = o;
+      v = make_float2((float)o.x, (float)o.y);
+    }
+    rf[s] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const int i = tid + s * nt;
+    if (i < m * m) Rf[(i / m) * ld + i % m] = rf[s];
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += nt) rinv[i] = 1.f / Rf[i * ld + i].x;
+  __syncthreads();
+  // Z1 = R1^{-1} (an FP32 output; R1 is well conditioned after the shift
+  // check): z_ic = (delta_ic - sum_{i<l<=c} R_il z_lc) / R_ii from the bottom,
+  // column c by four lanes of one warp, so a warp barrier per row suffices
+  {
+    const int c = tid >> 2, part = tid & 3;
+    for (int i = m - 1; i >= 0; --i) {
+      float2 acc = make_float2(0.f, 0.f);
+      if (c < m && i <= c)
+        for (int l = i + 1 + part; l <= c; l += 4) cfma(acc, Rf[i * ld + l], Zt[c * ldz + l]);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+      if (c < m && i <= c && part == 0)
+        Zt[c * ldz + i] = make_float2(((i == c ? 1.f : 0.f) - acc.x) * rinv[i], -acc.y * rinv[i]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  float2* Zb = Z1 + (long)bc * m * m;
+  for (int i = tid; i < m * m; i += nt) {
+    const int r = i / m, c = i % m;
+    Zb[i] = c >= r ? Zt[c * ldz + r] : make_float2(0.f, 0.f);
+  }
+  if (tid == 0) flags[bc] = flag;
+}
+
+// ---------------------------------------------------------------------------
+// Top-k eigenpairs of the real symmetric tridiagonal (d, f): Sturm
+// multisection (FP32), then inverse iteration and Rayleigh quotients (FP64).
+// ---------------------------------------------------------------------------
 
 // number of eigenvalues of the real symmetric tridiagonal (d, f) below x, in
 // FP32 (locates eigenvalues to ~1e-7 |T|; they are refined in FP64 later)
@@ -542,8 +475,8 @@ __device__ int sturm_count32(const float* d, const float* f2, int n, float x, fl
 }
 
 // LU factorisation with partial pivoting of the tridiagonal T - lam (diagonal
-// d, off-diagonal f): U has diagonals a, c, c2; L has multipliers l and the
-// row swaps in the bit mask piv
+// d, off-diagonal f): U has diagonals a (stored as reciprocals), c, c2; L has
+// multipliers l and the row swaps in the bit mask piv
 struct TriLU {
   double a[kMaxM], c[kMaxM], c2[kMaxM], l[kMaxM];
   unsigned long long piv;
@@ -576,8 +509,10 @@ __device__ void tri_factor(const double* d, const double* f, int n, double lam, 
       F.c[i] = tmp;
     }
   }
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (fabs(F.a[i]) < tiny) F.a[i] = F.a[i] < 0 ? -tiny : tiny;
+    F.a[i] = 1.0 / F.a[i];
+  }
 }
 
 // one step of inverse iteration: z <- (T - lam)^{-1} z with the factors F
@@ -595,92 +530,132 @@ __device__ void tri_solve(const TriLU& F, int n, double* z) {
     double sacc = z[i];
     if (i + 1 < n) sacc -= F.c[i] * z[i + 1];
     if (i + 2 < n) sacc -= F.c2[i] * z[i + 2];
-    z[i] = sacc / F.a[i];
+    z[i] = sacc * F.a[i];
   }
 }
 
-// Stage 2: R2 = chol(G2), R = R2 R1, H = R R^dag, top-k eigenpairs of H,
-// sigma = sqrt(lambda), W2 = R2^{-1} U~_k (FP32), optional Sigma_k V_k^dag = U~_k^dag R.
-// Global scratch per block-chirality: G (in: G2, out: R2), R1 (in: R1,
-// out: R), Hg (H).
+// ---------------------------------------------------------------------------
+// Stage 2, one CTA per block-chirality:
+//   1. R2 = chol(G2) = 1 + F in FP32 deviations (G2 = Q1^dag Q1 is 1 up to
+//      rounding, so F carries FP32 relative accuracy);
+//   2. R = R2 R1 = R1 + F R1 (the small correction in FP32, the sum in
+//      double-float; FP64 through global scratch if F is not small);
+//   3. H = R R^dag (lower triangle, double-float);
+//   4. Householder tridiagonalisation of H (double-float), T = Q^dag H Q;
+//   5. top-k eigenpairs of T (multisection FP32, inverse iteration FP64);
+//   6. back-transform U~_k = Q Delta Z (double-float, in registers);
+//   7. sigma = sqrt(lambda), W2 = R2^{-1} U~_k (FP32) and optionally
+//      Sigma_k V_k^dag = U~_k^dag R (FP64).
+// Global scratch per block-chirality: G2 (in; F as FP32 out), R1 (in; R out
+// when the coarse test vectors are wanted), Hg (R in FP64 if F is not small).
+// ---------------------------------------------------------------------------
 constexpr int kBisect = 10;  // points per multisection step
+constexpr int kHSlots = (kMaxM * (kMaxM + 1) / 2 + kThreads - 1) / kThreads;
 
 __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
     double2* __restrict__ G2, double2* __restrict__ R1, double2* __restrict__ Hg,
     float2* __restrict__ W2, double* __restrict__ sigma, float2* __restrict__ ctv,
     int32_t* __restrict__ flags, int m, int k) {
   extern __shared__ double2 dsm[];
-  const int ld = m + 1;
-  double2* M = dsm;            // [m][ld]
-  double2* Uk = M + m * ld;    // [m][k]
-  __shared__ double d[kMaxM], tau[kMaxM], fo[kMaxM];
-  __shared__ float d32[kMaxM], f232[kMaxM];
-  __shared__ double s_dmax;
-  __shared__ double2 e[kMaxM], delta[kMaxM], uv[kMaxM], pv[kMaxM], rowbuf[kMaxM];
-  __shared__ double red[32];
-  __shared__ double lo[kMaxK], hi[kMaxK], lam[kMaxK];
+  const int ld = m + 1, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  constexpr int nt = kThreads, nw = kThreads / 32;
+  float2* E = reinterpret_cast<float2*>(dsm);            // [m][ld] F = R2 - 1 (steps 1-2, 7)
+  float2* R1f = E + m * ld;                              // [m][m] R1 in FP32 (step 2)
+  dz* Mz = reinterpret_cast<dz*>(dsm);                   // [m][ld] R, H, reflectors (2-6)
+  double* Zt = reinterpret_cast<double*>(dsm + m * ld);  // [k][m] eigenvectors of T_r
+  double2* Ut = dsm + m * ld;                            // [m][k] U~_k for the test vectors
+  __shared__ dz uvb[2][kMaxM], pvz[kMaxM], wvz[kMaxM];
+  __shared__ df taud[kMaxM], kred[nw];
+  __shared__ double d[kMaxM], fo[kMaxM], lam[kMaxK];
+  __shared__ double2 e[kMaxM], delta[kMaxM];
+  __shared__ double lo[kMaxK], hi[kMaxK];
+  __shared__ float d32[kMaxM], f232[kMaxM], rinv[kMaxM], redf[nw];
   __shared__ int cnt[kMaxK][kBisect];
-  __shared__ int s_fail;
   __shared__ int leader[kMaxK];
+  __shared__ int s_fail;
+  __shared__ float s_tn;
   const int bc = blockIdx.x;
   double2* Gb = G2 + (long)bc * m * m;
+  float2* Fg = reinterpret_cast<float2*>(Gb);
   double2* Rg = R1 + (long)bc * m * m;
   double2* Hb = Hg + (long)bc * m * m;
-  // R2 = chol(G2), kept in global for W2
-  double mx = 0;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    const double2 v = Gb[i];
-    M[(i / m) * ld + i % m] = v;
-    if (i / m == i % m) mx = fmax(mx, v.x);
+
+  // ---- 1. R2 = 1 + F.  Every update acts on small quantities (the pivot as
+  // f_jj = e_jj / (1 + sqrt(1 + e_jj)), free of cancellation).  Row j is
+  // scaled by 1 / r_jj one step late, when nothing reads it any more, so each
+  // step takes one barrier.
+  for (int i = tid; i < m * m; i += nt) {
+    const int r = i / m, c = i % m;
+    if (c >= r) {
+      const double2 v = Gb[i];
+      E[r * ld + c] = make_float2((float)(v.x - (r == c ? 1.0 : 0.0)), (float)v.y);
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  if (tid == 0) s_fail = 0;
   __syncthreads();
-  double maxd = 0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) maxd = fmax(maxd, red[i]);
-  int32_t flag = 0;
-  // G2 = Q1^dag Q1 is the identity up to the rounding of Q1: the Cholesky of
-  // its deviation in FP32 keeps R2 - 1 to FP32 relative accuracy
-  (void)maxd;
-  if (!chol_upper_near1(M, m, ld, &s_fail)) flag |= 4;
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) Gb[i] = M[(i / m) * ld + i % m];
-  __syncthreads();
-  // R = R2 R1 = R1 + (R2 - 1) R1.  After CholeskyQR2's first pass R2 = 1 + D
-  // with D small, so the correction D R1 is formed in FP32 and added to R1 in
-  // FP64: its error u_fp32 |D| |R1| is below the FP32 rounding of the input
-  // vectors by the factor |D| < 1e-3.  A larger D takes the FP64 product.
-  // Column c of R1 is read in chunks of 16 rows; each thread keeps 16 rows of
-  // one column.  R -> Hb.
   {
-    double dm = 0;
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-      const int i = idx / m, c = idx % m;
-      const double2 v = M[i * ld + c];
-      dm = fmax(dm, fabs(v.x - (i == c ? 1.0 : 0.0)) + fabs(v.y));
+    float inv_prev = 1.f, f_prev = 0.f;
+    for (int j = 0; j <= m; ++j) {
+      float inv = 1.f, fjj = 0.f;
+      if (j < m) {
+        float dj = E[j * ld + j].x;
+        const bool bad = !(1.f + dj > 1e-6f);
+        if (bad) dj = 0.f;
+        if (bad && tid == 0) s_fail = 1;
+        fjj = dj / (1.f + sqrtf(1.f + dj));
+        inv = 1.f / (1.f + fjj);
+      }
+      if (j > 0)
+        for (int l = j - 1 + tid; l < m; l += nt) {
+          float2& x = E[(j - 1) * ld + l];
+          x = l == j - 1 ? make_float2(f_prev, 0.f) : make_float2(x.x * inv_prev, x.y * inv_prev);
+        }
+      if (j < m) {
+        const float inv2 = inv * inv;
+        const int n = m - j - 1;
+        for (int idx = tid; idx < n * (n + 1) / 2; idx += nt) {
+          int a, b;
+          tri_index(idx, a, b);
+          const int r = j + 1 + b, c = j + 1 + a;  // r <= c
+          const float2 x = E[j * ld + r], y = E[j * ld + c];
+          float2& v = E[r * ld + c];
+          v = make_float2(v.x - (x.x * y.x + x.y * y.y) * inv2, v.y - (x.x * y.y - x.y * y.x) * inv2);
+        }
+      }
+      inv_prev = inv;
+      f_prev = fjj;
+      __syncthreads();
     }
-    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmax(t, red[i]);
-      s_dmax = t;
+  }
+
+  // ---- 2. R = R1 + F R1.  With |F| < 1e-3 the FP32 correction's error is
+  // below the FP32 rounding of the input vectors by that factor.
+  {
+    float dm = 0.f;
+    for (int i = tid; i < m * m; i += nt) {
+      const int r = i / m, c = i % m;
+      float2 f = make_float2(0.f, 0.f);
+      if (c >= r) {
+        f = E[r * ld + c];
+        dm = fmaxf(dm, fabsf(f.x) + fabsf(f.y));
+      }
+      Fg[i] = f;
+      const double2 v = Rg[i];
+      R1f[i] = make_float2((float)v.x, (float)v.y);
     }
-    __syncthreads();
-    const bool small = s_dmax < 1e-3;
-    const int c = threadIdx.x % 64, r0 = threadIdx.x / 64;  // rows r0, r0+4, ...
-    if (c < m) {
-      if (small) {
-        float2 acc[16];
+    const bool small = block_max(dm, redf) < 1e-3f;
+    const int c = tid & 63, r0 = tid >> 6;  // rows r0, r0 + 4, ...
+    float2 acc[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) acc[r] = make_float2(0.f, 0.f);
+    for (int r = 0; r < 16; ++r) acc[r] = make_float2(0.f, 0.f);
+    if (small) {
+      if (c < m)
         for (int l0 = 0; l0 < m; l0 += 16) {
           float2 col[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const int l = l0 + q;
-            const double2 v = l < m ? Rg[l * m + c] : make_double2(0.0, 0.0);
-            col[q] = make_float2((float)v.x, (float)v.y);
+            col[q] = l < m ? R1f[l * m + c] : make_float2(0.f, 0.f);
           }
 #pragma unroll
           for (int r = 0; r < 16; ++r) {
@@ -689,132 +664,281 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
               const int l = l0 + q;
-              if (l < m && l >= i) {
-                const double2 dv = M[i * ld + l];
-                cfma(acc[r], make_float2((float)(dv.x - (l == i ? 1.0 : 0.0)), (float)dv.y), col[q]);
-              }
+              if (l < m && l >= i && l <= c) cfma(acc[r], E[i * ld + l], col[q]);
             }
           }
         }
+    } else if (c < m) {
+      for (int i = r0; i < m; i += 4) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int l = i; l <= c; ++l) {
+          const float2 f = E[i * ld + l];
+          s = zadd(s, zmul(make_double2((l == i ? 1.0 : 0.0) + (double)f.x, (double)f.y), Rg[l * m + c]));
+        }
+        Hb[i * m + c] = c >= i ? s : make_double2(0.0, 0.0);
+      }
+    }
+    __syncthreads();  // E and R1f are consumed; R (double-float) overwrites them
+    if (c < m) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int i = r0 + 4 * r;
-          if (i < m) {
-            const double2 base = c >= i ? Rg[i * m + c] : make_double2(0.0, 0.0);
-            Hb[i * m + c] = c >= i ? make_double2(base.x + acc[r].x, base.y + acc[r].y)
-                                   : make_double2(0.0, 0.0);
-          }
+      for (int r = 0; r < 16; ++r) {
+        const int i = r0 + 4 * r;
+        if (i >= m) continue;
+        double2 rv = make_double2(0.0, 0.0);
+        if (!small) {
+          rv = Hb[i * m + c];
+        } else if (c >= i) {
+          const double2 b = Rg[i * m + c];
+          rv = make_double2(b.x + (double)acc[r].x, b.y + (double)acc[r].y);
         }
-      } else {
-        for (int i = r0; i < m; i += 4) {
-          double2 acc = make_double2(0.0, 0.0);
-          for (int l = i; l <= c; ++l) acc = zadd(acc, zmul(M[i * ld + l], Rg[l * m + c]));
-          Hb[i * m + c] = acc;
-        }
+        Mz[i * ld + c] = dz_from(rv);
+        if (ctv) Rg[i * m + c] = rv;
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-      const double2 v = Hb[i];
-      M[(i / m) * ld + i % m] = v;
-      Rg[i] = v;
+  }
+
+  // ---- 3. H = R R^dag, lower triangle: h_ij = sum_{l>=i} r_il conj(r_jl),
+  // j <= i.  The results wait in registers until every thread has read R.
+  {
+    const int T = m * (m + 1) / 2;
+    dz h[kHSlots];
+#pragma unroll
+    for (int s = 0; s < kHSlots; ++s) {
+      const int idx = tid + s * nt;
+      dz a = dz_zero();
+      if (idx < T) {
+        int i, jj;
+        tri_index(idx, i, jj);
+        for (int l = i; l < m; ++l) a = dz_add(a, dz_mul(Mz[i * ld + l], dz_conj(Mz[jj * ld + l])));
+      }
+      h[s] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < kHSlots; ++s) {
+      const int idx = tid + s * nt;
+      if (idx < T) {
+        int i, jj;
+        tri_index(idx, i, jj);
+        Mz[i * ld + jj] = h[s];
+      }
     }
     __syncthreads();
   }
-  // R in double-float, in place (a dz occupies the 16 bytes of its double2)
-  dz* Mz = reinterpret_cast<dz*>(M);
-  for (int i = threadIdx.x; i < m * ld; i += blockDim.x) Mz[i] = dz_from(M[i]);
-  __syncthreads();
-  // H = R R^dag (upper triangle computed, mirrored) -> global, then back into M
-  dz* Hz = reinterpret_cast<dz*>(Hb);
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    const int i = idx / m, jj = idx % m;
-    if (jj < i) continue;
-    dz acc = dz_zero();
-    for (int l = jj; l < m; ++l) acc = dz_add(acc, dz_mul(Mz[i * ld + l], dz_conj(Mz[jj * ld + l])));
-    Hz[i * m + jj] = acc;
-    Hz[jj * m + i] = dz_conj(acc);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) Mz[(i / m) * ld + i % m] = Hz[i];
-  __syncthreads();
-  dz* uvz = reinterpret_cast<dz*>(uv);
-  tridiagonalise(Mz, m, ld, d, e, tau, uvz, reinterpret_cast<dz*>(pv), red);
-  if (threadIdx.x == 0) {
-    delta[0] = make_double2(1.0, 0.0);
-    for (int j = 0; j + 1 < m; ++j) {
-      const double ae = sqrt(zabs2(e[j]));
-      fo[j] = ae;
-      f232[j] = (float)(ae * ae);
-      delta[j + 1] = ae > 0 ? zmul(delta[j], zscale(e[j], 1.0 / ae)) : delta[j];
+
+  // ---- 4. Householder tridiagonalisation on the lower triangle.  Step j
+  // (reflector 1 - t u u^dag on rows j+1..): warp 0 forms u and t from column
+  // j, which it holds in registers (u0 = x0 + x0 |x| / |x0|, beta = -x0 |x| /
+  // |x0|, t = 1 / (|x| (|x| + |x0|)), all in double-float); then p = t A u
+  // over the trailing block A (four lanes per row), w = p - (t/2)(u^dag p) u,
+  // and A -= u w^dag + w u^dag, warp 0 taking A's first column, which is the
+  // next step's column.  u stays in column j (rows j+1..) for step 6.  Three
+  // barriers per step.
+  {
+    dz cv0 = dz_zero(), cv1 = dz_zero();  // warp 0: rows j + lane, j + 32 + lane of column j
+    if (w == 0) {
+      if (lane < m) cv0 = Mz[lane * ld];
+      if (lane + 32 < m) cv1 = Mz[(lane + 32) * ld];
     }
-    for (int j = 0; j < m; ++j) d32[j] = (float)d[j];
+    for (int j = 0; j + 2 < m; ++j) {
+      const int n = m - j - 1, len = m - j;
+      dz* uv = uvb[j & 1];
+      if (w == 0) {
+        df tail = df{0.f, 0.f};
+        if (lane >= 2 && lane < len) tail = dz_abs2(cv0);
+        if (lane + 32 < len) tail = df_add(tail, dz_abs2(cv1));
+        tail = df_warp_sum(tail);
+        const dz x0 = dz_shfl(cv0, 1);
+        df t = df{0.f, 0.f};
+        dz beta = x0, u0 = x0;
+        if (tail.hi > 0.f) {
+          const df ax2 = dz_abs2(x0);
+          const df nx = df_sqrt(df_add(ax2, tail));
+          df ax = df{0.f, 0.f};
+          if (ax2.hi > 0.f) {
+            ax = df_sqrt(ax2);
+            beta = dz_scale(x0, df_neg(df_mul(nx, df_recip(ax))));
+            u0 = dz_sub(x0, beta);
+          } else {
+            beta = dz{df_neg(nx), df{0.f, 0.f}};
+            u0 = dz{nx, df{0.f, 0.f}};
+          }
+          t = df_recip(df_mul(nx, df_add(nx, ax)));
+        }
+        if (lane >= 1 && lane < len) uv[lane - 1] = lane == 1 ? u0 : cv0;
+        if (lane + 32 < len) uv[lane + 31] = cv1;
+        if (lane == 1) Mz[(j + 1) * ld + j] = u0;
+        if (lane == 0) {
+          taud[j] = t;
+          e[j] = dz_to(beta);
+        }
+      }
+      __syncthreads();
+      const df t = taud[j];
+      if (t.hi != 0.f) {
+        {
+          const int a = tid >> 2, part = tid & 3;
+          dz s = dz_zero();
+          if (a < n)
+            for (int b = part; b < n; b += 4) {
+              const int rr = a > b ? a : b, cc = a > b ? b : a;
+              dz v = Mz[(j + 1 + rr) * ld + j + 1 + cc];
+              if (b > a) v.im = df_neg(v.im);
+              s = dz_add(s, dz_mul(v, uv[b]));
+            }
+          s = dz_add(s, dz_shfl_xor(s, 1));
+          s = dz_add(s, dz_shfl_xor(s, 2));
+          const dz p = dz_scale(s, t);
+          df kc = df{0.f, 0.f};
+          if (a < n && part == 0) {
+            pvz[a] = p;
+            const dz ua = uv[a];
+            kc = df_add(df_mul(ua.re, p.re), df_mul(ua.im, p.im));
+          }
+          kc = df_warp_sum(kc);
+          if (lane == 0) kred[w] = kc;
+        }
+        __syncthreads();
+        if (tid < n) {
+          df K = kred[0];
+          for (int i = 1; i < nw; ++i) K = df_add(K, kred[i]);
+          K = df_half(df_mul(K, t));
+          wvz[tid] = dz_sub(pvz[tid], dz_scale(uv[tid], K));
+        }
+        __syncthreads();
+        if (w == 0) {
+          const dz u0 = uv[0], w0 = wvz[0];
+          dz nv[2];
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int a = lane + 32 * h2;
+            nv[h2] = dz_zero();
+            if (a < n) {
+              dz* pp = Mz + (j + 1 + a) * ld + j + 1;
+              const dz v = dz_sub(*pp, dz_add(dz_mul(uv[a], dz_conj(w0)), dz_mul(wvz[a], dz_conj(u0))));
+              *pp = v;
+              nv[h2] = v;
+            }
+          }
+          cv0 = nv[0];
+          cv1 = nv[1];
+        } else {
+          const int T1 = n * (n - 1) / 2;
+          for (int idx = tid - 32; idx < T1; idx += nt - 32) {
+            int a, b;
+            tri_index(idx, a, b);
+            ++a;
+            ++b;
+            dz* pp = Mz + (j + 1 + a) * ld + j + 1 + b;
+            *pp = dz_sub(*pp, dz_add(dz_mul(uv[a], dz_conj(wvz[b])), dz_mul(wvz[a], dz_conj(uv[b]))));
+          }
+        }
+      } else if (w == 0) {
+        cv0 = lane < n ? Mz[(j + 1 + lane) * ld + j + 1] : dz_zero();
+        cv1 = lane + 32 < n ? Mz[(j + 33 + lane) * ld + j + 1] : dz_zero();
+      }
+    }
   }
   __syncthreads();
-  double tnorm = 0;
-  for (int i = 0; i < m; ++i) {
-    const double r = fabs(d[i]) + (i > 0 ? fo[i - 1] : 0.0) + (i + 1 < m ? fo[i] : 0.0);
-    tnorm = fmax(tnorm, r);
+  for (int i = tid; i < m; i += nt) d[i] = df_to(Mz[i * ld + i].re);
+  if (tid == 0 && m >= 2) e[m - 2] = dz_to(Mz[(m - 1) * ld + m - 2]);
+  __syncthreads();
+
+  // ---- 5. T = Delta T_r Delta^dag with T_r real (off-diagonal |e_j|) and the
+  // phases delta_{j+1} = delta_j e_j / |e_j|; top-k eigenpairs of T_r
+  for (int j = tid; j + 1 < m; j += nt) {
+    const double ae = sqrt(zabs2(e[j]));
+    fo[j] = ae;
+    f232[j] = (float)(ae * ae);
+    delta[j + 1] = ae > 0 ? zscale(e[j], 1.0 / ae) : make_double2(1.0, 0.0);
   }
+  for (int j = tid; j < m; j += nt) d32[j] = (float)d[j];
+  __syncthreads();
+  if (tid == 0) {
+    delta[0] = make_double2(1.0, 0.0);
+    for (int j = 1; j < m; ++j) delta[j] = zmul(delta[j - 1], delta[j]);
+  } else if (w == 1) {
+    float tn = 0.f;
+    for (int i = lane; i < m; i += 32)
+      tn = fmaxf(tn, fabsf(d32[i]) + (i > 0 ? (float)fo[i - 1] : 0.f) +
+                         (i + 1 < m ? (float)fo[i] : 0.f));
+    for (int o = 16; o > 0; o >>= 1) tn = fmaxf(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    if (lane == 0) s_tn = tn;
+  }
+  __syncthreads();
+  // Gershgorin bound (widened past its FP32 rounding)
+  const float tn = s_tn * 1.00001f + 1e-30f;
+  const double tnorm = (double)tn;
   const double tiny = 1e-300 + 1e-15 * tnorm;
-  // multisection: kBisect points per eigenvalue (the ei-th largest); the
-  // k * kBisect (eigenvalue, point) pairs are spread over the block's threads
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    lo[i] = -tnorm;
-    hi[i] = tnorm;
+  if (tid < k) {
+    lo[tid] = -tnorm;
+    hi[tid] = tnorm;
   }
   __syncthreads();
   {
-    const float tiny32 = 1e-30f + 1e-20f * (float)tnorm;
+    // multisection: kBisect points per eigenvalue (the ei-th largest); the
+    // k * kBisect (eigenvalue, point) pairs are spread over the block's threads.
+    // The Sturm counts are FP32; the interval ends stay FP64, so that equal
+    // eigenvalues end in equal intervals within FP32 rounding of their value.
+    const float tiny32 = 1e-30f + 1e-20f * tn;
+    constexpr double kStep = 1.0 / (kBisect + 1);
     for (int it = 0; it < 9; ++it) {
-      for (int w = threadIdx.x; w < k * kBisect; w += blockDim.x) {
-        const int ei = w / kBisect, sp = w % kBisect;
+      for (int q = tid; q < k * kBisect; q += nt) {
+        const int ei = q / kBisect, sp = q % kBisect;
         const double l0 = lo[ei], h0 = hi[ei];
-        const double x = l0 + (h0 - l0) * (double)(sp + 1) / (double)(kBisect + 1);
+        const double x = l0 + (h0 - l0) * ((double)(sp + 1) * kStep);
         cnt[ei][sp] = sturm_count32(d32, f232, m, (float)x, tiny32);
       }
       __syncthreads();
-      for (int ei = threadIdx.x; ei < k; ei += blockDim.x) {
-        const int target = m - 1 - ei;  // index among ascending eigenvalues
-        const double l0 = lo[ei], h0 = hi[ei];
+      if (tid < k) {
+        const int target = m - 1 - tid;  // index among ascending eigenvalues
+        const double l0 = lo[tid], h0 = hi[tid];
         double nl = l0, nh = h0;
         for (int q = 0; q < kBisect; ++q) {
-          const double x = l0 + (h0 - l0) * (double)(q + 1) / (double)(kBisect + 1);
-          if (cnt[ei][q] > target) {
+          const double x = l0 + (h0 - l0) * ((double)(q + 1) * kStep);
+          if (cnt[tid][q] > target) {
             nh = x;
             break;
           }
           nl = x;
         }
-        lo[ei] = nl;
-        hi[ei] = nh;
+        lo[tid] = nl;
+        hi[tid] = nh;
       }
       __syncthreads();
     }
   }
-  if (threadIdx.x < k) lam[threadIdx.x] = 0.5 * (lo[threadIdx.x] + hi[threadIdx.x]);
+  if (tid < k) lam[tid] = 0.5 * (lo[tid] + hi[tid]);
   __syncthreads();
   // clusters (eigenvalues closer than 1e-6 |T|, above the FP32 resolution of
   // the multisection) are handled by their first member
-  if (threadIdx.x < k) {
-    const int i = threadIdx.x;
-    leader[i] = (i == 0 || fabs(lam[i - 1] - lam[i]) > 1e-6 * tnorm) ? 1 : 0;
-  }
+  if (tid < k) leader[tid] = (tid == 0 || fabs(lam[tid - 1] - lam[tid]) > 1e-6 * tnorm) ? 1 : 0;
   __syncthreads();
-  // inverse iteration; the real eigenvector z_i of T' goes to Uk column i (.x)
-  if (threadIdx.x < k && leader[threadIdx.x]) {
-    int i = threadIdx.x;
+  // inverse iteration; the real eigenvector z_i of T_r goes to Zt row i
+  if (tid < k && leader[tid]) {
+    int i = tid;
     do {
       double z[kMaxM];
       TriLU F;
       tri_factor(d, fo, m, lam[i], tiny, F);
-      for (int r = 0; r < m; ++r) z[r] = 1.0 + 0.01 * r + 0.001 * i;
+      // start vector: hashed entries in [0.5, 1.5), different for every
+      // member of a cluster, so that the members' starts span the cluster's
+      // eigenspace (starts differing by a multiple of one vector span two
+      // dimensions of it, and the orthogonalisation leaves only rounding)
+      for (int r = 0; r < m; ++r) {
+        uint32_t h = (uint32_t)r * 0x9E3779B1u + (uint32_t)(i + 1) * 0x85EBCA77u;
+        h ^= h >> 15;
+        h *= 0x2C1B3C6Du;
+        h ^= h >> 12;
+        z[r] = 0.5 + (double)(h & 0xFFFFu) * (1.0 / 65536.0);
+      }
       for (int it = 0; it < 3; ++it) {
         tri_solve(F, m, z);
-        for (int pj = threadIdx.x; pj < i; ++pj) {  // previous members of this cluster
+        for (int pj = tid; pj < i; ++pj) {  // previous members of this cluster
           double dot = 0;
-          for (int r = 0; r < m; ++r) dot += Uk[r * k + pj].x * z[r];
-          for (int r = 0; r < m; ++r) z[r] -= dot * Uk[r * k + pj].x;
+          for (int r = 0; r < m; ++r) dot += Zt[pj * m + r] * z[r];
+          for (int r = 0; r < m; ++r) z[r] -= dot * Zt[pj * m + r];
         }
         double nrm = 0;
         for (int r = 0; r < m; ++r) nrm += z[r] * z[r];
@@ -826,79 +950,100 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
       for (int r = 0; r < m; ++r) rq += d[r] * z[r] * z[r];
       for (int r = 0; r + 1 < m; ++r) rq += 2.0 * fo[r] * z[r] * z[r + 1];
       lam[i] = rq;
-      for (int r = 0; r < m; ++r) Uk[r * k + i] = make_double2(z[r], 0.0);
+      for (int r = 0; r < m; ++r) Zt[i * m + r] = z[r];
       ++i;
     } while (i < k && !leader[i]);
   }
   __syncthreads();
-  // back-transform (double-float): y = Q (delta .* z); reflector j copied to uv first
-  dz* Ukz = reinterpret_cast<dz*>(Uk);
-  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x)
-    Ukz[idx] = dz_from(zscale(delta[idx / k], Uk[idx].x));
-  __syncthreads();
-  {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (tid < k) sigma[(long)bc * k + tid] = sqrt(fmax(lam[tid], 0.0));
+
+  // ---- 6. back-transform y = Q (Delta z), Q = H_0 H_1 ... H_{m-3}: eight
+  // lanes per eigenvector, each keeping rows part + 8q in registers, so the
+  // reflectors need no block barrier
+  const int ci = tid >> 3, part = tid & 7;
+  const bool warp_live = 4 * w < k;  // the warp holds at least one eigenvector
+  dz y[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int r = part + 8 * q;
+    y[q] = (ci < k && r < m) ? dz_from(zscale(delta[r], Zt[ci * m + r])) : dz_zero();
+  }
+  if (warp_live)
     for (int j = m - 3; j >= 0; --j) {
-      if (tau[j] == 0.0) continue;
-      const int n = m - j - 1;
-      const df tj = df_from(tau[j]);
-      for (int a = threadIdx.x; a < n; a += blockDim.x) uvz[a] = Mz[(j + 1 + a) * ld + j];
-      __syncthreads();
-      for (int i = w; i < k; i += nw) {
-        dz sacc = dz_zero();
-        for (int a = lane; a < n; a += 32)
-          sacc = dz_add(sacc, dz_mulc(uvz[a], Ukz[(j + 1 + a) * k + i]));
-        sacc = dz_scale(dz_warp_sum(sacc), tj);
-        for (int a = lane; a < n; a += 32)
-          Ukz[(j + 1 + a) * k + i] = dz_sub(Ukz[(j + 1 + a) * k + i], dz_mul(sacc, uvz[a]));
+      const df tj = taud[j];
+      if (tj.hi == 0.f) continue;
+      dz s = dz_zero();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = part + 8 * q;
+        if (r > j && r < m) s = dz_add(s, dz_mulc(Mz[r * ld + j], y[q]));
       }
-      __syncthreads();
+      s = dz_add(s, dz_shfl_xor(s, 1));
+      s = dz_add(s, dz_shfl_xor(s, 2));
+      s = dz_add(s, dz_shfl_xor(s, 4));
+      s = dz_scale(s, tj);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = part + 8 * q;
+        if (r > j && r < m) y[q] = dz_sub(y[q], dz_mul(s, Mz[r * ld + j]));
+      }
     }
-  }
-  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) Uk[idx] = dz_to(Ukz[idx]);
+  __syncthreads();  // every warp is done with the reflectors
+
+  // ---- 7. W2 = R2^{-1} U~_k (FP32; R2 = 1 + F is close to 1): substitution
+  // from the bottom within each eigenvector's eight lanes
+  for (int i = tid; i < m * m; i += nt) E[(i / m) * ld + i % m] = Fg[i];
   __syncthreads();
-  if (threadIdx.x < k) sigma[(long)bc * k + threadIdx.x] = sqrt(fmax(lam[threadIdx.x], 0.0));
-  if (ctv) {
-    // Sigma_k V_k^dag = U~_k^dag R  (R from global)
-    float2* cb = ctv + (long)bc * k * m;
-    for (int idx = threadIdx.x; idx < k * m; idx += blockDim.x) {
-      const int i = idx / m, c = idx % m;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int l = 0; l <= c; ++l) acc = zadd(acc, zmulc(Uk[l * k + i], Rg[l * m + c]));
-      cb[idx] = make_float2((float)acc.x, (float)acc.y);
-    }
-    __syncthreads();
-  }
-  // W2 = R2^{-1} U~_k (an FP32 output; R2 is close to 1): FP32 substitution
-  // from the bottom, eight threads per column, R2 staged into M
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) M[(i / m) * ld + i % m] = Gb[i];
+  for (int i = tid; i < m; i += nt) rinv[i] = 1.f / (1.f + E[i * ld + i].x);
   __syncthreads();
-  {
-    const int c = threadIdx.x >> 3, part = threadIdx.x & 7;
-    for (int i = m - 1; i >= 0; --i) {
+  float2 yf[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) yf[q] = dz_to_f(y[q]);
+  if (warp_live)
+    for (int r = m - 1; r >= 0; --r) {
       float2 acc = make_float2(0.f, 0.f);
-      if (c < k)
-        for (int l = i + 1 + part; l < m; l += 8) {
-          const double2 r = M[i * ld + l], u = Uk[l * k + c];
-          cfma(acc, make_float2((float)r.x, (float)r.y), make_float2((float)u.x, (float)u.y));
-        }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int l = part + 8 * q;
+        if (l > r && l < m) cfma(acc, E[r * ld + l], yf[q]);
+      }
 #pragma unroll
       for (int o = 1; o < 8; o <<= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
       }
-      if (c < k && part == 0) {
-        const float inv = (float)(1.0 / M[i * ld + i].x);
-        const double2 u = Uk[i * k + c];
-        Uk[i * k + c] = make_double2(((float)u.x - acc.x) * inv, ((float)u.y - acc.y) * inv);
+      if (part == (r & 7)) {
+        const float ri = rinv[r];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q == (r >> 3)) yf[q] = make_float2((yf[q].x - acc.x) * ri, (yf[q].y - acc.y) * ri);
       }
-      __syncthreads();
+    }
+  float2* Wb = W2 + (long)bc * m * k;
+  if (ci < k)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = part + 8 * q;
+      if (r < m) Wb[r * k + ci] = yf[q];
+    }
+  if (ctv) {
+    // Sigma_k V_k^dag = U~_k^dag R  (R from global, FP64)
+    if (ci < k)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = part + 8 * q;
+        if (r < m) Ut[r * k + ci] = dz_to(y[q]);
+      }
+    __syncthreads();
+    float2* cb = ctv + (long)bc * k * m;
+    for (int idx = tid; idx < k * m; idx += nt) {
+      const int i = idx / m, c = idx % m;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int l = 0; l <= c; ++l) acc = zadd(acc, zmulc(Ut[l * k + i], Rg[l * m + c]));
+      cb[idx] = make_float2((float)acc.x, (float)acc.y);
     }
   }
-  float2* Wb = W2 + (long)bc * m * k;
-  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x)
-    Wb[idx] = make_float2((float)Uk[idx].x, (float)Uk[idx].y);
-  if (threadIdx.x == 0) flags[bc] |= flag;
+  if (tid == 0 && s_fail) flags[bc] |= 4;
 }
 
 // U_k rows = (A Z1) W2 for every row of the block, written in the block-major
@@ -967,7 +1112,8 @@ cudaError_t launch_truncate(const Geom& g, const float2* psi, float2* Uk, double
   const int m = g.m, k = g.k;
   const size_t sm_gram0 = sizeof(float2) * (size_t)(2 * kChunkRows * m);
   const size_t sm_gram1 = sm_gram0 + sizeof(float2) * (size_t)m * m;
-  const size_t sm_chol = sizeof(double2) * (size_t)m * (m + 1) + sizeof(float2) * (size_t)m * m;
+  const size_t sm_chol = std::max(sizeof(double2) * (size_t)m * (m + 1),
+                                  sizeof(float2) * ((size_t)m * (m + 1) + (size_t)m * (m + 4)));
   const size_t sm_svd = sizeof(double2) * ((size_t)m * (m + 1) + (size_t)m * k);
   const size_t sm_uk = sm_gram1 + sizeof(float2) * ((size_t)m * k + (size_t)kChunkRows * k);
   static PerDeviceOnce attr_once;
