@@ -285,24 +285,11 @@ __device__ __forceinline__ float2 dz_to_f(dz a) {
   return make_float2(__fadd_rn(a.re.hi, a.re.lo), __fadd_rn(a.im.hi, a.im.lo));
 }
 __device__ __forceinline__ dz dz_zero() { return dz{df{0.f, 0.f}, df{0.f, 0.f}}; }
-__device__ __forceinline__ dz dz_add(dz a, dz b) { return dz{df_add(a.re, b.re), df_add(a.im, b.im)}; }
 __device__ __forceinline__ dz dz_sub(dz a, dz b) { return dz{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
-__device__ __forceinline__ dz dz_mul(dz a, dz b) {  // a b
-  return dz{df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)),
-            df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
-}
-__device__ __forceinline__ dz dz_mulc(dz a, dz b) {  // conj(a) b
-  return dz{df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)),
-            df_sub(df_mul(a.re, b.im), df_mul(a.im, b.re))};
-}
-__device__ __forceinline__ dz dz_conj(dz a) { return dz{a.re, df_neg(a.im)}; }
 __device__ __forceinline__ dz dz_scale(dz a, df s) { return dz{df_mul(a.re, s), df_mul(a.im, s)}; }
 __device__ __forceinline__ df dz_abs2(dz a) { return df_add(df_mul(a.re, a.re), df_mul(a.im, a.im)); }
 __device__ __forceinline__ df df_shfl_xor(df a, int o) {
   return df{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-}
-__device__ __forceinline__ dz dz_shfl_xor(dz a, int o) {
-  return dz{df_shfl_xor(a.re, o), df_shfl_xor(a.im, o)};
 }
 __device__ __forceinline__ dz dz_shfl(dz a, int src) {
   return dz{df{__shfl_sync(0xffffffffu, a.re.hi, src), __shfl_sync(0xffffffffu, a.re.lo, src)},
@@ -311,6 +298,75 @@ __device__ __forceinline__ dz dz_shfl(dz a, int src) {
 __device__ __forceinline__ df df_warp_sum(df a) {
   for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_xor(a, o));
   return a;
+}
+
+// Accumulator for sums of double-float products in the manner of Ogita, Rump
+// and Oishi's Dot2 ("Accurate sum and dot product", SIAM J. Sci. Comput. 26,
+// 2005): the running FP32 sum s, with the rounding error of every addition
+// (TwoSum) and of every product (FMA form of TwoProduct, plus the cross terms
+// of the low parts) collected in the FP32 term e.  s + e carries double-float
+// accuracy (the dropped lo * lo terms are 2^-48 of a product) for about half
+// the operations of double-float products and sums.
+struct dacc {
+  float s, e;
+};
+struct zacc {
+  dacc re, im;
+};
+__device__ __forceinline__ dacc acc_from(df a) { return dacc{a.hi, a.lo}; }
+// a += x y
+__device__ __forceinline__ void acc_prod(dacc& a, df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float q = __fmaf_rn(x.hi, y.hi, -p);
+  q = __fmaf_rn(x.hi, y.lo, q);
+  q = __fmaf_rn(x.lo, y.hi, q);
+  const float s = __fadd_rn(a.s, p);
+  const float bb = __fsub_rn(s, a.s);
+  const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  a.s = s;
+  a.e = __fadd_rn(a.e, __fadd_rn(t, q));
+}
+__device__ __forceinline__ dacc acc_merge(dacc a, dacc b) {
+  const df t = two_sum(a.s, b.s);
+  return dacc{t.hi, __fadd_rn(__fadd_rn(a.e, b.e), t.lo)};
+}
+__device__ __forceinline__ df acc_get(dacc a) { return two_sum(a.s, a.e); }
+__device__ __forceinline__ dz zacc_get(zacc a) { return dz{acc_get(a.re), acc_get(a.im)}; }
+__device__ __forceinline__ zacc zacc_from(dz a) { return zacc{acc_from(a.re), acc_from(a.im)}; }
+__device__ __forceinline__ zacc zacc_zero() { return zacc{dacc{0.f, 0.f}, dacc{0.f, 0.f}}; }
+// a += x y
+__device__ __forceinline__ void zacc_mul(zacc& a, dz x, dz y) {
+  acc_prod(a.re, x.re, y.re);
+  acc_prod(a.re, df_neg(x.im), y.im);
+  acc_prod(a.im, x.re, y.im);
+  acc_prod(a.im, x.im, y.re);
+}
+// a += conj(x) y
+__device__ __forceinline__ void zacc_mulc(zacc& a, dz x, dz y) {
+  acc_prod(a.re, x.re, y.re);
+  acc_prod(a.re, x.im, y.im);
+  acc_prod(a.im, x.re, y.im);
+  acc_prod(a.im, df_neg(x.im), y.re);
+}
+// a += x conj(y)
+__device__ __forceinline__ void zacc_mul_conj(zacc& a, dz x, dz y) {
+  acc_prod(a.re, x.re, y.re);
+  acc_prod(a.re, x.im, y.im);
+  acc_prod(a.im, x.im, y.re);
+  acc_prod(a.im, df_neg(x.re), y.im);
+}
+// a -= x conj(y)
+__device__ __forceinline__ void zacc_sub_mul_conj(zacc& a, dz x, dz y) {
+  acc_prod(a.re, df_neg(x.re), y.re);
+  acc_prod(a.re, df_neg(x.im), y.im);
+  acc_prod(a.im, df_neg(x.im), y.re);
+  acc_prod(a.im, x.re, y.im);
+}
+__device__ __forceinline__ dacc acc_shfl_xor(dacc a, int o) {
+  return dacc{__shfl_xor_sync(0xffffffffu, a.s, o), __shfl_xor_sync(0xffffffffu, a.e, o)};
+}
+__device__ __forceinline__ zacc zacc_merge_xor(zacc a, int o) {
+  return zacc{acc_merge(a.re, acc_shfl_xor(a.re, o)), acc_merge(a.im, acc_shfl_xor(a.im, o))};
 }
 
 // (r, c) of entry idx of a lower triangle stored row by row (idx = r (r+1)/2 + c,
@@ -388,8 +444,11 @@ __global__ void __launch_bounds__(kThreads, 2) chol_stage1(const double2* __rest
         int a, b;
         tri_index(idx, a, b);
         const int r = j + 1 + b, c = j + 1 + a;  // r <= c
+        // g_rc -= conj(g_jr) (g_jc / d_j)
         const dz x = Gz[j * ld + r], y = dz_scale(Gz[j * ld + c], inv);
-        Gz[r * ld + c] = dz_sub(Gz[r * ld + c], dz_mulc(x, y));
+        zacc acc = zacc_from(Gz[r * ld + c]);
+        zacc_sub_mul_conj(acc, y, x);
+        Gz[r * ld + c] = zacc_get(acc);
       }
       __syncthreads();
     }
@@ -706,13 +765,13 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
 #pragma unroll
     for (int s = 0; s < kHSlots; ++s) {
       const int idx = tid + s * nt;
-      dz a = dz_zero();
+      zacc a = zacc_zero();
       if (idx < T) {
         int i, jj;
         tri_index(idx, i, jj);
-        for (int l = i; l < m; ++l) a = dz_add(a, dz_mul(Mz[i * ld + l], dz_conj(Mz[jj * ld + l])));
+        for (int l = i; l < m; ++l) zacc_mul_conj(a, Mz[i * ld + l], Mz[jj * ld + l]);
       }
-      h[s] = a;
+      h[s] = zacc_get(a);
     }
     __syncthreads();
 #pragma unroll
@@ -779,25 +838,26 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
       if (t.hi != 0.f) {
         {
           const int a = tid >> 2, part = tid & 3;
-          dz s = dz_zero();
+          zacc sa = zacc_zero();
           if (a < n)
             for (int b = part; b < n; b += 4) {
               const int rr = a > b ? a : b, cc = a > b ? b : a;
               dz v = Mz[(j + 1 + rr) * ld + j + 1 + cc];
               if (b > a) v.im = df_neg(v.im);
-              s = dz_add(s, dz_mul(v, uv[b]));
+              zacc_mul(sa, v, uv[b]);
             }
-          s = dz_add(s, dz_shfl_xor(s, 1));
-          s = dz_add(s, dz_shfl_xor(s, 2));
-          const dz p = dz_scale(s, t);
-          df kc = df{0.f, 0.f};
+          sa = zacc_merge_xor(sa, 1);
+          sa = zacc_merge_xor(sa, 2);
+          const dz p = dz_scale(zacc_get(sa), t);
+          dacc kc = dacc{0.f, 0.f};
           if (a < n && part == 0) {
             pvz[a] = p;
             const dz ua = uv[a];
-            kc = df_add(df_mul(ua.re, p.re), df_mul(ua.im, p.im));
+            acc_prod(kc, ua.re, p.re);
+            acc_prod(kc, ua.im, p.im);
           }
-          kc = df_warp_sum(kc);
-          if (lane == 0) kred[w] = kc;
+          for (int o = 16; o > 0; o >>= 1) kc = acc_merge(kc, acc_shfl_xor(kc, o));
+          if (lane == 0) kred[w] = acc_get(kc);
         }
         __syncthreads();
         if (tid < n) {
@@ -816,7 +876,10 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
             nv[h2] = dz_zero();
             if (a < n) {
               dz* pp = Mz + (j + 1 + a) * ld + j + 1;
-              const dz v = dz_sub(*pp, dz_add(dz_mul(uv[a], dz_conj(w0)), dz_mul(wvz[a], dz_conj(u0))));
+              zacc acc = zacc_from(*pp);
+              zacc_sub_mul_conj(acc, uv[a], w0);
+              zacc_sub_mul_conj(acc, wvz[a], u0);
+              const dz v = zacc_get(acc);
               *pp = v;
               nv[h2] = v;
             }
@@ -831,7 +894,10 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
             ++a;
             ++b;
             dz* pp = Mz + (j + 1 + a) * ld + j + 1 + b;
-            *pp = dz_sub(*pp, dz_add(dz_mul(uv[a], dz_conj(wvz[b])), dz_mul(wvz[a], dz_conj(uv[b]))));
+            zacc acc = zacc_from(*pp);
+            zacc_sub_mul_conj(acc, uv[a], wvz[b]);
+            zacc_sub_mul_conj(acc, wvz[a], uv[b]);
+            *pp = zacc_get(acc);
           }
         }
       } else if (w == 0) {
@@ -972,21 +1038,29 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
     for (int j = m - 3; j >= 0; --j) {
       const df tj = taud[j];
       if (tj.hi == 0.f) continue;
-      dz s = dz_zero();
+      // slots whose eight rows all lie at or above row j are skipped (a
+      // warp-uniform test)
+      zacc sa = zacc_zero();
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int r = part + 8 * q;
-        if (r > j && r < m) s = dz_add(s, dz_mulc(Mz[r * ld + j], y[q]));
-      }
-      s = dz_add(s, dz_shfl_xor(s, 1));
-      s = dz_add(s, dz_shfl_xor(s, 2));
-      s = dz_add(s, dz_shfl_xor(s, 4));
-      s = dz_scale(s, tj);
+      for (int q = 0; q < 8; ++q)
+        if (8 * q + 7 > j) {
+          const int r = part + 8 * q;
+          if (r > j && r < m) zacc_mulc(sa, Mz[r * ld + j], y[q]);
+        }
+      sa = zacc_merge_xor(sa, 1);
+      sa = zacc_merge_xor(sa, 2);
+      sa = zacc_merge_xor(sa, 4);
+      const dz s = dz_scale(zacc_get(sa), df_neg(tj));
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int r = part + 8 * q;
-        if (r > j && r < m) y[q] = dz_sub(y[q], dz_mul(s, Mz[r * ld + j]));
-      }
+      for (int q = 0; q < 8; ++q)
+        if (8 * q + 7 > j) {
+          const int r = part + 8 * q;
+          if (r > j && r < m) {
+            zacc acc = zacc_from(y[q]);
+            zacc_mul(acc, s, Mz[r * ld + j]);
+            y[q] = zacc_get(acc);
+          }
+        }
     }
   __syncthreads();  // every warp is done with the reflectors
 
