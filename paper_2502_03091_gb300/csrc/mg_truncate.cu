@@ -288,16 +288,9 @@ __device__ __forceinline__ dz dz_zero() { return dz{df{0.f, 0.f}, df{0.f, 0.f}};
 __device__ __forceinline__ dz dz_sub(dz a, dz b) { return dz{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
 __device__ __forceinline__ dz dz_scale(dz a, df s) { return dz{df_mul(a.re, s), df_mul(a.im, s)}; }
 __device__ __forceinline__ df dz_abs2(dz a) { return df_add(df_mul(a.re, a.re), df_mul(a.im, a.im)); }
-__device__ __forceinline__ df df_shfl_xor(df a, int o) {
-  return df{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-}
 __device__ __forceinline__ dz dz_shfl(dz a, int src) {
   return dz{df{__shfl_sync(0xffffffffu, a.re.hi, src), __shfl_sync(0xffffffffu, a.re.lo, src)},
             df{__shfl_sync(0xffffffffu, a.im.hi, src), __shfl_sync(0xffffffffu, a.im.lo, src)}};
-}
-__device__ __forceinline__ df df_warp_sum(df a) {
-  for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_xor(a, o));
-  return a;
 }
 
 // Accumulator for sums of double-float products in the manner of Ogita, Rump
@@ -534,62 +527,77 @@ __device__ int sturm_count32(const float* d, const float* f2, int n, float x, fl
 }
 
 // LU factorisation with partial pivoting of the tridiagonal T - lam (diagonal
-// d, off-diagonal f): U has diagonals a (stored as reciprocals), c, c2; L has
-// multipliers l and the row swaps in the bit mask piv
+// d, off-diagonal f), in double-float: U has diagonals a (stored as
+// reciprocals), c, c2; L has multipliers l and the row swaps in the bit mask
+// piv.  The recurrences carry the running entries in registers, so the loads
+// and stores of the factor arrays stay off the dependency chain.
 struct TriLU {
-  double a[kMaxM], c[kMaxM], c2[kMaxM], l[kMaxM];
+  df a[kMaxM], c[kMaxM], c2[kMaxM], l[kMaxM];
   unsigned long long piv;
 };
 
-__device__ void tri_factor(const double* d, const double* f, int n, double lam, double tiny,
-                           TriLU& F) {
-  F.piv = 0ull;
-  for (int i = 0; i < n; ++i) {
-    F.a[i] = d[i] - lam;
-    F.c[i] = i + 1 < n ? f[i] : 0.0;
-    F.c2[i] = 0.0;
-  }
+__device__ void tri_factor(const df* d, const df* f, int n, df lam, float tiny, TriLU& F) {
+  const df zero = df{0.f, 0.f};
+  unsigned long long piv = 0ull;
+  df ai = df_sub(d[0], lam);         // current diagonal entry a_i
+  df ci = n > 1 ? f[0] : zero;       // current super-diagonal entry c_i
   for (int i = 0; i + 1 < n; ++i) {
-    const double bsub = f[i];
-    if (fabs(F.a[i]) >= fabs(bsub)) {
-      if (F.a[i] == 0.0) F.a[i] = tiny;
-      F.l[i] = bsub / F.a[i];
-      F.a[i + 1] -= F.l[i] * F.c[i];
-    } else {
-      F.piv |= 1ull << i;
-      F.l[i] = F.a[i] / bsub;
+    const df bsub = f[i];
+    const df dn = df_sub(d[i + 1], lam);  // a_{i+1} before step i
+    const df cn = i + 2 < n ? f[i + 1] : zero;
+    df l, an, cnext;
+    if (fabsf(ai.hi) >= fabsf(bsub.hi)) {
+      if (ai.hi == 0.f) ai = df{tiny, 0.f};
+      l = df_mul(bsub, df_recip(ai));
+      F.a[i] = ai;
+      F.c[i] = ci;
+      F.c2[i] = zero;
+      an = df_sub(dn, df_mul(l, ci));
+      cnext = cn;
+    } else {  // rows i and i+1 swap
+      piv |= 1ull << i;
+      l = df_mul(ai, df_recip(bsub));
       F.a[i] = bsub;
-      const double tmp = F.a[i + 1];
-      F.a[i + 1] = F.c[i] - F.l[i] * tmp;
-      if (i + 2 < n) {
-        F.c2[i] = F.c[i + 1];
-        F.c[i + 1] = -F.l[i] * F.c2[i];
-      }
-      F.c[i] = tmp;
+      F.c[i] = dn;
+      F.c2[i] = cn;
+      an = df_sub(ci, df_mul(l, dn));
+      cnext = df_neg(df_mul(l, cn));
     }
+    F.l[i] = l;
+    ai = an;
+    ci = cnext;
   }
+  F.a[n - 1] = ai;
+  F.c[n - 1] = zero;
+  F.c2[n - 1] = zero;
+  F.piv = piv;
   for (int i = 0; i < n; ++i) {
-    if (fabs(F.a[i]) < tiny) F.a[i] = F.a[i] < 0 ? -tiny : tiny;
-    F.a[i] = 1.0 / F.a[i];
+    df v = F.a[i];
+    if (fabsf(v.hi) < tiny) v = df{v.hi < 0.f ? -tiny : tiny, 0.f};
+    F.a[i] = df_recip(v);
   }
 }
 
 // one step of inverse iteration: z <- (T - lam)^{-1} z with the factors F
-__device__ void tri_solve(const TriLU& F, int n, double* z) {
+__device__ void tri_solve(const TriLU& F, int n, df* z) {
+  df zi = z[0];
   for (int i = 0; i + 1 < n; ++i) {
+    const df zn = z[i + 1], l = F.l[i];
     if ((F.piv >> i) & 1ull) {
-      const double t = z[i];
-      z[i] = z[i + 1];
-      z[i + 1] = t - F.l[i] * z[i + 1];
+      z[i] = zn;
+      zi = df_sub(zi, df_mul(l, zn));
     } else {
-      z[i + 1] -= F.l[i] * z[i];
+      z[i] = zi;
+      zi = df_sub(zn, df_mul(l, zi));
     }
   }
+  z[n - 1] = zi;
+  df z1 = df{0.f, 0.f}, z2 = df{0.f, 0.f};  // z_{i+1}, z_{i+2}
   for (int i = n - 1; i >= 0; --i) {
-    double sacc = z[i];
-    if (i + 1 < n) sacc -= F.c[i] * z[i + 1];
-    if (i + 2 < n) sacc -= F.c2[i] * z[i + 2];
-    z[i] = sacc * F.a[i];
+    const df v = df_mul(df_sub(df_sub(z[i], df_mul(F.c[i], z1)), df_mul(F.c2[i], z2)), F.a[i]);
+    z[i] = v;
+    z2 = z1;
+    z1 = v;
   }
 }
 
@@ -621,11 +629,12 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
   float2* E = reinterpret_cast<float2*>(dsm);            // [m][ld] F = R2 - 1 (steps 1-2, 7)
   float2* R1f = E + m * ld;                              // [m][m] R1 in FP32 (step 2)
   dz* Mz = reinterpret_cast<dz*>(dsm);                   // [m][ld] R, H, reflectors (2-6)
-  double* Zt = reinterpret_cast<double*>(dsm + m * ld);  // [k][m] eigenvectors of T_r
+  df* Zt = reinterpret_cast<df*>(dsm + m * ld);          // [k][m] eigenvectors of T_r
   double2* Ut = dsm + m * ld;                            // [m][k] U~_k for the test vectors
-  __shared__ dz uvb[2][kMaxM], pvz[kMaxM], wvz[kMaxM];
+  __shared__ dz uvb[2][kMaxM], pvz[kMaxM], wvw[kThreads / 32][kMaxM];
   __shared__ df taud[kMaxM], kred[nw];
   __shared__ double d[kMaxM], fo[kMaxM], lam[kMaxK];
+  __shared__ df dd[kMaxM], fd[kMaxM];
   __shared__ double2 e[kMaxM], delta[kMaxM];
   __shared__ double lo[kMaxK], hi[kMaxK];
   __shared__ float d32[kMaxM], f232[kMaxM], rinv[kMaxM], redf[nw];
@@ -792,7 +801,7 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
   // |x0|, t = 1 / (|x| (|x| + |x0|)), all in double-float); then p = t A u
   // over the trailing block A (four lanes per row), w = p - (t/2)(u^dag p) u,
   // and A -= u w^dag + w u^dag, warp 0 taking A's first column, which is the
-  // next step's column.  u stays in column j (rows j+1..) for step 6.  Three
+  // next step's column.  u stays in column j (rows j+1..) for step 6.  Two
   // barriers per step.
   {
     dz cv0 = dz_zero(), cv1 = dz_zero();  // warp 0: rows j + lane, j + 32 + lane of column j
@@ -804,10 +813,17 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
       const int n = m - j - 1, len = m - j;
       dz* uv = uvb[j & 1];
       if (w == 0) {
-        df tail = df{0.f, 0.f};
-        if (lane >= 2 && lane < len) tail = dz_abs2(cv0);
-        if (lane + 32 < len) tail = df_add(tail, dz_abs2(cv1));
-        tail = df_warp_sum(tail);
+        dacc ta = dacc{0.f, 0.f};
+        if (lane >= 2 && lane < len) {
+          acc_prod(ta, cv0.re, cv0.re);
+          acc_prod(ta, cv0.im, cv0.im);
+        }
+        if (lane + 32 < len) {
+          acc_prod(ta, cv1.re, cv1.re);
+          acc_prod(ta, cv1.im, cv1.im);
+        }
+        for (int o = 16; o > 0; o >>= 1) ta = acc_merge(ta, acc_shfl_xor(ta, o));
+        const df tail = acc_get(ta);
         const dz x0 = dz_shfl(cv0, 1);
         df t = df{0.f, 0.f};
         dz beta = x0, u0 = x0;
@@ -860,13 +876,16 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
           if (lane == 0) kred[w] = acc_get(kc);
         }
         __syncthreads();
-        if (tid < n) {
-          df K = kred[0];
-          for (int i = 1; i < nw; ++i) K = df_add(K, kred[i]);
-          K = df_half(df_mul(K, t));
-          wvz[tid] = dz_sub(pvz[tid], dz_scale(uv[tid], K));
+        // w = p - K u, K = (t/2) u^dag p: every warp forms its own copy, so no
+        // block barrier separates it from the update
+        dz* wvz = wvw[w];
+        {
+          dacc ka = acc_from(kred[0]);
+          for (int i = 1; i < nw; ++i) ka = acc_merge(ka, acc_from(kred[i]));
+          const df K = df_half(df_mul(acc_get(ka), t));
+          for (int a = lane; a < n; a += 32) wvz[a] = dz_sub(pvz[a], dz_scale(uv[a], K));
+          __syncwarp();
         }
-        __syncthreads();
         if (w == 0) {
           const dz u0 = uv[0], w0 = wvz[0];
           dz nv[2];
@@ -907,7 +926,10 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
     }
   }
   __syncthreads();
-  for (int i = tid; i < m; i += nt) d[i] = df_to(Mz[i * ld + i].re);
+  for (int i = tid; i < m; i += nt) {
+    dd[i] = Mz[i * ld + i].re;
+    d[i] = df_to(dd[i]);
+  }
   if (tid == 0 && m >= 2) e[m - 2] = dz_to(Mz[(m - 1) * ld + m - 2]);
   __syncthreads();
 
@@ -916,6 +938,7 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
   for (int j = tid; j + 1 < m; j += nt) {
     const double ae = sqrt(zabs2(e[j]));
     fo[j] = ae;
+    fd[j] = df_from(ae);
     f232[j] = (float)(ae * ae);
     delta[j + 1] = ae > 0 ? zscale(e[j], 1.0 / ae) : make_double2(1.0, 0.0);
   }
@@ -936,7 +959,7 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
   // Gershgorin bound (widened past its FP32 rounding)
   const float tn = s_tn * 1.00001f + 1e-30f;
   const double tnorm = (double)tn;
-  const double tiny = 1e-300 + 1e-15 * tnorm;
+  const float tiny = 1e-30f + 1e-15f * tn;
   if (tid < k) {
     lo[tid] = -tnorm;
     hi[tid] = tnorm;
@@ -981,13 +1004,15 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
   // the multisection) are handled by their first member
   if (tid < k) leader[tid] = (tid == 0 || fabs(lam[tid - 1] - lam[tid]) > 1e-6 * tnorm) ? 1 : 0;
   __syncthreads();
-  // inverse iteration; the real eigenvector z_i of T_r goes to Zt row i
+  // inverse iteration in double-float (one lane per eigenvalue, all in warp 0:
+  // the recurrences are serial, and on the FP32 pipe they issue at 64 times
+  // the FP64 rate); the real eigenvector z_i of T_r goes to Zt row i
   if (tid < k && leader[tid]) {
     int i = tid;
     do {
-      double z[kMaxM];
+      df z[kMaxM];
       TriLU F;
-      tri_factor(d, fo, m, lam[i], tiny, F);
+      tri_factor(dd, fd, m, df_from(lam[i]), tiny, F);
       // start vector: hashed entries in [0.5, 1.5), different for every
       // member of a cluster, so that the members' starts span the cluster's
       // eigenspace (starts differing by a multiple of one vector span two
@@ -997,25 +1022,30 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
         h ^= h >> 15;
         h *= 0x2C1B3C6Du;
         h ^= h >> 12;
-        z[r] = 0.5 + (double)(h & 0xFFFFu) * (1.0 / 65536.0);
+        z[r] = df{0.5f + (float)(h & 0xFFFFu) * (1.f / 65536.f), 0.f};
       }
       for (int it = 0; it < 3; ++it) {
         tri_solve(F, m, z);
         for (int pj = tid; pj < i; ++pj) {  // previous members of this cluster
-          double dot = 0;
-          for (int r = 0; r < m; ++r) dot += Zt[pj * m + r] * z[r];
-          for (int r = 0; r < m; ++r) z[r] -= dot * Zt[pj * m + r];
+          dacc dot = dacc{0.f, 0.f};
+          for (int r = 0; r < m; ++r) acc_prod(dot, Zt[pj * m + r], z[r]);
+          const df nd = df_neg(acc_get(dot));
+          for (int r = 0; r < m; ++r) {
+            dacc v = acc_from(z[r]);
+            acc_prod(v, nd, Zt[pj * m + r]);
+            z[r] = acc_get(v);
+          }
         }
-        double nrm = 0;
-        for (int r = 0; r < m; ++r) nrm += z[r] * z[r];
-        nrm = 1.0 / sqrt(nrm);
-        for (int r = 0; r < m; ++r) z[r] *= nrm;
+        dacc nrm = dacc{0.f, 0.f};
+        for (int r = 0; r < m; ++r) acc_prod(nrm, z[r], z[r]);
+        const df rs = df_recip(df_sqrt(acc_get(nrm)));
+        for (int r = 0; r < m; ++r) z[r] = df_mul(z[r], rs);
       }
-      // FP64 Rayleigh quotient z^T T z refines the FP32 multisection value
-      double rq = 0;
-      for (int r = 0; r < m; ++r) rq += d[r] * z[r] * z[r];
-      for (int r = 0; r + 1 < m; ++r) rq += 2.0 * fo[r] * z[r] * z[r + 1];
-      lam[i] = rq;
+      // Rayleigh quotient z^T T z (double-float) refines the FP32 multisection value
+      dacc rq = dacc{0.f, 0.f};
+      for (int r = 0; r < m; ++r) acc_prod(rq, dd[r], df_mul(z[r], z[r]));
+      for (int r = 0; r + 1 < m; ++r) acc_prod(rq, df{2.f * fd[r].hi, 2.f * fd[r].lo}, df_mul(z[r], z[r + 1]));
+      lam[i] = df_to(acc_get(rq));
       for (int r = 0; r < m; ++r) Zt[i * m + r] = z[r];
       ++i;
     } while (i < k && !leader[i]);
@@ -1032,7 +1062,7 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int r = part + 8 * q;
-    y[q] = (ci < k && r < m) ? dz_from(zscale(delta[r], Zt[ci * m + r])) : dz_zero();
+    y[q] = (ci < k && r < m) ? dz_scale(dz_from(delta[r]), Zt[ci * m + r]) : dz_zero();
   }
   if (warp_live)
     for (int j = m - 3; j >= 0; --j) {
