@@ -114,8 +114,8 @@ def kernel_work(w, prec="fp32"):
         "trunc_gram_q1": ("fp32", nbc * (8 * K * m * m + 4 * K * m * m), "flop"),
         "trunc_form_uk": ("fp32", nbc * (4 * K * m * m + 8 * K * m * k), "flop"),
         # one CTA per m' x m' problem, a serial chain of factorisation steps
-        # (FP64 Cholesky; the eigen stage mostly in double-float on the FP32
-        # pipe): latency-bound, reported with its achieved rate and no peak
+        # (double-float on the FP32 pipe): latency-bound, reported with its
+        # achieved rate and no peak
         "trunc_chol64": ("latency", nbc * (8 * m ** 3 / 3 + 8 * m ** 3 / 3), "flop"),
         "trunc_chol_eig64": ("latency", nbc * (8 * m ** 3 / 3 + 8 * m ** 3 / 3 + 8 * m ** 3 / 3
                                                + 16 * m ** 3 / 3 + 8 * m * m * k), "flop"),
@@ -304,18 +304,18 @@ def run_reference(args, w):
 
 
 PRECISION_NOTE = {
-    "fp32": "FP32 plain: complex64 storage and FP32 arithmetic on the CUDA cores; FP64 "
-            "Cholesky and small eigenproblem",
+    "fp32": "FP32 plain: complex64 storage and FP32 arithmetic on the CUDA cores; Cholesky "
+            "and small eigenproblem in double-float (pairs of FP32)",
     "mixed": "mixed: smoother as FP32 plain; truncation Grams, Q1 = A R1^-1, U_k and the "
              "Galerkin contractions on tcgen05 tensor cores with FP32 accumulation (first Gram "
-             "BF16, the rest FP16 hi/lo split, 3 products); FP64 Cholesky and small eigenproblem",
+             "BF16, the rest FP16 hi/lo split, 3 products); Cholesky and small eigenproblem in double-float",
     "mixed_fp16": "mixed with FP16 storage of the smoother fields (FP32 arithmetic); truncation "
                   "and coarsening as mixed",
 }
-DTYPE = {"fp32": "f32",
-         "mixed": "f32 smoother; fp16x3+bf16 tensor-core contractions (f32 accum); f64 eig",
+DTYPE = {"fp32": "f32; double-float (2xf32) eig",
+         "mixed": "f32 smoother; fp16x3+bf16 tensor-core contractions (f32 accum); double-float (2xf32) eig",
          "mixed_fp16": "f16-stored smoother (f32 math); fp16x3+bf16 tensor-core contractions; "
-                       "f64 eig"}
+                       "double-float (2xf32) eig"}
 PREC_ID = {"fp32": 0, "mixed": 1, "mixed_fp16": 2}
 
 
