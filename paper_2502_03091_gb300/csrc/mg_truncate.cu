@@ -536,41 +536,39 @@ struct TriLU {
   unsigned long long piv;
 };
 
+__device__ __forceinline__ df df_sel(bool c, df a, df b) { return df{c ? a.hi : b.hi, c ? a.lo : b.lo}; }
+
+// The pivot choice is a select, not a branch: the lanes of the warp (one per
+// eigenvalue) stay converged.
 __device__ void tri_factor(const df* d, const df* f, int n, df lam, float tiny, TriLU& F) {
   const df zero = df{0.f, 0.f};
   unsigned long long piv = 0ull;
   df ai = df_sub(d[0], lam);         // current diagonal entry a_i
   df ci = n > 1 ? f[0] : zero;       // current super-diagonal entry c_i
+#pragma unroll 2
   for (int i = 0; i + 1 < n; ++i) {
     const df bsub = f[i];
     const df dn = df_sub(d[i + 1], lam);  // a_{i+1} before step i
     const df cn = i + 2 < n ? f[i + 1] : zero;
-    df l, an, cnext;
-    if (fabsf(ai.hi) >= fabsf(bsub.hi)) {
-      if (ai.hi == 0.f) ai = df{tiny, 0.f};
-      l = df_mul(bsub, df_recip(ai));
-      F.a[i] = ai;
-      F.c[i] = ci;
-      F.c2[i] = zero;
-      an = df_sub(dn, df_mul(l, ci));
-      cnext = cn;
-    } else {  // rows i and i+1 swap
-      piv |= 1ull << i;
-      l = df_mul(ai, df_recip(bsub));
-      F.a[i] = bsub;
-      F.c[i] = dn;
-      F.c2[i] = cn;
-      an = df_sub(ci, df_mul(l, dn));
-      cnext = df_neg(df_mul(l, cn));
-    }
+    const bool sw = fabsf(ai.hi) < fabsf(bsub.hi);  // rows i and i+1 swap
+    if (!sw && ai.hi == 0.f) ai = df{tiny, 0.f};
+    const df num = df_sel(sw, ai, bsub), den = df_sel(sw, bsub, ai);
+    const df l = df_mul(num, df_recip(den));
+    piv |= (unsigned long long)sw << i;
+    F.a[i] = den;
+    F.c[i] = df_sel(sw, dn, ci);
+    F.c2[i] = df_sel(sw, cn, zero);
     F.l[i] = l;
+    const df an = df_sub(df_sel(sw, ci, dn), df_mul(l, df_sel(sw, dn, ci)));
+    const df lc = df_mul(l, cn);
+    ci = df_sel(sw, df_neg(lc), cn);
     ai = an;
-    ci = cnext;
   }
   F.a[n - 1] = ai;
   F.c[n - 1] = zero;
   F.c2[n - 1] = zero;
   F.piv = piv;
+#pragma unroll 4
   for (int i = 0; i < n; ++i) {
     df v = F.a[i];
     if (fabsf(v.hi) < tiny) v = df{v.hi < 0.f ? -tiny : tiny, 0.f};
@@ -581,18 +579,17 @@ __device__ void tri_factor(const df* d, const df* f, int n, df lam, float tiny, 
 // one step of inverse iteration: z <- (T - lam)^{-1} z with the factors F
 __device__ void tri_solve(const TriLU& F, int n, df* z) {
   df zi = z[0];
+#pragma unroll 4
   for (int i = 0; i + 1 < n; ++i) {
     const df zn = z[i + 1], l = F.l[i];
-    if ((F.piv >> i) & 1ull) {
-      z[i] = zn;
-      zi = df_sub(zi, df_mul(l, zn));
-    } else {
-      z[i] = zi;
-      zi = df_sub(zn, df_mul(l, zi));
-    }
+    const bool sw = (F.piv >> i) & 1ull;
+    const df b = df_sel(sw, zn, zi);
+    z[i] = b;
+    zi = df_sub(df_sel(sw, zi, zn), df_mul(l, b));
   }
   z[n - 1] = zi;
   df z1 = df{0.f, 0.f}, z2 = df{0.f, 0.f};  // z_{i+1}, z_{i+2}
+#pragma unroll 4
   for (int i = n - 1; i >= 0; --i) {
     const df v = df_mul(df_sub(df_sub(z[i], df_mul(F.c[i], z1)), df_mul(F.c2[i], z2)), F.a[i]);
     z[i] = v;
@@ -717,25 +714,16 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
 #pragma unroll
     for (int r = 0; r < 16; ++r) acc[r] = make_float2(0.f, 0.f);
     if (small) {
-      if (c < m)
-        for (int l0 = 0; l0 < m; l0 += 16) {
-          float2 col[16];
+      if (c < m) {
+        // row i of F times column c of R1: l from i to c (both triangular)
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int l = l0 + q;
-            col[q] = l < m ? R1f[l * m + c] : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int r = 0; r < 16; ++r) {
-            const int i = r0 + 4 * r;
-            if (i >= m) continue;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const int l = l0 + q;
-              if (l < m && l >= i && l <= c) cfma(acc[r], E[i * ld + l], col[q]);
-            }
-          }
+        for (int r = 0; r < 16; ++r) {
+          const int i = r0 + 4 * r;
+          float2 s2 = make_float2(0.f, 0.f);
+          for (int l = i; l <= c; ++l) cfma(s2, E[i * ld + l], R1f[l * m + c]);
+          acc[r] = s2;
         }
+      }
     } else if (c < m) {
       for (int i = r0; i < m; i += 4) {
         double2 s = make_double2(0.0, 0.0);
