@@ -288,15 +288,15 @@ __device__ void stage_gram(const TcRows& g, const long* table, int bc, int c, fl
 
 // GEMM staging: chunk c of bc into K-major tiles (M = row, K = real column):
 // element (row r, column q) at (r>>3)*2048 + (q>>3)*128 + (r&7)*16 + (q&7)*2.
-// Thread t covers row t&127 and the column groups (t>>7) + 2p.
-__device__ void stage_gemm_rows(const TcRows& g, const long* table, int bc, int c, float s,
-                                unsigned char* hi, unsigned char* lo) {
+// Thread t covers row t&127 and the column groups (t>>7) + 2p.  The loads
+// (16 x 16 bytes per thread) are issued one chunk ahead into registers, so
+// they arrive while the previous chunk's MMAs and epilogue run.
+__device__ __forceinline__ void load_gemm_rows(const TcRows& g, const long* table, int bc, int c,
+                                               float4 ld[16]) {
   const int rl = threadIdx.x & 127;
   const int r = c * kTcRows + rl;
   const int nreal = 2 * g.m;
   const float* rp = r < g.K ? row_ptr(g, table, bc, r) : nullptr;
-  // all of the thread's loads in flight at once (16 x 16 bytes)
-  float4 ld[16];
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
     const int cg = (threadIdx.x >> 7) + 2 * p;
@@ -305,6 +305,10 @@ __device__ void stage_gemm_rows(const TcRows& g, const long* table, int bc, int 
     ld[2 * p + 1] =
         ok ? __ldg(reinterpret_cast<const float4*>(rp + 8 * cg + 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+}
+__device__ __forceinline__ void store_gemm_rows(const float4 ld[16], float s, unsigned char* hi,
+                                                unsigned char* lo) {
+  const int rl = threadIdx.x & 127;
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
     const int cg = (threadIdx.x >> 7) + 2 * p;
@@ -621,6 +625,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     cm = 0.f;
     __syncthreads();
+    float4 pre[16];  // chunk c's rows, loaded during chunk c-1
+    load_gemm_rows(g, table, bc, 0, pre);
     for (int c = 0; c < nchunk; ++c, ++gidx) {
       const int b = gidx & 1;
       unsigned char* ahi = atiles + 2 * b * kTcTile;
@@ -629,7 +635,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (gidx >= 2 && !bar_wait(&bar[b], (gidx - 2) >> 1)) s_abort = 1;
       __syncthreads();
       if (s_abort) break;
-      stage_gemm_rows(g, table, bc, c, sa, ahi, alo);
+      store_gemm_rows(pre, sa, ahi, alo);
+      if (c + 1 < nchunk) load_gemm_rows(g, table, bc, c + 1, pre);
       fence_async();
       sync_before();
       __syncthreads();
