@@ -400,8 +400,7 @@ __global__ void __launch_bounds__(kThreads, 2) chol_stage1(const double2* __rest
   dz* Gz = reinterpret_cast<dz*>(dsm);          // [m][ld] during the elimination
   float2* Rf = reinterpret_cast<float2*>(dsm);  // [m][ld] R1 (FP32) afterwards
   float2* Zt = Rf + m * ld;                     // [m][ldz]: column c of Z1 in row c
-  __shared__ double piv[kMaxM];
-  __shared__ df rs[kMaxM];
+  __shared__ df piv[kMaxM], rs[kMaxM], rd[kMaxM];
   __shared__ float rinv[kMaxM], redf[kThreads / 32];
   __shared__ int s_fail;
   const int bc = blockIdx.x;
@@ -428,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 2) chol_stage1(const double2* __rest
       const bool bad = !(dj.hi > tol);
       if (bad) dj = df{1.f, 0.f};
       if (tid == 0) {
-        piv[j] = df_to(dj);
+        piv[j] = dj;
         if (bad) s_fail = 1;
       }
       const df inv = df_recip(dj);
@@ -451,9 +450,14 @@ __global__ void __launch_bounds__(kThreads, 2) chol_stage1(const double2* __rest
     flag |= attempt ? 2 : 1;
   }
   // R1 = D^(1/2) L^dag
-  for (int i = tid; i < m; i += nt) rs[i] = df_recip(df_sqrt(df_from(piv[i])));
+  for (int i = tid; i < m; i += nt) {
+    rd[i] = df_sqrt(piv[i]);
+    rs[i] = df_recip(rd[i]);
+  }
   __syncthreads();
-  double2* Rb = R1 + (long)bc * m * m;
+  // R1 is stored in double-float (a dz in each 16-byte entry): its only reader,
+  // the second stage, works in double-float too
+  dz* Rb = reinterpret_cast<dz*>(R1) + (long)bc * m * m;
   constexpr int kSlots = kMaxM * kMaxM / kThreads;
   float2 rf[kSlots];
 #pragma unroll
@@ -462,13 +466,13 @@ __global__ void __launch_bounds__(kThreads, 2) chol_stage1(const double2* __rest
     float2 v = make_float2(0.f, 0.f);
     if (i < m * m) {
       const int r = i / m, c = i % m;
-      double2 o = make_double2(0.0, 0.0);
+      dz o = dz_zero();
       if (c > r)
-        o = dz_to(dz_scale(Gz[r * ld + c], rs[r]));
+        o = dz_scale(Gz[r * ld + c], rs[r]);
       else if (c == r)
-        o = make_double2(sqrt(piv[r]), 0.0);
+        o.re = rd[r];
       Rb[i] = o;
-      v = make_float2((float)o.x, (float)o.y);
+      v = dz_to_f(o);
     }
     rf[s] = v;
   }
@@ -693,9 +697,13 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
     }
   }
 
-  // ---- 2. R = R1 + F R1.  With |F| < 1e-3 the FP32 correction's error is
-  // below the FP32 rounding of the input vectors by that factor.
+  // ---- 2. R = R1 + F R1 (R1 arrives in double-float).  With |F| < 1e-3 the
+  // FP32 product F R1 errs below the FP32 rounding of the input vectors by that
+  // factor; a larger F (a first Gram far from A's, e.g. the BF16 one of a
+  // nearly square block) takes the product in double-float.
   {
+    const dz* Rz = reinterpret_cast<const dz*>(Rg);
+    dz* Hz = reinterpret_cast<dz*>(Hb);
     float dm = 0.f;
     for (int i = tid; i < m * m; i += nt) {
       const int r = i / m, c = i % m;
@@ -705,8 +713,8 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
         dm = fmaxf(dm, fabsf(f.x) + fabsf(f.y));
       }
       Fg[i] = f;
-      const double2 v = Rg[i];
-      R1f[i] = make_float2((float)v.x, (float)v.y);
+      const dz v = Rz[i];
+      R1f[i] = make_float2(v.re.hi, v.im.hi);
     }
     const bool small = block_max(dm, redf) < 1e-3f;
     const int c = tid & 63, r0 = tid >> 6;  // rows r0, r0 + 4, ...
@@ -725,13 +733,17 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
         }
       }
     } else if (c < m) {
+      // R = (1 + F) R1 in double-float, through global scratch
       for (int i = r0; i < m; i += 4) {
-        double2 s = make_double2(0.0, 0.0);
+        zacc sa = zacc_zero();
         for (int l = i; l <= c; ++l) {
           const float2 f = E[i * ld + l];
-          s = zadd(s, zmul(make_double2((l == i ? 1.0 : 0.0) + (double)f.x, (double)f.y), Rg[l * m + c]));
+          dz fz;
+          fz.re = l == i ? two_sum(1.f, f.x) : df{f.x, 0.f};
+          fz.im = df{f.y, 0.f};
+          zacc_mul(sa, fz, Rz[l * m + c]);
         }
-        Hb[i * m + c] = c >= i ? s : make_double2(0.0, 0.0);
+        Hz[i * m + c] = c >= i ? zacc_get(sa) : dz_zero();
       }
     }
     __syncthreads();  // E and R1f are consumed; R (double-float) overwrites them
@@ -740,15 +752,15 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
       for (int r = 0; r < 16; ++r) {
         const int i = r0 + 4 * r;
         if (i >= m) continue;
-        double2 rv = make_double2(0.0, 0.0);
+        dz rv = dz_zero();
         if (!small) {
-          rv = Hb[i * m + c];
+          rv = Hz[i * m + c];
         } else if (c >= i) {
-          const double2 b = Rg[i * m + c];
-          rv = make_double2(b.x + (double)acc[r].x, b.y + (double)acc[r].y);
+          const dz b = Rz[i * m + c];
+          rv = dz{df_add(b.re, df{acc[r].x, 0.f}), df_add(b.im, df{acc[r].y, 0.f})};
         }
-        Mz[i * ld + c] = dz_from(rv);
-        if (ctv) Rg[i * m + c] = rv;
+        Mz[i * ld + c] = rv;
+        if (ctv) Rg[i * m + c] = dz_to(rv);  // R in FP64 for the test vectors
       }
     }
     __syncthreads();
