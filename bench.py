@@ -97,13 +97,18 @@ def kernel_work(w, prec="fp32"):
     spinor = abi // 2 if prec == "mixed_fp16" else abi  # one smoother field
     uk = V * 12 * k * 8  # U_k (and P): [V][2][6][k] complex64
     xy = (V // nb) * 9 * (2 * k) ** 2 * 8  # X and Y
+    n_upd = max(w["N"] - 1, 1)
+    upd_streams = (3 * ((w["N"] - 1 + 1) // 2) + 6 * ((w["N"] - 1) // 2)) / n_upd
     return {
         "mr_input_norm": ("hbm", abi, "B"),
         "mr_to_slab": ("hbm", abi + spinor, "B"),
         "mr_neg_dslash": ("hbm", dslash_bytes(w, prec), "B"),
         "mr_dslash_dot": ("hbm", dslash_bytes(w, prec), "B"),
-        "mr_update": ("hbm", 5 * spinor, "B"),          # read r, w, psi; write r, psi
-        "mr_last_update": ("hbm", 3 * spinor, "B"),
+        # odd iterations read r, w and write r; even ones also read r_{t-2} and
+        # read and write psi (its update deferred by one iteration): per launch
+        # the mean over the N - 1 updates
+        "mr_update": ("hbm", upd_streams * spinor, "B"),
+        "mr_last_update": ("hbm", (4 if w["N"] % 2 == 0 and w["N"] >= 2 else 3) * spinor, "B"),
         "mr_scale": ("hbm", spinor + abi, "B"),
         "trunc_gram": ("hbm", abi, "B"),               # read every block once
         "trunc_gram_tc": ("hbm", abi, "B"),            # the same on BF16 tensor cores

@@ -143,10 +143,12 @@ SmoothWs smooth_ws_layout(const Geom& g) {
   w.ra = o; o = align256(o + field);
   w.wa = o; o = align256(o + field);
   w.ps = o; o = align256(o + field);
+  w.rb = o; o = align256(o + field);
   // partial sums: one per (right-hand side, patch of 32 sites of a timeslice)
   const size_t npatch = ((size_t)(g.V / g.L[3]) + 31) / 32;
   w.part = o; o = align256(o + sizeof(double) * 4 * npatch * g.m);
   w.alpha = o; o = align256(o + sizeof(float2) * g.m);
+  w.alpha_b = o; o = align256(o + sizeof(float2) * g.m);
   w.scale = o; o = align256(o + sizeof(float) * g.m);
   w.bytes = o;
   return w;

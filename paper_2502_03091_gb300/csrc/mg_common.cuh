@@ -41,6 +41,7 @@ constexpr int kMaxK = 32;  // largest k this build supports
 // ---------------------------------------------------------------------------
 struct SmoothWs {
   size_t ra, wa, ps, part, alpha, scale, bytes;
+  size_t rb, alpha_b;  // second r buffer and a array (the deferred psi update)
 };
 struct TruncWs {
   size_t gram, r1, z1, w2, hm, flags, q1, qmax, bytes;  // q1, qmax: 0 unless tensor cores

@@ -649,33 +649,69 @@ __global__ void to_slab(const float4* __restrict__ src, T* __restrict__ dst,
   }
 }
 
-// MR update between two dslash passes: r <- r - a w (r_{t+1}),
-// psi <- psi + a r_t.  One element (a pair of right-hand sides) per thread.
+// MR update between two dslash passes, with psi's update deferred by one
+// iteration (paper Eq. 1; the terms are the same, the psi field is read and
+// written every other iteration):
+//   odd t:  r_t = r_{t-1} - a_{t-1} w_{t-1}                  (r_t into the other r buffer)
+//   even t: psi += a_{t-2} r_{t-2}, then psi += a_{t-1} r_{t-1}, and r_t as above,
+//           written over r_{t-2} after it is read.
+// One element (a pair of right-hand sides) per thread.  The two psi terms are
+// added in the order and with the operations of one update per iteration.
+__device__ __forceinline__ void pair_alpha(const float2* alpha, int gp, float2& ar, float2& ai) {
+  const float2 a0 = alpha[2 * gp], a1 = alpha[2 * gp + 1];
+  ar = make_float2(a0.x, a1.x);
+  ai = make_float2(a0.y, a1.y);
+}
+// r - a w per right-hand side (ar, ai = Re a, Im a of the pair)
+__device__ __forceinline__ CP mr_r_next(const CP& rv, const CP& wv, float2 ar, float2 ai) {
+  CP rn;
+  rn.re = make_float2(rv.re.x - (ar.x * wv.re.x - ai.x * wv.im.x),
+                      rv.re.y - (ar.y * wv.re.y - ai.y * wv.im.y));
+  rn.im = make_float2(rv.im.x - (ar.x * wv.im.x + ai.x * wv.re.x),
+                      rv.im.y - (ar.y * wv.im.y + ai.y * wv.re.y));
+  return rn;
+}
+// psi + a r per right-hand side
+__device__ __forceinline__ CP mr_psi_next(const CP& pv, const CP& rv, float2 ar, float2 ai) {
+  CP pn;
+  pn.re = make_float2(pv.re.x + (ar.x * rv.re.x - ai.x * rv.im.x),
+                      pv.re.y + (ar.y * rv.re.y - ai.y * rv.im.y));
+  pn.im = make_float2(pv.im.x + (ar.x * rv.im.x + ai.x * rv.re.x),
+                      pv.im.y + (ar.y * rv.im.y + ai.y * rv.re.y));
+  return pn;
+}
+
 template <int PAIRS, typename T>
-__global__ void mr_update(T* __restrict__ r, const T* __restrict__ w, T* __restrict__ psi,
-                          const float2* __restrict__ alpha, int V, int np) {
+__global__ void mr_update_r(const T* __restrict__ r, const T* __restrict__ w, T* __restrict__ rn,
+                            const float2* __restrict__ alpha, int V, int np) {
   const long n = (long)V * 12 * np;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x) {
     int q, x, e, p;
     slab_coords<PAIRS>(i, V, q, x, e, p);
-    const int gp = q * PAIRS + p;
-    const float2 a0 = alpha[2 * gp], a1 = alpha[2 * gp + 1];
-    const float2 ar = make_float2(a0.x, a1.x), ai = make_float2(a0.y, a1.y);
-    const CP rv = cp_unpack(__ldcs(r + i)), wv = cp_unpack(__ldcs(w + i));
-    const CP pv = cp_unpack(__ldcs(psi + i));
-    CP rn, pn;
-    // r - a w and psi + a r, per right-hand side (ar, ai = Re a, Im a of the pair)
-    rn.re = make_float2(rv.re.x - (ar.x * wv.re.x - ai.x * wv.im.x),
-                        rv.re.y - (ar.y * wv.re.y - ai.y * wv.im.y));
-    rn.im = make_float2(rv.im.x - (ar.x * wv.im.x + ai.x * wv.re.x),
-                        rv.im.y - (ar.y * wv.im.y + ai.y * wv.re.y));
-    pn.re = make_float2(pv.re.x + (ar.x * rv.re.x - ai.x * rv.im.x),
-                        pv.re.y + (ar.y * rv.re.y - ai.y * rv.im.y));
-    pn.im = make_float2(pv.im.x + (ar.x * rv.im.x + ai.x * rv.re.x),
-                        pv.im.y + (ar.y * rv.im.y + ai.y * rv.re.y));
-    __stcs(r + i, cp_pack<T>(rn));
-    __stcs(psi + i, cp_pack<T>(pn));
+    float2 ar, ai;
+    pair_alpha(alpha, q * PAIRS + p, ar, ai);
+    __stcs(rn + i, cp_pack<T>(mr_r_next(cp_unpack(__ldcs(r + i)), cp_unpack(__ldcs(w + i)), ar, ai)));
+  }
+}
+
+template <int PAIRS, typename T>
+__global__ void mr_update_rpsi(const T* __restrict__ r1, const T* __restrict__ w,
+                               T* __restrict__ r2, T* __restrict__ psi,
+                               const float2* __restrict__ alpha1, const float2* __restrict__ alpha2,
+                               int V, int np) {
+  const long n = (long)V * 12 * np;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    int q, x, e, p;
+    slab_coords<PAIRS>(i, V, q, x, e, p);
+    float2 ar1, ai1, ar2, ai2;
+    pair_alpha(alpha1, q * PAIRS + p, ar1, ai1);
+    pair_alpha(alpha2, q * PAIRS + p, ar2, ai2);
+    const CP rv1 = cp_unpack(__ldcs(r1 + i)), rv2 = cp_unpack(__ldcs(r2 + i));
+    const CP pv = mr_psi_next(mr_psi_next(cp_unpack(__ldcs(psi + i)), rv2, ar2, ai2), rv1, ar1, ai1);
+    __stcs(psi + i, cp_pack<T>(pv));
+    __stcs(r2 + i, cp_pack<T>(mr_r_next(rv1, cp_unpack(__ldcs(w + i)), ar1, ai1)));
   }
 }
 
@@ -687,25 +723,24 @@ __global__ void mr_update(T* __restrict__ r, const T* __restrict__ w, T* __restr
 template <int PAIRS, typename T>
 __global__ void __launch_bounds__(256) last_update(const T* __restrict__ r, T* __restrict__ psi,
                                                    const float2* __restrict__ alpha,
+                                                   const T* __restrict__ r_old,
+                                                   const float2* __restrict__ alpha_old,
                                                    double* __restrict__ part, int V, int cs,
                                                    int nchunk) {
   constexpr int NW = 256 / 32;
   __shared__ double red[NW][PAIRS][2];
   const int q = blockIdx.x / nchunk, g = blockIdx.x % nchunk;
   const int p = threadIdx.x % PAIRS;
-  const int gp = q * PAIRS + p;
-  const float2 a0 = alpha[2 * gp], a1 = alpha[2 * gp + 1];
+  float2 ar, ai, aro = make_float2(0.f, 0.f), aio = aro;
+  pair_alpha(alpha, q * PAIRS + p, ar, ai);
+  if (r_old) pair_alpha(alpha_old, q * PAIRS + p, aro, aio);
   const long x0 = (long)g * cs, x1 = min((long)V, x0 + cs);
   const long i0 = slab_index(q, V, (int)x0, 0, PAIRS, 0), i1 = slab_index(q, V, (int)x1, 0, PAIRS, 0);
   float s0 = 0.f, s1 = 0.f;
   for (long i = i0 + threadIdx.x; i < i1; i += 256) {
-    const CP rc = cp_unpack(__ldcs(r + i));
-    const CP pc = cp_unpack(__ldcs(psi + i));
-    CP pn;
-    pn.re = make_float2(pc.re.x + a0.x * rc.re.x - a0.y * rc.im.x,
-                        pc.re.y + a1.x * rc.re.y - a1.y * rc.im.y);
-    pn.im = make_float2(pc.im.x + a0.x * rc.im.x + a0.y * rc.re.x,
-                        pc.im.y + a1.x * rc.im.y + a1.y * rc.re.y);
+    CP pn = cp_unpack(__ldcs(psi + i));
+    if (r_old) pn = mr_psi_next(pn, cp_unpack(__ldcs(r_old + i)), aro, aio);  // pending term
+    pn = mr_psi_next(pn, cp_unpack(__ldcs(r + i)), ar, ai);
     s0 += pn.re.x * pn.re.x + pn.im.x * pn.im.x;
     s1 += pn.re.y * pn.re.y + pn.im.y * pn.im.y;
     __stcs(psi + i, cp_pack<T>(pn));
@@ -995,22 +1030,39 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
   a.out = w;
   if ((e = run_march<PAIRS, MODE_D_DOT, T>(a, nsl, s)) != cudaSuccess) return e;
   reduce(0);
+  // r_t alternates between two buffers and a_t between two arrays: psi's update
+  // waits one iteration and takes two terms (see mr_update_rpsi)
+  T* rbuf[2] = {r, reinterpret_cast<T*>(ws + lay.rb)};
+  float2* abuf[2] = {alpha, reinterpret_cast<float2*>(ws + lay.alpha_b)};
   for (int t = 1; t < g.niter; ++t) {
-    // r_t = r_{t-1} - a w_{t-1}, psi_t = psi_{t-1} + a r_{t-1}; w_t = D r_t -> a_t
     {
       TimedScope ts("mr_update", s);
-      mr_update<PAIRS, T><<<4096, 256, 0, s>>>(r, w, ps, alpha, a.V, a.np);
+      if (t & 1)
+        mr_update_r<PAIRS, T><<<4096, 256, 0, s>>>(rbuf[(t - 1) & 1], w, rbuf[t & 1],
+                                                   abuf[(t - 1) & 1], a.V, a.np);
+      else
+        mr_update_rpsi<PAIRS, T><<<4096, 256, 0, s>>>(rbuf[(t - 1) & 1], w, rbuf[t & 1], ps,
+                                                      abuf[(t - 1) & 1], abuf[t & 1], a.V, a.np);
     }
+    // w_t = D r_t -> a_t
+    a.in = rbuf[t & 1];
     if ((e = run_march<PAIRS, MODE_D_DOT, T>(a, nsl, s)) != cudaSuccess) return e;
-    reduce(0);
+    {
+      TimedScope ts("mr_reduce", s);
+      finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, 0, abuf[t & 1], scale);
+    }
   }
-  // psi_N = psi_{N-1} + a_{N-1} r_{N-1}; |psi_N|^2 partials over npatch
-  // chunks of the slab (the partial-sum array holds npatch entries per
-  // right-hand side)
+  // psi_N = psi_{N-1} + a_{N-1} r_{N-1} (and the pending a_{N-2} r_{N-2} when N
+  // is even); |psi_N|^2 partials over npatch chunks of the slab (the
+  // partial-sum array holds npatch entries per right-hand side)
   {
+    const int N = g.niter;
     const int cs = (a.V + G - 1) / G;
+    const bool pend = N >= 2 && (N & 1) == 0;
     TimedScope ts("mr_last_update", s);
-    last_update<PAIRS, T><<<nsl * G, 256, 0, s>>>(r, ps, alpha, part, a.V, cs, G);
+    last_update<PAIRS, T><<<nsl * G, 256, 0, s>>>(
+        rbuf[(N - 1) & 1], ps, abuf[(N - 1) & 1], pend ? rbuf[(N - 2) & 1] : nullptr,
+        pend ? abuf[(N - 2) & 1] : nullptr, part, a.V, cs, G);
   }
   reduce(1);
   {
