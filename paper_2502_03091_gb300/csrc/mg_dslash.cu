@@ -546,9 +546,10 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), march_min_blocks<PAIRS
       }
     }
     if (MODE == MODE_D_DOT && ((t & 7) == 7 || t == Lt - 1)) {
-      // lane = 2 * (s * PAIRS + p) + hf: FP64 sum over hf and the warp's sites, per pair
-      double pr[6] = {(double)sre.x, (double)sim.x, (double)snn.x,
-                      (double)sre.y, (double)sim.y, (double)snn.y};
+      // lane = 2 * (s * PAIRS + p) + hf: FP32 sum over hf and the warp's sites
+      // (at most 8 lanes), per pair, then FP64 across steps and warps (FP64
+      // issues at 1/64 of the FP32 rate here; the short FP32 sums cost a few ulp)
+      float pr[6] = {sre.x, sim.x, snn.x, sre.y, sim.y, snn.y};
 #pragma unroll
       for (int i = 0; i < 6; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], 1);
 #pragma unroll
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(march_threads<PAIRS>(), march_min_blocks<PAIRS
         for (int i = 0; i < 6; ++i) pr[i] += __shfl_xor_sync(0xffffffffu, pr[i], off);
       if (lane < 2 * PAIRS && (lane & 1) == 0)
 #pragma unroll
-        for (int i = 0; i < 6; ++i) red[warp][lane >> 1][i] += pr[i];
+        for (int i = 0; i < 6; ++i) red[warp][lane >> 1][i] += (double)pr[i];
       sre = sim = snn = make_float2(0.f, 0.f);
     }
   }
@@ -772,21 +773,39 @@ __global__ void __launch_bounds__(256) last_update(const T* __restrict__ r, T* _
 
 // Second stage of the inner products, in a fixed order (deterministic):
 //   mode 0: a_i = <w,r>_i / <w,w>_i,   mode 1: scale_i = 1 / |psi_i|.
-__global__ void finish_reduction(const double* __restrict__ part, int G, int m, int mode,
-                                 float2* __restrict__ alpha, float* __restrict__ scale) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
+// One CTA of kRedThreads per right-hand side: thread j sums partials j,
+// j + kRedThreads, ... and a fixed tree combines the threads (deterministic).
+constexpr int kRedThreads = 128;
+__global__ void __launch_bounds__(kRedThreads) finish_reduction(const double* __restrict__ part,
+                                                                int G, int m, int mode,
+                                                                float2* __restrict__ alpha,
+                                                                float* __restrict__ scale) {
+  __shared__ double sred[3][kRedThreads];
+  const int i = blockIdx.x;
   double re = 0, im = 0, nn = 0;
-  for (int g = 0; g < G; ++g) {
+  for (int g = threadIdx.x; g < G; g += kRedThreads) {
     const double* pp = part + ((long)i * G + g) * 4;
     re += pp[0];
     im += pp[1];
     nn += pp[2];
   }
-  if (mode == 0) {
-    alpha[i] = nn > 0 ? make_float2((float)(re / nn), (float)(im / nn)) : make_float2(0.f, 0.f);
-  } else {
-    scale[i] = nn > 0 ? (float)(1.0 / sqrt(nn)) : 1.0f;
+  sred[0][threadIdx.x] = re;
+  sred[1][threadIdx.x] = im;
+  sred[2][threadIdx.x] = nn;
+  __syncthreads();
+  for (int h = kRedThreads / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int c = 0; c < 3; ++c) sred[c][threadIdx.x] += sred[c][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    re = sred[0][0];
+    im = sred[1][0];
+    nn = sred[2][0];
+    if (mode == 0)
+      alpha[i] = nn > 0 ? make_float2((float)(re / nn), (float)(im / nn)) : make_float2(0.f, 0.f);
+    else
+      scale[i] = nn > 0 ? (float)(1.0 / sqrt(nn)) : 1.0f;
   }
 }
 
@@ -986,7 +1005,7 @@ cudaError_t march_setup(const Geom& g, const float2* U, const float2* C, const f
     TimedScope ts("mr_input_norm", s);
     abi_norm_partials<<<G, a.np * (256 / a.np), 0, s>>>(reinterpret_cast<const float4*>(in),
                                                        a.part, a.V, a.np, cs, G);
-    finish_reduction<<<(g.m + 63) / 64, 64, 0, s>>>(a.part, G, g.m, 1, alpha, scale);
+    finish_reduction<<<g.m, kRedThreads, 0, s>>>(a.part, G, g.m, 1, alpha, scale);
     scl = scale;
     mul = (float)sqrt(12.0 * (double)g.V);
   }
@@ -1015,10 +1034,9 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
   if (e != cudaSuccess) return e;
   const int nsl = a.np / PAIRS;
   const int G = a.npatch;  // partial sums per right-hand side
-  const int nred = (g.m + 63) / 64;
   auto reduce = [&](int mode) {
     TimedScope ts("mr_reduce", s);
-    finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, mode, alpha, scale);
+    finish_reduction<<<g.m, kRedThreads, 0, s>>>(part, G, g.m, mode, alpha, scale);
   };
 
   // r_0 = -D psi_0
@@ -1049,7 +1067,7 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
     if ((e = run_march<PAIRS, MODE_D_DOT, T>(a, nsl, s)) != cudaSuccess) return e;
     {
       TimedScope ts("mr_reduce", s);
-      finish_reduction<<<nred, 64, 0, s>>>(part, G, g.m, 0, abuf[t & 1], scale);
+      finish_reduction<<<g.m, kRedThreads, 0, s>>>(part, G, g.m, 0, abuf[t & 1], scale);
     }
   }
   // psi_N = psi_{N-1} + a_{N-1} r_{N-1} (and the pending a_{N-2} r_{N-2} when N
