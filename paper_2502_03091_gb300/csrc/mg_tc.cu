@@ -200,6 +200,20 @@ struct TcRows {
   int nb, K, m, nbc;
 };
 
+// One complex Gram entry in double-float, the form the Gram's readers compute
+// in: (re hi, re lo, im hi, im lo) in the 16 bytes of a complex FP64 entry.
+struct dz2 {
+  float re_hi, re_lo, im_hi, im_lo;
+};
+// (a + b) inv, (c + d) inv exactly (TwoSum; inv a power of two)
+__device__ __forceinline__ dz2 dz2_of(float a, float b, float c, float d, float inv) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  const float t = __fadd_rn(c, d), dd = __fsub_rn(t, c);
+  const float f = __fadd_rn(__fsub_rn(c, __fsub_rn(t, dd)), __fsub_rn(d, dd));
+  return dz2{s * inv, e * inv, t * inv, f * inv};
+}
+
 // global site of local site `loc` of block `j`
 __device__ __forceinline__ int tc_block_site(const TcRows& g, int j, int loc) {
   int jc[4], lc[4];
@@ -456,8 +470,8 @@ __global__ void __launch_bounds__(kTcThreads, PREC == TC_BF16 ? 3 : 1)
       // lane = row rho = 32 warp + lane; rows 2i, 2i+1 (re, im of column i of
       // A) are neighbouring lanes
       const int rho = warp * 32 + lane, i = rho >> 1;
-      const double inv = 1.0 / ((double)s * (double)s);
-      double2* Gb = G + (long)bc * m * m;
+      const float inv = 1.f / (s * s);  // a power of two: the scaling is exact
+      dz2* Gb = reinterpret_cast<dz2*>(G) + (long)bc * m * m;
       if (X3) add_chunk((gidx - 1) & 1);
 #pragma unroll
       for (int cb = 0; cb < kTcCols / 16; ++cb) {
@@ -475,8 +489,7 @@ __global__ void __launch_bounds__(kTcThreads, PREC == TC_BF16 ? 3 : 1)
           const float im_im = __shfl_down_sync(0xffffffffu, re_im, 1);
           const int jj = cb * 8 + t;
           if ((lane & 1) == 0 && i < m && jj < m)
-            Gb[(long)i * m + jj] = make_double2(((double)re_re + (double)im_im) * inv,
-                                                ((double)re_im - (double)im_re) * inv);
+            Gb[(long)i * m + jj] = dz2_of(re_re, im_im, re_im, -im_re, inv);
         }
       }
     }
@@ -587,10 +600,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // scales of A and B
     float abnd = 1.f;
     if (gdiag) {
-      const double2* Gb = gdiag + (long)bc * m * m;
-      double mx = 0;
-      for (int i = 0; i < m; ++i) mx = fmax(mx, Gb[(long)i * m + i].x);
-      abnd = (float)sqrt(mx);
+      // the largest diagonal entry of the Gram, one per thread and a block
+      // maximum (FP32 is plenty for a power-of-two scale with 4x headroom)
+      const dz2* Gb = reinterpret_cast<const dz2*>(gdiag) + (long)bc * m * m;
+      const float di = (int)threadIdx.x < m ? Gb[(long)threadIdx.x * m + threadIdx.x].re_hi : 0.f;
+      abnd = sqrtf(block_max(di, red));
     } else if (abound) {
       abnd = abound[bc];
     }

@@ -122,94 +122,6 @@ __device__ __forceinline__ void right_mul_upper(const float2* As, const float2* 
 }
 
 // ---------------------------------------------------------------------------
-// Gram of the (optionally transformed) block: G[bc] = B^dag B, B = A or A Z.
-// One CTA per block-chirality; each active thread owns a 4x4 tile of the
-// upper triangle of tiles; FP32 within a chunk, FP64 across chunks.
-// ---------------------------------------------------------------------------
-template <bool TRANSFORM>
-__global__ void __launch_bounds__(kThreads) gram_kernel(const float2* __restrict__ psi,
-                                                        const float2* __restrict__ Z,
-                                                        double2* __restrict__ G, BlockGeom g) {
-  extern __shared__ float4 smem4[];
-  float2* As = reinterpret_cast<float2*>(smem4);
-  float2* Qs = As + kChunkRows * g.m;
-  float2* Zs = Qs + kChunkRows * g.m;
-  const int bc = blockIdx.x, m = g.m, TT = m / 4;
-  if (TRANSFORM) {
-    const float2* Zb = Z + (long)bc * m * m;
-    for (int i = threadIdx.x; i < m * m; i += blockDim.x) Zs[i] = Zb[i];
-  }
-  // tile (ti, tj), ti <= tj, enumerated row by row
-  int ti = -1, tj = -1;
-  {
-    int t = threadIdx.x;
-    for (int r = 0; r < TT; ++r) {
-      if (t < TT - r) {
-        ti = r;
-        tj = r + t;
-        break;
-      }
-      t -= TT - r;
-    }
-  }
-  double2 dacc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) dacc[a][c] = make_double2(0.0, 0.0);
-  const int nch = (g.nb + g.csites - 1) / g.csites;
-  for (int ch = 0; ch < nch; ++ch) {
-    __syncthreads();
-    load_chunk(psi, g, bc, ch, As);
-    __syncthreads();
-    const float2* Bs = As;
-    if (TRANSFORM) {
-      right_mul_upper(As, Zs, Qs, kChunkRows, m);
-      __syncthreads();
-      Bs = Qs;
-    }
-    if (ti >= 0) {
-      float2 acc[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
-      for (int r = 0; r < kChunkRows; ++r) {
-        const float4* row = reinterpret_cast<const float4*>(Bs + r * m);
-        const float4 a01 = row[2 * ti], a23 = row[2 * ti + 1];
-        const float4 b01 = row[2 * tj], b23 = row[2 * tj + 1];
-        const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
-                              make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
-        const float2 bv[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
-                              make_float2(b23.x, b23.y), make_float2(b23.z, b23.w)};
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) cfmac(acc[a][c], av[a], bv[c]);
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          dacc[a][c].x += (double)acc[a][c].x;
-          dacc[a][c].y += (double)acc[a][c].y;
-        }
-    }
-  }
-  if (ti >= 0) {
-    double2* Gb = G + (long)bc * m * m;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i = 4 * ti + a, jj = 4 * tj + c;
-        Gb[i * m + jj] = dacc[a][c];
-        Gb[jj * m + i] = zconj(dacc[a][c]);
-      }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Double-float numbers: value = hi + lo, two FP32 with |lo| <= ulp(hi) / 2.
 // Sums by Knuth's TwoSum and products by the FMA form of Dekker's TwoProduct
 // (error-free transformations; cf. Hida, Li, Bailey, "Algorithms for quad-double
@@ -362,6 +274,96 @@ __device__ __forceinline__ zacc zacc_merge_xor(zacc a, int o) {
   return zacc{acc_merge(a.re, acc_shfl_xor(a.re, o)), acc_merge(a.im, acc_shfl_xor(a.im, o))};
 }
 
+// ---------------------------------------------------------------------------
+// Gram of the (optionally transformed) block: G[bc] = B^dag B, B = A or A Z.
+// One CTA per block-chirality; each active thread owns a 4x4 tile of the
+// upper triangle of tiles; FP32 within a chunk, FP64 across chunks.
+// ---------------------------------------------------------------------------
+template <bool TRANSFORM>
+__global__ void __launch_bounds__(kThreads) gram_kernel(const float2* __restrict__ psi,
+                                                        const float2* __restrict__ Z,
+                                                        double2* __restrict__ G, BlockGeom g) {
+  extern __shared__ float4 smem4[];
+  float2* As = reinterpret_cast<float2*>(smem4);
+  float2* Qs = As + kChunkRows * g.m;
+  float2* Zs = Qs + kChunkRows * g.m;
+  const int bc = blockIdx.x, m = g.m, TT = m / 4;
+  if (TRANSFORM) {
+    const float2* Zb = Z + (long)bc * m * m;
+    for (int i = threadIdx.x; i < m * m; i += blockDim.x) Zs[i] = Zb[i];
+  }
+  // tile (ti, tj), ti <= tj, enumerated row by row
+  int ti = -1, tj = -1;
+  {
+    int t = threadIdx.x;
+    for (int r = 0; r < TT; ++r) {
+      if (t < TT - r) {
+        ti = r;
+        tj = r + t;
+        break;
+      }
+      t -= TT - r;
+    }
+  }
+  double2 dacc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dacc[a][c] = make_double2(0.0, 0.0);
+  const int nch = (g.nb + g.csites - 1) / g.csites;
+  for (int ch = 0; ch < nch; ++ch) {
+    __syncthreads();
+    load_chunk(psi, g, bc, ch, As);
+    __syncthreads();
+    const float2* Bs = As;
+    if (TRANSFORM) {
+      right_mul_upper(As, Zs, Qs, kChunkRows, m);
+      __syncthreads();
+      Bs = Qs;
+    }
+    if (ti >= 0) {
+      float2 acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
+      for (int r = 0; r < kChunkRows; ++r) {
+        const float4* row = reinterpret_cast<const float4*>(Bs + r * m);
+        const float4 a01 = row[2 * ti], a23 = row[2 * ti + 1];
+        const float4 b01 = row[2 * tj], b23 = row[2 * tj + 1];
+        const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
+                              make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
+        const float2 bv[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
+                              make_float2(b23.x, b23.y), make_float2(b23.z, b23.w)};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) cfmac(acc[a][c], av[a], bv[c]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          dacc[a][c].x += (double)acc[a][c].x;
+          dacc[a][c].y += (double)acc[a][c].y;
+        }
+    }
+  }
+  if (ti >= 0) {
+    // the Gram is stored in double-float (a pair of FP32 per real number in
+    // each 16-byte entry), the form its readers compute in
+    dz* Gb = reinterpret_cast<dz*>(G) + (long)bc * m * m;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = 4 * ti + a, jj = 4 * tj + c;
+        Gb[i * m + jj] = dz_from(dacc[a][c]);
+        Gb[jj * m + i] = dz_from(zconj(dacc[a][c]));
+      }
+  }
+}
+
 // (r, c) of entry idx of a lower triangle stored row by row (idx = r (r+1)/2 + c,
 // c <= r); the FP32 square root is within one of the row, fixed up exactly
 __device__ __forceinline__ void tri_index(int idx, int& r, int& c) {
@@ -404,20 +406,20 @@ __global__ void __launch_bounds__(kThreads, 2) chol_stage1(const double2* __rest
   __shared__ float rinv[kMaxM], redf[kThreads / 32];
   __shared__ int s_fail;
   const int bc = blockIdx.x;
-  const double2* Gb = G + (long)bc * m * m;
+  const dz* Gb = reinterpret_cast<const dz*>(G) + (long)bc * m * m;
   float mx = 0.f;
-  for (int i = tid; i < m; i += nt) mx = fmaxf(mx, (float)Gb[i * m + i].x);
+  for (int i = tid; i < m; i += nt) mx = fmaxf(mx, Gb[i * m + i].re.hi);
   const float maxd = block_max(mx, redf);
   const float tol = 1e-13f * maxd;
   int32_t flag = 0;
   for (int attempt = 0; attempt < 2; ++attempt) {
-    const double shift = attempt ? 1e-5 * (double)maxd : 0.0;
+    const df shift = df{attempt ? 1e-5f * maxd : 0.f, 0.f};
     for (int i = tid; i < m * m; i += nt) {
       const int r = i / m, c = i % m;
       if (c >= r) {
-        double2 v = Gb[i];
-        if (r == c) v.x += shift;
-        Gz[r * ld + c] = dz_from(v);
+        dz v = Gb[i];
+        if (r == c) v.re = df_add(v.re, shift);
+        Gz[r * ld + c] = v;
       }
     }
     if (tid == 0) s_fail = 0;
@@ -656,8 +658,9 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
   for (int i = tid; i < m * m; i += nt) {
     const int r = i / m, c = i % m;
     if (c >= r) {
-      const double2 v = Gb[i];
-      E[r * ld + c] = make_float2((float)(v.x - (r == c ? 1.0 : 0.0)), (float)v.y);
+      const dz v = reinterpret_cast<const dz*>(Gb)[i];
+      const df er = r == c ? df_sub(v.re, df{1.f, 0.f}) : v.re;
+      E[r * ld + c] = make_float2(__fadd_rn(er.hi, er.lo), __fadd_rn(v.im.hi, v.im.lo));
     }
   }
   if (tid == 0) s_fail = 0;
