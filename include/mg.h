@@ -81,15 +81,17 @@ typedef enum {
 } mg_status;
 
 typedef enum {
-  MG_PREC_FP32 = 0,       /* complex64 storage, FP32 arithmetic on the CUDA cores; FP64
-                             for the small Cholesky / R-factor eigen problems */
+  MG_PREC_FP32 = 0,       /* complex64 storage, FP32 arithmetic on the CUDA cores; the
+                             small Cholesky / R-factor eigen problems in double-float
+                             (pairs of FP32, ~2^-44 relative) */
   MG_PREC_MIXED = 1,      /* the smoother as MG_PREC_FP32; the truncation's dense
                              contractions on the tensor cores with FP32 accumulation:
                              the first Gram (only the preconditioner of CholeskyQR2's
                              second pass) in BF16, the second Gram, Q1 = A R1^-1 and
                              U_k with FP16 operands split into hi + lo parts (three
                              products, about FP32 accuracy, a power-of-two scale per
-                             block-chirality); FP64 Cholesky / R-factor eigen problem.
+                             block-chirality); double-float Cholesky / R-factor eigen
+                             problem.
                              Results agree with the FP64 reference as closely as the
                              MG_PREC_FP32 path's do. */
   MG_PREC_MIXED_FP16 = 2  /* as MG_PREC_MIXED, but the smoother's fields are stored

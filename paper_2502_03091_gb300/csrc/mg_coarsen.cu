@@ -21,23 +21,32 @@ namespace {
 __global__ void prolongator_kernel(const float2* __restrict__ Uk, float2* __restrict__ P, int L0,
                                    int L1, int L2, int L3, int b0, int b1, int b2, int b3,
                                    int k, int rps) {
+  // one warp per (site, chirality): its row of rps * k complex numbers is
+  // contiguous in both layouts (16-byte copies when the count is even)
   const long V = (long)L0 * L1 * L2 * L3;
   const int nb = b0 * b1 * b2 * b3;
   const int row = rps * k;  // complex per (site, chirality)
-  const long n = V * 2 * row;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
-    const long x = i / (2 * row);
-    const int rem = (int)(i % (2 * row));
-    const int al = rem / row, e = rem % row;
+  const int nf4 = row / 2;
+  const int lane = threadIdx.x & 31;
+  const long nw = (long)gridDim.x * (blockDim.x >> 5);
+  const int Lc0 = L0 / b0, Lc1 = L1 / b1, Lc2 = L2 / b2;
+  for (long wr = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); wr < 2 * V; wr += nw) {
+    const long x = wr >> 1;
+    const int al = (int)(wr & 1);
     int t = (int)x;
     const int x0 = t % L0; t /= L0;
     const int x1 = t % L1; t /= L1;
     const int x2 = t % L2; const int x3 = t / L2;
-    const int Lc0 = L0 / b0, Lc1 = L1 / b1, Lc2 = L2 / b2;
     const int j = x0 / b0 + Lc0 * (x1 / b1 + Lc1 * (x2 / b2 + Lc2 * (x3 / b3)));
     const int loc = x0 % b0 + b0 * (x1 % b1 + b1 * (x2 % b2 + b2 * (x3 % b3)));
-    P[i] = Uk[(((long)j * 2 + al) * nb + loc) * row + e];
+    const float2* src = Uk + (((long)j * 2 + al) * nb + loc) * row;
+    float2* dst = P + wr * row;
+    if ((row & 1) == 0) {
+      for (int f = lane; f < nf4; f += 32)
+        __stcs(reinterpret_cast<float4*>(dst) + f, __ldcs(reinterpret_cast<const float4*>(src) + f));
+    } else {
+      for (int f = lane; f < row; f += 32) dst[f] = src[f];
+    }
   }
 }
 
@@ -303,7 +312,7 @@ __global__ void coarse_apply_kernel(const float2* __restrict__ X, const float2* 
 
 cudaError_t launch_prolongator(const Geom& g, const float2* Uk, float2* P, cudaStream_t s) {
   TimedScope ts("prolongator", s);
-  prolongator_kernel<<<2048, 256, 0, s>>>(Uk, P, g.L[0], g.L[1], g.L[2], g.L[3], g.b[0], g.b[1],
+  prolongator_kernel<<<4 * 152 * 8, 256, 0, s>>>(Uk, P, g.L[0], g.L[1], g.L[2], g.L[3], g.b[0], g.b[1],
                                            g.b[2], g.b[3], g.k, g.rps);
   return cudaGetLastError();
 }
