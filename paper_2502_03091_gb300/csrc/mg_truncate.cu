@@ -684,14 +684,15 @@ __global__ void __launch_bounds__(kThreads, 2) svd_stage2(
         }
       if (j < m) {
         const float inv2 = inv * inv;
-        const int n = m - j - 1;
-        for (int idx = tid; idx < n * (n + 1) / 2; idx += nt) {
-          int a, b;
-          tri_index(idx, a, b);
-          const int r = j + 1 + b, c = j + 1 + a;  // r <= c
-          const float2 x = E[j * ld + r], y = E[j * ld + c];
-          float2& v = E[r * ld + c];
-          v = make_float2(v.x - (x.x * y.x + x.y * y.y) * inv2, v.y - (x.x * y.y - x.y * y.x) * inv2);
+        // column c = tid % 64, rows j+1 + tid/64 + 4s
+        const int c = tid & 63;
+        if (c > j && c < m) {
+          const float2 y = E[j * ld + c];
+          for (int r = j + 1 + (tid >> 6); r <= c; r += 4) {
+            const float2 x = E[j * ld + r];
+            float2& v = E[r * ld + c];
+            v = make_float2(v.x - (x.x * y.x + x.y * y.y) * inv2, v.y - (x.x * y.y - x.y * y.x) * inv2);
+          }
         }
       }
       inv_prev = inv;
