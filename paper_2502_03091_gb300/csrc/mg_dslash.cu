@@ -243,24 +243,62 @@ __device__ __forceinline__ void hop_v(CP zu[3], CP zl[3], int hf, const T v[6],
   } else {
     kr = ki = -S * hw;
   }
+  if constexpr (sizeof(T) < 16) {
+    // FP16 storage (128 registers): one colour at a time
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      CP g{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (S > 0) lmul(g, L[c * 3 + d], h[d], nh[d]);
+        else lmulc(g, L[d * 3 + c], h[d], nh[d]);
+      }
+      zu[c].re = pfma(dup(hw), g.re, zu[c].re);
+      zu[c].im = pfma(dup(hw), g.im, zu[c].im);
+      if (MU == 0 || MU == 1) {
+        g.re.x = __shfl_xor_sync(0xffffffffu, g.re.x, 1);
+        g.re.y = __shfl_xor_sync(0xffffffffu, g.re.y, 1);
+        g.im.x = __shfl_xor_sync(0xffffffffu, g.im.x, 1);
+        g.im.y = __shfl_xor_sync(0xffffffffu, g.im.y, 1);
+      }
+      const float2 X = (MU == 0 || MU == 2) ? g.im : g.re;
+      const float2 Y = (MU == 0 || MU == 2) ? g.re : g.im;
+      zl[c].re = pfma(dup(kr), X, zl[c].re);
+      zl[c].im = pfma(dup(ki), Y, zl[c].im);
+    }
+    return;
+  }
+  // FP32 storage: the three colours' link products first (six independent FMA
+  // chains), then the accumulations and the partner exchange, so no shuffle
+  // sits between the chains (1% faster here; it spills at 128 registers)
+  CP g[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    CP g{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    g[c] = CP{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      if (S > 0) lmul(g, L[c * 3 + d], h[d], nh[d]);
-      else lmulc(g, L[d * 3 + c], h[d], nh[d]);
+      if (S > 0) lmul(g[c], L[c * 3 + d], h[d], nh[d]);
+      else lmulc(g[c], L[d * 3 + c], h[d], nh[d]);
     }
-    zu[c].re = pfma(dup(hw), g.re, zu[c].re);
-    zu[c].im = pfma(dup(hw), g.im, zu[c].im);
-    if (MU == 0 || MU == 1) {
-      g.re.x = __shfl_xor_sync(0xffffffffu, g.re.x, 1);
-      g.re.y = __shfl_xor_sync(0xffffffffu, g.re.y, 1);
-      g.im.x = __shfl_xor_sync(0xffffffffu, g.im.x, 1);
-      g.im.y = __shfl_xor_sync(0xffffffffu, g.im.y, 1);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    zu[c].re = pfma(dup(hw), g[c].re, zu[c].re);
+    zu[c].im = pfma(dup(hw), g[c].im, zu[c].im);
+  }
+  if (MU == 0 || MU == 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      g[c].re.x = __shfl_xor_sync(0xffffffffu, g[c].re.x, 1);
+      g[c].re.y = __shfl_xor_sync(0xffffffffu, g[c].re.y, 1);
+      g[c].im.x = __shfl_xor_sync(0xffffffffu, g[c].im.x, 1);
+      g[c].im.y = __shfl_xor_sync(0xffffffffu, g[c].im.y, 1);
     }
-    const float2 X = (MU == 0 || MU == 2) ? g.im : g.re;
-    const float2 Y = (MU == 0 || MU == 2) ? g.re : g.im;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float2 X = (MU == 0 || MU == 2) ? g[c].im : g[c].re;
+    const float2 Y = (MU == 0 || MU == 2) ? g[c].re : g[c].im;
     zl[c].re = pfma(dup(kr), X, zl[c].re);
     zl[c].im = pfma(dup(ki), Y, zl[c].im);
   }
@@ -295,7 +333,7 @@ __device__ __forceinline__ void cmul_acc(CP& acc, float2 c, const CP& v) {
 //
 // MODE_NEG_D: out = -D in.  MODE_D_DOT: out = D in, plus per-patch partial
 // sums <out, in> and |out|^2 per right-hand side (per lane in FP32 over 8
-// steps, then reduced over the warp in FP64 into shared memory).
+// steps, reduced over the warp in FP32, accumulated in FP64 in shared memory).
 // Lanes: threadIdx = (site * P + pair) * 2 + hf.
 // ---------------------------------------------------------------------------
 constexpr int kSPC = 32;

@@ -96,6 +96,23 @@ def test_dirac_apply(name):
     assert err.max() <= 1e-6, err.max()
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 5])
+def test_smoother_iteration_counts(N):
+    """psi's update waits one iteration and takes two terms; odd and even N end
+    with one or two pending terms (and N = 1 with none of the two-term steps)."""
+    c = _case("4^4 Wilson m'=8 k=4 (workload 1)")
+    p0 = c["p0"]
+    p = mg.Problem(dims=c["dims"], block=c["block"], m0=c["m0"], n_vec=c["m"], k=c["k"],
+                   mr_iters=N, csw=c["csw"], xi=c["xi"])
+    U, C = _dev(c)
+    psi = torch.empty(p0.shape, dtype=torch.complex64, device="cuda")
+    mg.mg_smooth_testvecs(p, U, C, to_dev(p0), psi, mg.workspace(p, mg.MG_CALL_SMOOTH))
+    mg.mg_sync_status()
+    ref = O.mr(c["dims"], c["m0"], c["xi"], c["U"], c["C"], p0, N)
+    err = np.linalg.norm((to_host(psi) - ref).reshape(-1, c["m"]), axis=0)
+    assert err.max() <= 2e-5, (N, err.max())
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_smoother(name):
     c = _case(name)
