@@ -713,8 +713,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // block) or, for the sites on the block's +mu face, into Y_{+mu}; then
 // X = S + sigma_3 S^dag sigma_3 and Y_{-mu}(j + mu) = sigma_3 Y_{+mu}(j)^dag sigma_3.
 // Over the reals, with 8 rows per site (the 6 of L or R and two zero rows)
-// and chunks of 8 sites, a chunk is D = L~^T R~ with M = 4k real columns of
-// L~ (padded to 128), N = 4k padded to a multiple of 32, K = 64, operands
+// and chunks of 12 sites, a chunk is D = L~^T R~ with M = 4k real columns of
+// L~ (padded to 128), N = 4k padded to a multiple of 32, K = 96, operands
 // FP16 hi/lo (P and L scaled by 2^14: every entry of a block-orthonormal P
 // is at most 1 in modulus; R by 2^8: |R| <= 64).  Per chunk D1 (hi*hi) and
 // D2 (hi*lo + lo*hi) accumulate in TMEM from zero and are added on the CUDA
@@ -733,9 +733,9 @@ struct TcCoarsen {
   float diag;
 };
 
-constexpr int kCsSites = 8;                    // sites per chunk
-constexpr int kCsSbo = kCsSites * 128;         // bytes between 8-row groups (K = 64)
-constexpr int kCsTileL = (kTcCols / 8) * kCsSbo;  // L~^T tile: M = 128 (16 KB)
+constexpr int kCsSites = 12;                   // sites per chunk (K = 96: six K steps)
+constexpr int kCsSbo = kCsSites * 128;         // bytes between 8-row groups
+constexpr int kCsTileL = (kTcCols / 8) * kCsSbo;  // L~^T tile: M = 128 (24 KB)
 constexpr float kCsScaleL = 16384.f;           // 2^14
 constexpr float kCsScaleR = 256.f;             // 2^8
 
@@ -965,7 +965,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_coarsen_kernel(TcCoarsen a,
             sync_after();
             const uint32_t d1 = taddr + b * 2 * NPAD, d2 = d1 + NPAD;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
+            for (int kk = 0; kk < kCsSites / 2; ++kk) {
               const uint64_t dlh = smem_desc(su32(lhi) + kk * 256, 128, kCsSbo);
               const uint64_t dll = smem_desc(su32(llo) + kk * 256, 128, kCsSbo);
               const uint64_t drh = smem_desc(su32(rhi) + kk * 256, 128, kCsSbo);
