@@ -587,17 +587,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int rows = min(kTcRows, g.K - cc * kTcRows);
     for (int row = warp; row < rows; row += kTcThreads / 32) {
       float2* out = C + ((long)bc * g.K + cc * kTcRows + row) * n;
-      if ((n & 1) == 0) {
-        // two complex numbers per 16-byte store (rows start 16-byte aligned)
-        for (int jj = 2 * lane; jj < n; jj += 64) {
-          const float2 z0 = stg[row * ld + (n < 64 ? jj : (jj ^ (row & 31)))];
-          const float2 z1 = stg[row * ld + (n < 64 ? jj + 1 : ((jj + 1) ^ (row & 31)))];
-          *reinterpret_cast<float4*>(out + jj) = make_float4(z0.x, z0.y, z1.x, z1.y);
-        }
-      } else {
-        for (int jj = lane; jj < n; jj += 32)
-          out[jj] = stg[row * ld + (n < 64 ? jj : (jj ^ (row & 31)))];
-      }
+      for (int jj = lane; jj < n; jj += 32)
+        out[jj] = stg[row * ld + (n < 64 ? jj : (jj ^ (row & 31)))];
     }
   };
 
