@@ -671,20 +671,55 @@ __global__ void __launch_bounds__(256) abi_norm_partials(const float4* __restric
   }
 }
 
-// psi_0 (ABI layout [V][12][m'] complex) -> slab layout, each vector times
-// mul * scale[i] (scale == nullptr: no scaling)
+// Layout conversions between the ABI layout [V][12][m'] (complex) and the slab
+// layout.  A CTA moves tiles of kTrSites consecutive sites: in the ABI layout
+// a tile is one contiguous region, in slab q a contiguous run of
+// kTrSites * 12 * PAIRS elements, so both sides are read and written in long
+// coalesced runs, with the transpose in shared memory (rows of the tile hold
+// the np pairs of one (site, component) at a pitch of np + PAIRS elements, so
+// the 16-byte reads of consecutive rows fall on different bank groups).
+constexpr int kTrSites = 4;
+constexpr int kTrThreads = 256;
+constexpr int kTrBlocksPerSm = 8;
+
+inline size_t tr_smem(int np, int pairs) {  // at most 27.6 KB (np <= 32)
+  return sizeof(float4) * (size_t)kTrSites * 12 * (np + pairs);
+}
+// kTrBlocksPerSm CTAs per SM, each walking its tiles
+inline int tr_grid() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    n = 152;
+  return n * kTrBlocksPerSm;
+}
+
+// psi_0 (ABI layout) -> slab layout, each vector times mul * scale[i]
+// (scale == nullptr: no scaling)
 template <int PAIRS, typename T>
-__global__ void to_slab(const float4* __restrict__ src, T* __restrict__ dst,
-                        const float* __restrict__ scale, float mul, int V, int np) {
-  const long n = (long)V * 12 * np;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
-    int q, x, e, p;
-    slab_coords<PAIRS>(i, V, q, x, e, p);
-    const int gp = q * PAIRS + p;
-    const float4 v = __ldcs(src + ((long)x * 12 + e) * np + gp);
-    const float s0 = scale ? mul * scale[2 * gp] : 1.f, s1 = scale ? mul * scale[2 * gp + 1] : 1.f;
-    __stcs(dst + i, cp_pack<T>(CP{make_float2(v.x * s0, v.z * s1), make_float2(v.y * s0, v.w * s1)}));
+__global__ void __launch_bounds__(kTrThreads) to_slab(const float4* __restrict__ src,
+                                                      T* __restrict__ dst,
+                                                      const float* __restrict__ scale, float mul,
+                                                      int V, int np) {
+  extern __shared__ float4 tr_tile[];  // [kTrSites * 12][np + PAIRS]
+  const int pitch = np + PAIRS, nsl = np / PAIRS;
+  for (int x0 = blockIdx.x * kTrSites; x0 < V; x0 += gridDim.x * kTrSites) {
+    const int nrow = min(kTrSites, V - x0) * 12, run = nrow * PAIRS;
+    const float4* s0 = src + (long)x0 * 12 * np;
+    for (int i = threadIdx.x; i < nrow * np; i += kTrThreads) {
+      const int row = i / np;
+      tr_tile[row * pitch + (i - row * np)] = __ldcs(s0 + i);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nsl * run; i += kTrThreads) {
+      const int q = i / run, k = i - q * run;  // k = (site * 12 + e) * PAIRS + p
+      const int row = k / PAIRS, gp = q * PAIRS + (k - row * PAIRS);
+      const float4 v = tr_tile[row * pitch + gp];
+      const float a0 = scale ? mul * scale[2 * gp] : 1.f, a1 = scale ? mul * scale[2 * gp + 1] : 1.f;
+      __stcs(dst + slab_index(q, V, x0, 0, PAIRS, 0) + k,
+             cp_pack<T>(CP{make_float2(v.x * a0, v.z * a1), make_float2(v.y * a0, v.w * a1)}));
+    }
+    __syncthreads();
   }
 }
 
@@ -851,20 +886,30 @@ __global__ void fill_kernel(float* __restrict__ v, int n, float x) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = x;
 }
 
-// psi (ABI layout) = scale * psi_slab
+// psi (ABI layout) = scale * psi_slab, tile by tile as in to_slab
 template <int PAIRS, typename T>
-__global__ void scale_to_abi(const T* __restrict__ src, float4* __restrict__ dst,
-                             const float* __restrict__ scale, int V, int np) {
-  const long n = (long)V * 12 * np;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x) {
-    int q, x, e, p;
-    slab_coords<PAIRS>(i, V, q, x, e, p);
-    const int gp = q * PAIRS + p;
-    const CP v = cp_unpack(__ldcs(src + i));
-    const float s0 = scale[2 * gp], s1 = scale[2 * gp + 1];
-    __stcs(dst + ((long)x * 12 + e) * np + gp,
-           make_float4(v.re.x * s0, v.im.x * s0, v.re.y * s1, v.im.y * s1));
+__global__ void __launch_bounds__(kTrThreads) scale_to_abi(const T* __restrict__ src,
+                                                           float4* __restrict__ dst,
+                                                           const float* __restrict__ scale,
+                                                           int V, int np) {
+  extern __shared__ float4 tr_tile[];  // [kTrSites * 12][np + PAIRS]
+  const int pitch = np + PAIRS, nsl = np / PAIRS;
+  for (int x0 = blockIdx.x * kTrSites; x0 < V; x0 += gridDim.x * kTrSites) {
+    const int nrow = min(kTrSites, V - x0) * 12, run = nrow * PAIRS;
+    for (int i = threadIdx.x; i < nsl * run; i += kTrThreads) {
+      const int q = i / run, k = i - q * run;
+      const int row = k / PAIRS, gp = q * PAIRS + (k - row * PAIRS);
+      const CP v = cp_unpack(__ldcs(src + slab_index(q, V, x0, 0, PAIRS, 0) + k));
+      const float a0 = scale[2 * gp], a1 = scale[2 * gp + 1];
+      tr_tile[row * pitch + gp] = make_float4(v.re.x * a0, v.im.x * a0, v.re.y * a1, v.im.y * a1);
+    }
+    __syncthreads();
+    float4* d0 = dst + (long)x0 * 12 * np;
+    for (int i = threadIdx.x; i < nrow * np; i += kTrThreads) {
+      const int row = i / np;
+      __stcs(d0 + i, tr_tile[row * pitch + (i - row * np)]);
+    }
+    __syncthreads();
   }
 }
 
@@ -1049,8 +1094,8 @@ cudaError_t march_setup(const Geom& g, const float2* U, const float2* C, const f
   }
   {
     TimedScope ts("mr_to_slab", s);
-    to_slab<PAIRS, T><<<4096, 256, 0, s>>>(reinterpret_cast<const float4*>(in), ps, scl, mul,
-                                           a.V, a.np);
+    to_slab<PAIRS, T><<<tr_grid(), kTrThreads, tr_smem(a.np, PAIRS), s>>>(
+        reinterpret_cast<const float4*>(in), ps, scl, mul, a.V, a.np);
   }
   return cudaGetLastError();
 }
@@ -1123,8 +1168,8 @@ cudaError_t smoother_impl(const Geom& g, const float2* U, const float2* C, const
   reduce(1);
   {
     TimedScope ts("mr_scale", s);
-    scale_to_abi<PAIRS, T><<<2048, 256, 0, s>>>(ps, reinterpret_cast<float4*>(psi), scale, a.V,
-                                                a.np);
+    scale_to_abi<PAIRS, T><<<tr_grid(), kTrThreads, tr_smem(a.np, PAIRS), s>>>(
+        ps, reinterpret_cast<float4*>(psi), scale, a.V, a.np);
   }
   return cudaGetLastError();
 }
@@ -1149,8 +1194,8 @@ cudaError_t dirac_impl(const Geom& g, const float2* U, const float2* C, const fl
     fill_kernel<<<1, 64, 0, s>>>(scale, g.m, -1.0f);
   }
   TimedScope ts("mr_scale", s);
-  scale_to_abi<PAIRS, T><<<2048, 256, 0, s>>>(r, reinterpret_cast<float4*>(out), scale, a.V,
-                                              a.np);
+  scale_to_abi<PAIRS, T><<<tr_grid(), kTrThreads, tr_smem(a.np, PAIRS), s>>>(
+      r, reinterpret_cast<float4*>(out), scale, a.V, a.np);
   return cudaGetLastError();
 }
 
