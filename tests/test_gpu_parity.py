@@ -96,6 +96,33 @@ def test_dirac_apply(name):
     assert err.max() <= 1e-6, err.max()
 
 
+@pytest.mark.parametrize("prec", [mg.MG_PREC_FP32, mg.MG_PREC_MIXED_FP16])
+def test_odd_volume_layout_tail(prec):
+    """A volume that is not a multiple of the 4-site tiles of the interface <->
+    slab transposes (3^3 x 5: 135 sites, a last tile of 3) and a timeslice of
+    27 sites (one ragged patch): D psi and 3 MR iterations against the oracle,
+    for FP32 and FP16 slab storage."""
+    dims, m0, xi, m = [3, 3, 3, 5], -0.1, 1.0, 8
+    U = G.round_to_c64(G.gauge_field(dims, 0.3, 31))
+    p0 = G.round_to_c64(G.psi0(dims, m, 32))
+    p = mg.Problem(dims=dims, block=[3, 3, 3, 5], m0=m0, n_vec=m, k=4, mr_iters=3, xi=xi,
+                   precision=prec)
+    ws = mg.workspace(p, mg.MG_CALL_SMOOTH)
+    out = torch.empty(p0.shape, dtype=torch.complex64, device="cuda")
+    mg.mg_apply_dirac(p, to_dev(U), None, to_dev(p0), out, ws)
+    mg.mg_sync_status()
+    ref = O.apply_D(dims, m0, xi, U, None, p0)
+    err = np.linalg.norm((to_host(out) - ref).reshape(-1, m), axis=0) / \
+        np.linalg.norm(ref.reshape(-1, m), axis=0)
+    assert err.max() <= (1e-6 if prec == mg.MG_PREC_FP32 else 4 * U16), err.max()
+    if prec == mg.MG_PREC_FP32:
+        mg.mg_smooth_testvecs(p, to_dev(U), None, to_dev(p0), out, ws)
+        mg.mg_sync_status()
+        ref = O.mr(dims, m0, xi, U, None, p0, 3)
+        err = np.linalg.norm((to_host(out) - ref).reshape(-1, m), axis=0)
+        assert err.max() <= 2e-5, err.max()
+
+
 @pytest.mark.parametrize("N", [1, 2, 3, 5])
 def test_smoother_iteration_counts(N):
     """psi's update waits one iteration and takes two terms; odd and even N end
