@@ -44,6 +44,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "mg_bulk.cuh"
 #include "mg_common.cuh"
 
 namespace mg {
@@ -141,6 +142,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t a, float v[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// two 16-column loads of this thread's TMEM lane, one wait
+__device__ __forceinline__ void tmem_ld16x2(uint32_t a, uint32_t b, float v[16], float w[16]) {
+  uint32_t r[16], q[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(a));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]),
+        "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]),
+        "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+      : "r"(b));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    v[i] = __uint_as_float(r[i]);
+    w[i] = __uint_as_float(q[i]);
+  }
 }
 
 __device__ __forceinline__ void sync_before() {
@@ -733,11 +759,28 @@ struct TcCoarsen {
   float diag;
 };
 
-constexpr int kCsSites = 12;                   // sites per chunk (K = 96: six K steps)
-constexpr int kCsSbo = kCsSites * 128;         // bytes between 8-row groups
-constexpr int kCsTileL = (kTcCols / 8) * kCsSbo;  // L~^T tile: M = 128 (24 KB)
 constexpr float kCsScaleL = 16384.f;           // 2^14
 constexpr float kCsScaleR = 256.f;             // 2^8
+
+// Per-NPAD layout of the coarsening kernel's shared memory:
+//  * one operand tile set: L~^T (hi, lo; M = 128) and R~^T (hi, lo; N = NPAD),
+//    element (real column q, row 8s + e) at (q>>3)*SBO + s*128 + (q&7)*16 + e*2;
+//  * two raw buffers, each the bulk-copied inputs of one chunk: per site the
+//    prolongator rows P(x) [12][k], the neighbour's P(x + mu) [12][k] (hop
+//    passes) and the links U(x) [4][9] (hop passes) or the clover C(x)
+//    [2][6][6] (site passes).
+template <int NPAD>
+struct CsCfg {
+  static constexpr int S = NPAD <= 96 ? 12 : 8;        // sites per chunk (K = 8 S)
+  static constexpr int KMAX = NPAD / 4;                // largest k of this NPAD
+  static constexpr int SBO = S * 128;                  // bytes between 8-row groups
+  static constexpr int TILE_L = (kTcCols / 8) * SBO;   // one 16-bit L~^T tile
+  static constexpr int TILE_R = (NPAD / 8) * SBO;      // one 16-bit R~^T tile
+  static constexpr int TILES = 2 * TILE_L + 2 * TILE_R;
+  static constexpr int PST = 12 * KMAX;                // float2 per site in the P areas
+  static constexpr int EST = 72;                       // float2 per site in the U / C area
+  static constexpr int RAW = S * (2 * PST + EST) * 8;  // bytes of one raw buffer
+};
 
 // Pi_mu's lower-chirality columns: row sp of -B_mu has a single non-zero
 // entry -B_mu[sp][t] = g
@@ -776,23 +819,28 @@ __device__ __forceinline__ int cs_site(const TcCoarsen& a, int j, int mu, int gr
   return x;
 }
 
-// stage chunk: L~^T and R~^T tiles (element (real column q, row 8s + e) at
-// (q>>3)*1024 + s*128 + (q&7)*16 + e*2)
-__device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const int* s_nbr,
+// stage a chunk from its raw buffer into the L~^T and R~^T tiles; s_site[s]
+// < 0 marks a site past the end of the group (zero rows)
+template <int NPAD>
+__device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const float2* raw,
                          unsigned char* lhi, unsigned char* llo, unsigned char* rhi,
                          unsigned char* rlo) {
+  using Cfg = CsCfg<NPAD>;
   const int k = a.k, n2 = 2 * k;
   const int mu = pass - 2;
-  for (int it = threadIdx.x; it < kCsSites * n2; it += blockDim.x) {
+  const float2* rawx = raw;                      // P(x)
+  const float2* rawn = raw + Cfg::S * Cfg::PST;  // P(x + mu)
+  const float2* rawe = rawn + Cfg::S * Cfg::PST; // U(x) or C(x)
+  // items it = r + 256 i with r = (tid + 128) mod 256: the threads that take a
+  // third item are in warps 4 and 5, not in warps 0 and 1, which fetch and issue
+  for (int it = (threadIdx.x + 128) & 255; it < Cfg::S * n2; it += blockDim.x) {
     const int s = it / n2, col = it % n2;
-    const int x = s_site[s];
     float2 Lv[6], Rv[6];
 #pragma unroll
     for (int e = 0; e < 6; ++e) Lv[e] = Rv[e] = make_float2(0.f, 0.f);
     const int al = col / k, i = col % k;
-    if (x >= 0) {
-      const int rowc = 12 * k;  // complex per site of P: [2][6][k]
-      const float2* Px = a.P + (long)x * rowc;
+    if (s_site[s] >= 0) {
+      const float2* Px = rawx + s * Cfg::PST;  // [2][6][k]
       if (mu < 0) {
         if (al == pass) {
 #pragma unroll
@@ -801,7 +849,7 @@ __device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const 
           for (int e = 0; e < 6; ++e) {
             float2 r = cscale(Lv[e], 0.5f * a.diag);
             if (a.C) {
-              const float2* cl = a.C + (long)x * 72 + al * 36 + e * 6;
+              const float2* cl = rawe + s * Cfg::EST + al * 36 + e * 6;
 #pragma unroll
               for (int f = 0; f < 6; ++f) cfma(r, cscale(cl[f], 0.5f), Lv[f]);
             }
@@ -809,8 +857,8 @@ __device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const 
           }
         }
       } else {
-        const float2* Py = a.P + (long)s_nbr[s] * rowc;
-        const float2* u = a.U + (long)x * 36 + mu * 9;
+        const float2* Py = rawn + s * Cfg::PST;
+        const float2* u = rawe + s * Cfg::EST + mu * 9;
 #pragma unroll
         for (int sp = 0; sp < 2; ++sp) {
           int tt;
@@ -844,7 +892,7 @@ __device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const 
     }
     uint4 lhr, llr, lhm, llm, rhr, rlr, rhm, rlm;
     const int q = 2 * col;
-    const uint32_t o0 = (q >> 3) * kCsSbo + s * 128 + (q & 7) * 16;
+    const uint32_t o0 = (q >> 3) * Cfg::SBO + s * 128 + (q & 7) * 16;
     split8<TC_FP16X3>(lre, kCsScaleL, lhr, llr);
     split8<TC_FP16X3>(lim, kCsScaleL, lhm, llm);
     split8<TC_FP16X3>(rre, kCsScaleR, rhr, rlr);
@@ -864,30 +912,100 @@ __device__ void cs_stage(const TcCoarsen& a, int pass, const int* s_site, const 
   }
 }
 
+// The chunk sequence of a CTA: blocks j = blockIdx.x, blockIdx.x + gridDim.x,
+// ...; per block the site passes 0 and 1 and, per direction mu, the sites off
+// the +mu face (group 0) and on it (group 1); per group, chunks of S sites.
+struct CsChunk {
+  int j, pass, grp, c0, cnt;
+};
+__device__ __forceinline__ int cs_count(const TcCoarsen& a, int pass, int grp) {
+  const int mu = pass - 2;
+  return mu < 0 ? a.nb : (grp == 0 ? a.nb - a.nb / a.b[mu] : a.nb / a.b[mu]);
+}
+template <int S>
+__device__ __forceinline__ void cs_advance(const TcCoarsen& a, CsChunk& c) {
+  c.c0 += S;
+  while (c.j < a.nblk && c.c0 >= c.cnt) {
+    c.c0 = 0;
+    if (c.pass >= 2 && c.grp == 0) {
+      c.grp = 1;
+    } else {
+      c.grp = 0;
+      if (++c.pass == 6) {
+        c.pass = 0;
+        c.j += gridDim.x;
+      }
+    }
+    c.cnt = cs_count(a, c.pass, c.grp);
+  }
+}
+__device__ __forceinline__ CsChunk cs_begin(const TcCoarsen& a) {
+  return CsChunk{(int)blockIdx.x, 0, 0, 0, cs_count(a, 0, 0)};
+}
+
+// warp 0: the sites of chunk c into s_site and the chunk's bulk copies into
+// the raw buffer, completing on bar (lane s handles site s)
+template <int NPAD>
+__device__ void cs_fetch(const TcCoarsen& a, const CsChunk& c, int* s_site, float2* raw,
+                         unsigned long long* bar) {
+  using Cfg = CsCfg<NPAD>;
+  const int lane = threadIdx.x & 31;
+  const int mu = c.pass - 2;
+  int x = -1, nbr = -1;
+  if (lane < Cfg::S && c.c0 + lane < c.cnt) x = cs_site(a, c.j, mu, c.grp, c.c0 + lane, &nbr);
+  if (lane < Cfg::S) s_site[lane] = x;
+  const uint32_t pbytes = 12u * a.k * sizeof(float2);
+  const uint32_t ebytes = mu >= 0 ? 36u * sizeof(float2) : (a.C ? 72u * sizeof(float2) : 0u);
+  const uint32_t per_site = pbytes + (mu >= 0 ? pbytes : 0u) + ebytes;
+  const int nvalid = __popc(__ballot_sync(0xffffffffu, x >= 0));
+  if (lane == 0) mbar_expect_tx(bar, (uint32_t)nvalid * per_site);
+  __syncwarp();
+  if (x >= 0) {
+    float2* rawx = raw;
+    float2* rawn = raw + Cfg::S * Cfg::PST;
+    float2* rawe = rawn + Cfg::S * Cfg::PST;
+    bulk_g2s(rawx + lane * Cfg::PST, a.P + (long)x * 12 * a.k, pbytes, bar);
+    if (mu >= 0) {
+      bulk_g2s(rawn + lane * Cfg::PST, a.P + (long)nbr * 12 * a.k, pbytes, bar);
+      bulk_g2s(rawe + lane * Cfg::EST, a.U + (long)x * 36, ebytes, bar);
+    } else if (a.C) {
+      bulk_g2s(rawe + lane * Cfg::EST, a.C + (long)x * 72, ebytes, bar);
+    }
+  }
+}
+
 template <int NPAD>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_coarsen_kernel(TcCoarsen a,
                                                                    int* __restrict__ status) {
+  using Cfg = CsCfg<NPAD>;
   constexpr int NH = NPAD / 2;                        // columns per thread
   constexpr int TCOLS = 4 * NPAD <= 256 ? 256 : 512;  // (D1, D2) x 2 slots
-  constexpr int kTileR = (NPAD / 8) * kCsSbo;
-  constexpr int kBuf = 2 * kCsTileL + 2 * kTileR;     // one staging buffer
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  float2* Ms = reinterpret_cast<float2*>(tc_smem + 2 * kBuf);  // [2k][2k + 1]
-  __shared__ __align__(8) unsigned long long bar[2];
+  unsigned char* lhi = tc_smem;  // one tile set; between chunks it also holds Ms
+  unsigned char* llo = lhi + Cfg::TILE_L;
+  unsigned char* rhi = llo + Cfg::TILE_L;
+  unsigned char* rlo = rhi + Cfg::TILE_R;
+  auto raw = [&](int b) { return reinterpret_cast<float2*>(tc_smem + Cfg::TILES + b * Cfg::RAW); };
+  float2* Ms = reinterpret_cast<float2*>(tc_smem);  // [2k][2k + 1]
+  __shared__ __align__(8) unsigned long long mma_bar;
+  __shared__ __align__(8) unsigned long long raw_bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
-  __shared__ int s_site[2][kCsSites], s_nbr[2][kCsSites];
+  __shared__ int s_site[2][Cfg::S];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = a.k, n2 = 2 * k;
   const int half = warp >> 2;
-  // zero both staging buffers once: padding rows (real columns >= 4k) are never written
-  for (int i = threadIdx.x; i < 2 * kBuf / 16; i += blockDim.x)
+  // zero the tiles once.  The padding (real columns >= 4k of L~ and R~) is
+  // never staged; between passes Ms may leave stale values there, which only
+  // reach rows and columns of the product that are never read.
+  for (int i = threadIdx.x; i < Cfg::TILES / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(tc_smem)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 0) tmem_alloc(&tmem_base, TCOLS);
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init(&mma_bar, 1);
+    mbar_init(&raw_bar[0], 1);
+    mbar_init(&raw_bar[1], 1);
+    mbar_fence_init();
     s_abort = 0;
   }
   sync_before();
@@ -898,7 +1016,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_coarsen_kernel(TcCoarsen a,
   const uint32_t idesc = idesc_f16(NPAD, 0);
   const float inv = 1.f / (kCsScaleL * kCsScaleR);
   float Sr[NH], Yr[NH];
-  int gidx = 0;
 
   // add the chunk in TMEM slot d to Sr (to_y = 0) or Yr
   auto add_chunk = [&](int d, int to_y) {
@@ -907,8 +1024,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_coarsen_kernel(TcCoarsen a,
     for (int cb = 0; cb < NH / 16; ++cb) {
       float v1[16], v2[16];
       const uint32_t ad = taddr + lane_base + d * 2 * NPAD + half * NH + cb * 16;
-      tmem_ld16(ad, v1);
-      tmem_ld16(ad + NPAD, v2);
+      tmem_ld16x2(ad, ad + NPAD, v1, v2);
 #pragma unroll
       for (int t = 0; t < 16; ++t) {
         if (to_y) Yr[cb * 16 + t] += v1[t] + v2[t];
@@ -932,114 +1048,120 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_coarsen_kernel(TcCoarsen a,
     }
   };
 
-  for (int j = blockIdx.x; j < a.nblk && !s_abort; j += gridDim.x) {
-#pragma unroll
-    for (int t = 0; t < NH; ++t) Sr[t] = 0.f;
-    int pend = -1, pend_y = 0;  // TMEM slot awaiting its epilogue, and its target
-    for (int pass = 0; pass < 6 && !s_abort; ++pass) {
-      const int mu = pass - 2;
-#pragma unroll
-      for (int t = 0; t < NH; ++t) Yr[t] = 0.f;
-      for (int grp = 0; grp < (mu < 0 ? 1 : 2) && !s_abort; ++grp) {
-        const int cnt = mu < 0 ? a.nb : (grp == 0 ? a.nb - a.nb / a.b[mu] : a.nb / a.b[mu]);
-        for (int c0 = 0; c0 < cnt; c0 += kCsSites, ++gidx) {
-          const int b = gidx & 1;
-          unsigned char* lhi = tc_smem + b * kBuf;
-          unsigned char* llo = lhi + kCsTileL;
-          unsigned char* rhi = llo + kCsTileL;
-          unsigned char* rlo = rhi + kTileR;
-          if (gidx >= 2 && !bar_wait(&bar[b], (gidx - 2) >> 1)) s_abort = 1;
-          if (threadIdx.x < kCsSites) {
-            const int t = c0 + threadIdx.x;
-            int nb_ = -1;
-            s_site[b][threadIdx.x] = t < cnt ? cs_site(a, j, mu, grp, t, &nb_) : -1;
-            s_nbr[b][threadIdx.x] = nb_;
-          }
-          __syncthreads();
-          if (s_abort) break;
-          cs_stage(a, pass, s_site[b], s_nbr[b], lhi, llo, rhi, rlo);
-          fence_async();
-          sync_before();
-          __syncthreads();
-          if (threadIdx.x == 0) {
-            sync_after();
-            const uint32_t d1 = taddr + b * 2 * NPAD, d2 = d1 + NPAD;
-#pragma unroll
-            for (int kk = 0; kk < kCsSites / 2; ++kk) {
-              const uint64_t dlh = smem_desc(su32(lhi) + kk * 256, 128, kCsSbo);
-              const uint64_t dll = smem_desc(su32(llo) + kk * 256, 128, kCsSbo);
-              const uint64_t drh = smem_desc(su32(rhi) + kk * 256, 128, kCsSbo);
-              const uint64_t drl = smem_desc(su32(rlo) + kk * 256, 128, kCsSbo);
-              mma(d1, dlh, drh, idesc, kk > 0 ? 1u : 0u);
-              mma(d2, dlh, drl, idesc, kk > 0 ? 1u : 0u);
-              mma(d2, dll, drh, idesc, 1u);
-            }
-            commit(&bar[b]);
-          }
-          if (pend >= 0) {
-            if (!bar_wait(&bar[pend], (gidx - 1) >> 1)) s_abort = 1;
-            __syncthreads();
-            if (s_abort) break;
-            add_chunk(pend, pend_y);
-          }
-          pend = b;
-          pend_y = mu >= 0 && grp == 1;
-          sync_before();
-          __syncthreads();
-        }
-      }
-      if (s_abort) break;
-      if (mu >= 0) {
-        // drain, then Y_{+mu}(j) and Y_{-mu}(j + mu) = sigma_3 Y_{+mu}(j)^dag sigma_3
-        if (pend >= 0) {
-          if (!bar_wait(&bar[pend], (gidx - 1) >> 1)) s_abort = 1;
-          __syncthreads();
-          if (s_abort) break;
-          add_chunk(pend, pend_y);
-          pend = -1;
-        }
-        to_ms(true);
-        __syncthreads();
-        int jc[4];
-        {
-          int u = j;
-          jc[0] = u % a.Lc[0]; u /= a.Lc[0];
-          jc[1] = u % a.Lc[1]; u /= a.Lc[1];
-          jc[2] = u % a.Lc[2]; jc[3] = u / a.Lc[2];
-        }
-        jc[mu] = (jc[mu] + 1) % a.Lc[mu];
-        const int jn = jc[0] + a.Lc[0] * (jc[1] + a.Lc[1] * (jc[2] + a.Lc[2] * jc[3]));
-        for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
-          const int r = idx / n2, c = idx % n2;
-          a.Y[(((long)j * 8 + mu) * n2 + r) * n2 + c] = Ms[r * (n2 + 1) + c];
-          float2 v = cconj(Ms[c * (n2 + 1) + r]);
-          if ((r < k) != (c < k)) v = make_float2(-v.x, -v.y);
-          a.Y[(((long)jn * 8 + 4 + mu) * n2 + r) * n2 + c] = v;
-        }
-        sync_before();
-        __syncthreads();
-      }
+  // Chunk g: its inputs arrive in raw buffer g & 1 (fetched two chunks
+  // ahead by warp 0), it is staged into the one tile set once the MMAs of
+  // chunk g-1 are done, multiplied into TMEM slot g & 1, and added to the
+  // registers one chunk later (or at once when it ends a pass).
+  CsChunk cur = cs_begin(a), pre = cur;
+  int issued = 0;  // chunks whose raw buffer was fetched
+  if (warp == 0) {
+    for (; issued < 2 && pre.j < a.nblk; ++issued) {
+      cs_fetch<NPAD>(a, pre, s_site[issued], raw(issued), &raw_bar[issued]);
+      cs_advance<Cfg::S>(a, pre);
     }
+  }
+  int pend = -1, pend_y = 0;  // TMEM slot awaiting its addition, and its target
+#pragma unroll
+  for (int t = 0; t < NH; ++t) Sr[t] = Yr[t] = 0.f;
+  int g = 0, committed = 0;
+  for (; cur.j < a.nblk; ++g) {
+    const int b = g & 1;
+    const int mu = cur.pass - 2;
+    bool ok = mbar_wait(&raw_bar[b], (uint32_t)((g >> 1) & 1));
+    if (g >= 1) ok = bar_wait(&mma_bar, g - 1) && ok;
+    if (!ok) s_abort = 1;
+    __syncthreads();  // s_site[b] (written by warp 0) and s_abort visible
     if (s_abort) break;
-    if (pend >= 0) {
-      if (!bar_wait(&bar[pend], (gidx - 1) >> 1)) s_abort = 1;
+    sync_after();
+    cs_stage<NPAD>(a, cur.pass, s_site[b], raw(b), lhi, llo, rhi, rlo);
+    fence_async();
+    sync_before();
+    __syncthreads();
+    if (threadIdx.x == 32) {
+      sync_after();
+      const uint32_t d1 = taddr + b * 2 * NPAD, d2 = d1 + NPAD;
+#pragma unroll
+      for (int kk = 0; kk < Cfg::S / 2; ++kk) {
+        const uint64_t dlh = smem_desc(su32(lhi) + kk * 256, 128, Cfg::SBO);
+        const uint64_t dll = smem_desc(su32(llo) + kk * 256, 128, Cfg::SBO);
+        const uint64_t drh = smem_desc(su32(rhi) + kk * 256, 128, Cfg::SBO);
+        const uint64_t drl = smem_desc(su32(rlo) + kk * 256, 128, Cfg::SBO);
+        mma(d1, dlh, drh, idesc, kk > 0 ? 1u : 0u);
+        mma(d2, dlh, drl, idesc, kk > 0 ? 1u : 0u);
+        mma(d2, dll, drh, idesc, 1u);
+      }
+      commit(&mma_bar);
+    }
+    committed = g + 1;
+    // raw buffer b is free again: fetch chunk g + 2 into it
+    if (warp == 0 && pre.j < a.nblk) {
+      cs_fetch<NPAD>(a, pre, s_site[b], raw(b), &raw_bar[b]);
+      cs_advance<Cfg::S>(a, pre);
+      ++issued;
+    }
+    // chunk g-1's MMAs were waited for above
+    if (pend >= 0) add_chunk(pend, pend_y);
+    pend = b;
+    pend_y = mu >= 0 && cur.grp == 1;
+    const bool pass_end = cur.c0 + Cfg::S >= cur.cnt && (mu < 0 || cur.grp == 1);
+    const int j = cur.j;
+    cs_advance<Cfg::S>(a, cur);
+    const bool block_end = cur.j != j;
+    if (mu >= 0 && pass_end) {
+      // drain, then Y_{+mu}(j) and Y_{-mu}(j + mu) = sigma_3 Y_{+mu}(j)^dag sigma_3
+      if (!bar_wait(&mma_bar, g)) s_abort = 1;
       __syncthreads();
       if (s_abort) break;
       add_chunk(pend, pend_y);
-    }
-    // X = S + sigma_3 S^dag sigma_3
-    to_ms(false);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
-      const int r = idx / n2, c = idx % n2;
-      float2 v = cconj(Ms[c * (n2 + 1) + r]);
-      if ((r < k) != (c < k)) v = make_float2(-v.x, -v.y);
-      a.X[((long)j * n2 + r) * n2 + c] = cadd(Ms[r * (n2 + 1) + c], v);
+      pend = -1;
+      sync_before();
+      to_ms(true);  // Ms overlays the tiles, which the finished MMAs no longer read
+      __syncthreads();
+      int jc[4];
+      {
+        int u = j;
+        jc[0] = u % a.Lc[0]; u /= a.Lc[0];
+        jc[1] = u % a.Lc[1]; u /= a.Lc[1];
+        jc[2] = u % a.Lc[2]; jc[3] = u / a.Lc[2];
+      }
+      jc[mu] = (jc[mu] + 1) % a.Lc[mu];
+      const int jn = jc[0] + a.Lc[0] * (jc[1] + a.Lc[1] * (jc[2] + a.Lc[2] * jc[3]));
+      for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
+        const int r = idx / n2, c = idx % n2;
+        a.Y[(((long)j * 8 + mu) * n2 + r) * n2 + c] = Ms[r * (n2 + 1) + c];
+        float2 v = cconj(Ms[c * (n2 + 1) + r]);
+        if ((r < k) != (c < k)) v = make_float2(-v.x, -v.y);
+        a.Y[(((long)jn * 8 + 4 + mu) * n2 + r) * n2 + c] = v;
+      }
+#pragma unroll
+      for (int t = 0; t < NH; ++t) Yr[t] = 0.f;
+      __syncthreads();  // Ms read before the next chunk's staging overwrites the tiles
+      if (block_end) {
+        // X = S + sigma_3 S^dag sigma_3
+        to_ms(false);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
+          const int r = idx / n2, c = idx % n2;
+          float2 v = cconj(Ms[c * (n2 + 1) + r]);
+          if ((r < k) != (c < k)) v = make_float2(-v.x, -v.y);
+          a.X[((long)j * n2 + r) * n2 + c] = cadd(Ms[r * (n2 + 1) + c], v);
+        }
+#pragma unroll
+        for (int t = 0; t < NH; ++t) Sr[t] = 0.f;
+        __syncthreads();
+      }
     }
     sync_before();
     __syncthreads();
   }
-  if (s_abort && threadIdx.x == 0 && gidx > 0) (void)bar_wait(&bar[(gidx - 1) & 1], (gidx - 1) >> 1);
+  if (s_abort) {
+    // let the copies and the matrix multiplies still in flight finish before
+    // the CTA's shared memory and TMEM are released
+    if (threadIdx.x == 0) {
+      for (int h = g; h < issued; ++h) (void)mbar_wait(&raw_bar[h & 1], (uint32_t)((h >> 1) & 1));
+      if (committed > 0) (void)bar_wait(&mma_bar, committed - 1);
+    }
+  }
   sync_before();
   __syncthreads();
   if (warp == 0) {
@@ -1050,9 +1172,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_coarsen_kernel(TcCoarsen a,
 }
 
 template <int NPAD>
-size_t cs_smem(int k) {
-  return (size_t)2 * (2 * kCsTileL + 2 * (NPAD / 8) * kCsSbo) +
-         sizeof(float2) * (size_t)(2 * k) * (2 * k + 1);
+size_t cs_smem(int) {
+  using Cfg = CsCfg<NPAD>;
+  return (size_t)Cfg::TILES + 2 * (size_t)Cfg::RAW;
 }
 
 int num_sms() {
