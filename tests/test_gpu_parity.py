@@ -377,19 +377,19 @@ def _galerkin_identity(c, P, X, Y, nprobe=4, tol=1e-6):
 #     coarse space (their mean) within 1% of the FP64 oracle's.
 # ---------------------------------------------------------------------------
 U16 = 2.0 ** -11
-MIXED_CASES = ["8^4 clover m'=48 k=24", "8^3x16 aniso m'=64 k=24"]
+FP16_STORAGE_CASES = ["8^4 clover m'=48 k=24", "8^3x16 aniso m'=64 k=24"]
 
 
-def _mixed(c):
+def _fp16_storage(c):
     p = c["prob"]
     return mg.Problem(dims=p.dims, block=p.block, m0=p.m0, n_vec=p.n_vec, k=p.k,
                       mr_iters=p.mr_iters, csw=p.csw, xi=p.xi, precision=mg.MG_PREC_MIXED_FP16)
 
 
-@pytest.mark.parametrize("name", MIXED_CASES)
+@pytest.mark.parametrize("name", FP16_STORAGE_CASES)
 def test_fp16_storage_dirac_apply(name):
     c = _case(name)
-    p = _mixed(c)
+    p = _fp16_storage(c)
     U, C = _dev(c)
     vin = to_dev(c["p0"])
     out = torch.empty_like(vin)
@@ -405,10 +405,10 @@ def test_fp16_storage_dirac_apply(name):
         0.6 * mg.mg_workspace_size(c["prob"], mg.MG_CALL_SMOOTH)
 
 
-@pytest.mark.parametrize("name", MIXED_CASES)
+@pytest.mark.parametrize("name", FP16_STORAGE_CASES)
 def test_fp16_storage_smoother_and_end_to_end(name):
     c = _case(name)
-    p = _mixed(c)
+    p = _fp16_storage(c)
     k = c["k"]
     U, C = _dev(c)
     # a per-vector scale of the starts changes nothing (MR is scale invariant
