@@ -269,42 +269,88 @@ __global__ void __launch_bounds__(256, 2) coarsen_kernel(CoarsenArgs a) {
 }
 
 // out(xc) = X v(xc) + sum_d Y[d] v(xc + mu_d) + Y[4+d] v(xc - mu_d)
-// One CTA per coarse site; thread (row, rhs); the nine source vectors are
-// staged in shared memory.
-__global__ void coarse_apply_kernel(const float2* __restrict__ X, const float2* __restrict__ Y,
-                                    const float2* __restrict__ vin, float2* __restrict__ vout,
-                                    int Lc0, int Lc1, int Lc2, int Lc3, int n2, int nrhs) {
+// One CTA per coarse site; the nine source vectors are staged in shared
+// memory.  A group of kApLanes consecutive lanes owns one output row: lane j
+// of the group takes the columns b = j, j + kApLanes, ... of that row of each
+// of the nine matrices, so the group reads a matrix row contiguously and every
+// matrix entry, loaded once, multiplies kApRhs right-hand sides.  The group's
+// partial sums are added by two shuffles in a fixed order (deterministic).
+// Each warp covers 32 / kApLanes consecutive rows per trip, with the same trip
+// count on all its lanes, so the shuffles always run on the full warp.
+constexpr int kApLanes = 4;
+constexpr int kApRhs = 8;  // right-hand sides per register pass
+__global__ void __launch_bounds__(256) coarse_apply_kernel(const float2* __restrict__ X,
+                                                           const float2* __restrict__ Y,
+                                                           const float2* __restrict__ vin,
+                                                           float2* __restrict__ vout, int Lc0,
+                                                           int Lc1, int Lc2, int Lc3, int n2,
+                                                           int nrhs) {
   extern __shared__ float2 vs[];  // [9][n2][nrhs]
   const int xc = blockIdx.x;
-  const int Lc[4] = {Lc0, Lc1, Lc2, Lc3};
-  int c[4];
+  int c0, c1, c2, c3;
   {
     int t = xc;
-    c[0] = t % Lc0; t /= Lc0;
-    c[1] = t % Lc1; t /= Lc1;
-    c[2] = t % Lc2; c[3] = t / Lc2;
+    c0 = t % Lc0; t /= Lc0;
+    c1 = t % Lc1; t /= Lc1;
+    c2 = t % Lc2; c3 = t / Lc2;
   }
   const int per = n2 * nrhs;
+#pragma unroll
   for (int d = 0; d < 9; ++d) {
-    int src = xc;
+    // term d: the site itself (d = 0), its +mu (d = 1..4) or -mu (d = 5..8) neighbour
+    // (a step of -1 is taken as L - 1 modulo L)
+    const int mu = (d + 3) % 4;
+    int a0 = c0, a1 = c1, a2 = c2, a3 = c3;
     if (d > 0) {
-      const int mu = (d - 1) % 4, st = d <= 4 ? 1 : -1;
-      int cc[4] = {c[0], c[1], c[2], c[3]};
-      cc[mu] = (cc[mu] + st + Lc[mu]) % Lc[mu];
-      src = cc[0] + Lc0 * (cc[1] + Lc1 * (cc[2] + Lc2 * cc[3]));
+      if (mu == 0) a0 = (c0 + (d <= 4 ? 1 : Lc0 - 1)) % Lc0;
+      if (mu == 1) a1 = (c1 + (d <= 4 ? 1 : Lc1 - 1)) % Lc1;
+      if (mu == 2) a2 = (c2 + (d <= 4 ? 1 : Lc2 - 1)) % Lc2;
+      if (mu == 3) a3 = (c3 + (d <= 4 ? 1 : Lc3 - 1)) % Lc3;
     }
+    const int src = a0 + Lc0 * (a1 + Lc1 * (a2 + Lc2 * a3));
     for (int i = threadIdx.x; i < per; i += blockDim.x) vs[d * per + i] = vin[(long)src * per + i];
   }
   __syncthreads();
-  for (int o = threadIdx.x; o < per; o += blockDim.x) {
-    const int row = o / nrhs, r = o % nrhs;
-    float2 s = make_float2(0.f, 0.f);
-    for (int d = 0; d < 9; ++d) {
-      const float2* M = d == 0 ? X + (long)xc * n2 * n2 : Y + ((long)xc * 8 + d - 1) * n2 * n2;
-      const float2* v = vs + d * per;
-      for (int b = 0; b < n2; ++b) cfma(s, __ldg(M + row * n2 + b), v[b * nrhs + r]);
+  constexpr int kGroupsPerWarp = 32 / kApLanes;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = lane % kApLanes, gw = lane / kApLanes;
+  const int nwarp = blockDim.x >> 5;
+  const long site = (long)xc * n2 * n2;
+  for (int row0 = warp * kGroupsPerWarp; row0 < n2; row0 += nwarp * kGroupsPerWarp) {
+    const int row = row0 + gw;
+    const bool active = row < n2;
+    for (int r0 = 0; r0 < nrhs; r0 += kApRhs) {
+      float2 s[kApRhs];
+#pragma unroll
+      for (int r = 0; r < kApRhs; ++r) s[r] = make_float2(0.f, 0.f);
+      if (active) {
+        for (int d = 0; d < 9; ++d) {
+          const float2* M = (d == 0 ? X + site : Y + ((long)xc * 8 + d - 1) * n2 * n2) +
+                            (long)row * n2;
+          const float2* v = vs + d * per + r0;
+#pragma unroll 4
+          for (int b = j; b < n2; b += kApLanes) {
+            const float2 m = __ldg(M + b);
+#pragma unroll
+            for (int r = 0; r < kApRhs; ++r)
+              if (r0 + r < nrhs) cfma(s[r], m, v[b * nrhs + r]);
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kApRhs; ++r) {
+#pragma unroll
+        for (int off = 1; off < kApLanes; off <<= 1) {
+          s[r].x += __shfl_xor_sync(0xffffffffu, s[r].x, off);
+          s[r].y += __shfl_xor_sync(0xffffffffu, s[r].y, off);
+        }
+      }
+      if (active && j == 0) {
+#pragma unroll
+        for (int r = 0; r < kApRhs; ++r)
+          if (r0 + r < nrhs) vout[((long)xc * n2 + row) * nrhs + r0 + r] = s[r];
+      }
     }
-    vout[(long)xc * per + o] = s;
   }
 }
 
