@@ -78,16 +78,6 @@ __device__ __forceinline__ int site_of(const CoarsenArgs& a, int j, int loc, int
   return xo[0] + a.L[0] * (xo[1] + a.L[1] * (xo[2] + a.L[2] * xo[3]));
 }
 
-// complex value of B_mu[s][t]
-__device__ __forceinline__ float2 bent(int mu, int s, int t) {
-  if (mu == 0) return s != t ? make_float2(0.f, -1.f) : make_float2(0.f, 0.f);
-  if (mu == 1) return s == 0 && t == 1 ? make_float2(-1.f, 0.f)
-                    : (s == 1 && t == 0 ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f));
-  if (mu == 2) return s != t ? make_float2(0.f, 0.f)
-                             : (s == 0 ? make_float2(0.f, -1.f) : make_float2(0.f, 1.f));
-  return s == t ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
-}
-
 // Coarsening as register-tiled complex GEMMs.  One CTA (16 x 16 threads) per
 // block j.  Thread (ti, tj) owns the T x T output entries
 // (a*16 + ti, b*16 + tj), a, b < T, of every 2k x 2k matrix (2k <= 16 T).
