@@ -182,7 +182,10 @@ mg_status mg_coarsen(const mg_problem* prob, const void* U, const void* C, const
 /* Coarse operator apply: out(xc) = X v(xc) + sum_{d<4} Y[d] v(xc + mu_d)
  * + Y[4+d] v(xc - mu_d) on the periodic coarse lattice dims/block.
  * In: X, Y, v_in [nc][2k][nrhs].  Out: v_out (must not alias v_in).
- * 1 <= nrhs <= 64. */
+ * 1 <= nrhs <= 64, and the nine source vectors of a coarse site,
+ * 9 x 2k x nrhs complex64, must fit the 200000 bytes the call stages in
+ * shared memory (nrhs <= 57 at k = 24, <= 43 at k = 32); a larger request is
+ * rejected with MG_ERR_UNSUPPORTED before anything is launched. */
 mg_status mg_coarse_apply(const mg_problem* prob, const void* X, const void* Y,
                           const void* v_in, void* v_out, int32_t nrhs, void* stream);
 

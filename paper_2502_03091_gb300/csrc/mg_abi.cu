@@ -427,6 +427,10 @@ mg_status mg_coarsen(const mg_problem* prob, const void* U, const void* C, const
                      "mg_coarsen");
 }
 
+// shared memory the coarse apply may stage per coarse site: the launch limit
+// that launch_coarse_apply (mg_coarsen.cu) sets for its kernel
+constexpr size_t kCoarseApplyMaxStage = 200000;
+
 mg_status mg_coarse_apply(const mg_problem* prob, const void* X, const void* Y,
                           const void* v_in, void* v_out, int32_t nrhs, void* stream) {
   Geom g;
@@ -435,6 +439,14 @@ mg_status mg_coarse_apply(const mg_problem* prob, const void* X, const void* Y,
   if (!X || !Y || !v_in || !v_out) return fail(MG_ERR_INVALID, "mg_coarse_apply: NULL array");
   if (nrhs < 1 || nrhs > 64) return fail(MG_ERR_INVALID, "nrhs = %d must be in [1, 64]", nrhs);
   if (v_in == v_out) return fail(MG_ERR_INVALID, "mg_coarse_apply: v_out aliases v_in");
+  // the nine source vectors of a coarse site are staged in shared memory
+  const size_t stage = sizeof(float2) * 9 * (size_t)(2 * g.k) * nrhs;
+  if (stage > kCoarseApplyMaxStage)
+    return fail(MG_ERR_UNSUPPORTED,
+                "mg_coarse_apply: 9 x 2k x nrhs = %zu complex numbers exceed the %zu bytes of "
+                "staging (nrhs <= %zu at k = %d)",
+                stage / sizeof(float2), kCoarseApplyMaxStage,
+                kCoarseApplyMaxStage / (sizeof(float2) * 9 * (size_t)(2 * g.k)), g.k);
   return cuda_status(launch_coarse_apply(g, static_cast<const float2*>(X),
                                          static_cast<const float2*>(Y),
                                          static_cast<const float2*>(v_in),

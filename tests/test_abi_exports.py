@@ -52,6 +52,18 @@ def test_version_and_validation(lib):
     assert st == 1 and b"NULL" in lib.mg_last_error()
     st = lib.mg_coarse_apply(ctypes.byref(pc), None, None, None, None, 8, None)
     assert st == 1
+    # a coarse apply whose nine staged source vectors (9 x 2k x nrhs complex64)
+    # exceed the 200000 bytes of shared memory is refused before any launch
+    # (the pointers are never dereferenced: validation fails first)
+    fake = [ctypes.c_void_p(256 * (i + 1)) for i in range(4)]
+    big = mg.Problem(dims=[8, 8, 8, 16], block=[4, 4, 4, 8], m0=0.0, n_vec=64, k=24,
+                     mr_iters=2).c()
+    st = lib.mg_coarse_apply(ctypes.byref(big), *fake, 58, None)
+    assert st == 7 and b"nrhs <= 57" in lib.mg_last_error()
+    big = mg.Problem(dims=[8, 8, 8, 16], block=[4, 4, 4, 8], m0=0.0, n_vec=64, k=32,
+                     mr_iters=2).c()
+    st = lib.mg_coarse_apply(ctypes.byref(big), *fake, 44, None)
+    assert st == 7 and b"nrhs <= 43" in lib.mg_last_error()
 
 
 def test_coarse_level_validation(lib):
