@@ -75,8 +75,10 @@ typedef enum {
   MG_ERR_SHAPE = 2,       /* dims not divisible by block, k out of range, ... */
   MG_ERR_NOMEM = 3,       /* reserved: the library itself never allocates */
   MG_ERR_CUDA = 4,        /* a CUDA launch or runtime call failed */
-  MG_ERR_NUMERICAL = 5,   /* reserved for host-visible numerical failure */
-  MG_ERR_TIMEOUT = 6,     /* reserved for bounded device waits */
+  MG_ERR_NUMERICAL = 5,   /* reserved: numerical trouble of a block is reported per block
+                             in blk_flags, not by a call's status */
+  MG_ERR_TIMEOUT = 6,     /* a bounded device wait gave up (returned by mg_sync_status
+                             and mg_solve); the outputs of the calls it covers are not valid */
   MG_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
 } mg_status;
 
@@ -84,12 +86,13 @@ typedef enum {
   MG_PREC_FP32 = 0,       /* complex64 storage, FP32 arithmetic on the CUDA cores; the
                              small Cholesky / R-factor eigen problems in double-float
                              (pairs of FP32, ~2^-44 relative) */
-  MG_PREC_MIXED = 1,      /* the smoother as MG_PREC_FP32; the truncation's dense
-                             contractions on the tensor cores with FP32 accumulation:
-                             the first Gram (only the preconditioner of CholeskyQR2's
-                             second pass) in BF16, the second Gram, Q1 = A R1^-1 and
-                             U_k with FP16 operands split into hi + lo parts (three
-                             products, about FP32 accuracy, a power-of-two scale per
+  MG_PREC_MIXED = 1,      /* the smoother as MG_PREC_FP32; the dense contractions of
+                             the truncation and of the Galerkin coarsening on the tensor
+                             cores with FP32 accumulation: the first Gram (only the
+                             preconditioner of CholeskyQR2's second pass) in BF16; the
+                             second Gram, Q1 = A R1^-1, U_k and the coarse-link products
+                             with FP16 operands split into hi + lo parts (three products,
+                             about FP32 accuracy, a power-of-two scale per block or
                              block-chirality); double-float Cholesky / R-factor eigen
                              problem.
                              Results agree with the FP64 reference as closely as the
