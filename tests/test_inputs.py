@@ -68,3 +68,28 @@ def test_stencil_operator_structure_and_chunking():
     s3 = np.tile(np.r_[np.ones(nc), -np.ones(nc)], V)
     H = s3[:, None] * D
     assert np.abs(H - H.conj().T).max() < 1e-12
+
+
+def test_splitmix64_published_sequence():
+    """SplitMix64 from state 0 (the state advances by the golden gamma
+    0x9E3779B97F4A7C15 per step) gives the generator's published first
+    outputs."""
+    gamma = 0x9E3779B97F4A7C15
+    states = np.array([0, gamma, (2 * gamma) % 2 ** 64], dtype=np.uint64)
+    got = [int(v) for v in G.splitmix64(states)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_uniforms_and_normals_distribution():
+    """Uniforms lie strictly inside (0, 1) with mean 1/2 and variance 1/12;
+    the Box-Muller normals have mean 0, variance 1 and fourth moment 3
+    (bounds: five standard errors of each sample moment)."""
+    n = 1 << 20
+    u = G.uniforms(7, G.STREAM_MISC, 0, n)
+    assert u.min() > 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 5 * np.sqrt(1 / 12 / n)
+    assert abs(u.var() - 1 / 12) < 5 * np.sqrt(1 / 180 / n)
+    z = G.normals(7, G.STREAM_MISC, 0, n)
+    assert abs(z.mean()) < 5 / np.sqrt(n)
+    assert abs(z.var() - 1.0) < 5 * np.sqrt(2 / n)
+    assert abs(np.mean(z ** 4) - 3.0) < 5 * np.sqrt(96 / n)
