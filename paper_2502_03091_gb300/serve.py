@@ -23,7 +23,7 @@ import collections
 import math
 import time
 from dataclasses import dataclass, field
-from typing import Dict, List, Optional
+from typing import Dict, List
 
 from . import mg
 
