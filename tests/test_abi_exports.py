@@ -124,3 +124,59 @@ def test_solve_validation(lib):
     st = lib.mg_solve(ctypes.byref(h), None, None, 4, 1e-5, 16, 10, ctypes.byref(it), rel, None,
                       0, None)
     assert st == 1
+
+
+@pytest.mark.parametrize("bad, status, msg", [
+    (dict(dims=[4, 4, 4, 0]), 2, "must be >= 1"),
+    (dict(block=[2, 2, 2, 0]), 2, "must be >= 1"),
+    (dict(block=[4, 4, 4, 3]), 2, "does not divide"),
+    (dict(n_vec=0), 7, "n_vec"),
+    (dict(n_vec=6), 7, "n_vec"),
+    (dict(n_vec=68), 7, "n_vec"),
+    (dict(k=0), 2, "k ="),
+    (dict(k=9), 2, "k ="),
+    (dict(xi=0.0), 1, "xi"),
+    (dict(xi=float("nan")), 1, "xi"),
+    (dict(precision=3), 7, "precision"),
+    (dict(block=[1, 1, 1, 1], n_vec=8, k=4), 2, "rows"),
+])
+def test_problem_preconditions_are_rejected_on_the_host(lib, bad, status, msg):
+    """The preconditions include/mg.h states for mg_problem (dims and block
+    extents >= 1 with block | dims; 4 <= m' <= 64, m' % 4 == 0, 6|Lambda| >= m';
+    1 <= k <= m'; xi > 0; a known precision) are checked before anything is
+    launched, with the status and a message; the workspace query answers 0."""
+    kw = dict(dims=[4, 4, 4, 4], block=[2, 2, 2, 2], m0=0.0, n_vec=8, k=4, mr_iters=2)
+    kw.update(bad)
+    pc = mg.Problem(**kw).c()
+    assert lib.mg_workspace_size(ctypes.byref(pc), mg.MG_CALL_SMOOTH) == 0
+    assert msg in lib.mg_last_error().decode()
+    fake = [ctypes.c_void_p(256 * (i + 1)) for i in range(6)]
+    st = lib.mg_smooth_testvecs(ctypes.byref(pc), fake[0], None, fake[1], fake[2], fake[3],
+                                1 << 30, None)
+    assert st == status, (bad, st, lib.mg_last_error())
+    st = lib.mg_chiral_truncate(ctypes.byref(pc), fake[0], fake[1], fake[2], None, fake[3],
+                                fake[4], 1 << 30, None)
+    assert st == status
+
+
+def test_workspace_too_small_and_aliasing_are_rejected(lib):
+    pc = mg.Problem(dims=[4, 4, 4, 4], block=[2, 2, 2, 2], m0=0.0, n_vec=8, k=4,
+                    mr_iters=2).c()
+    need = lib.mg_workspace_size(ctypes.byref(pc), mg.MG_CALL_SMOOTH)
+    fake = [ctypes.c_void_p(256 * (i + 1)) for i in range(6)]
+    st = lib.mg_smooth_testvecs(ctypes.byref(pc), fake[0], None, fake[1], fake[2], fake[3],
+                                need - 1, None)
+    assert st == 1 and b"workspace" in lib.mg_last_error()
+    st = lib.mg_apply_dirac(ctypes.byref(pc), fake[0], None, fake[1], fake[1], fake[3], need,
+                            None)
+    assert st == 1 and b"aliases" in lib.mg_last_error()
+    st = lib.mg_coarse_apply(ctypes.byref(pc), fake[0], fake[1], fake[2], fake[2], 8, None)
+    assert st == 1 and b"aliases" in lib.mg_last_error()
+    for nrhs in (0, 65):
+        st = lib.mg_coarse_apply(ctypes.byref(pc), fake[0], fake[1], fake[2], fake[3], nrhs, None)
+        assert st == 1 and b"nrhs" in lib.mg_last_error()
+    pc0 = mg.Problem(dims=[4, 4, 4, 4], block=[2, 2, 2, 2], m0=0.0, n_vec=8, k=4,
+                     mr_iters=0).c()
+    st = lib.mg_smooth_testvecs(ctypes.byref(pc0), fake[0], None, fake[1], fake[2], fake[3],
+                                1 << 30, None)
+    assert st == 1 and b"mr_iters" in lib.mg_last_error()
