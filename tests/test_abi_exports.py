@@ -180,3 +180,15 @@ def test_workspace_too_small_and_aliasing_are_rejected(lib):
     st = lib.mg_smooth_testvecs(ctypes.byref(pc0), fake[0], None, fake[1], fake[2], fake[3],
                                 1 << 30, None)
     assert st == 1 and b"mr_iters" in lib.mg_last_error()
+
+
+def test_static_truncation_rejects_oversized_problem_before_any_cuda_call(lib):
+    """mg_chiral_truncate_static refuses a problem whose truncation scratch
+    exceeds its built-in 64 MiB before it touches the device."""
+    pc = mg.Problem(dims=[16, 16, 16, 32], block=[4, 4, 4, 4], m0=0.0, n_vec=64, k=24,
+                    mr_iters=2).c()
+    assert lib.mg_workspace_size(ctypes.byref(pc), mg.MG_CALL_TRUNCATE) > 64 << 20
+    fake = [ctypes.c_void_p(256 * (i + 1)) for i in range(4)]
+    st = lib.mg_chiral_truncate_static(ctypes.byref(pc), fake[0], fake[1], fake[2], None,
+                                       fake[3], None)
+    assert st == 1 and b"built-in" in lib.mg_last_error()
