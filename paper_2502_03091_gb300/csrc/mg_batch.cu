@@ -176,7 +176,11 @@ mg_status mg_batch_create(const mg_level_desc* levels, int n, int n_streams, voi
   for (int i = 0; i < n; ++i) {
     const mg_level_desc& d = lv[i];
     Geom g;
-    if (make_geom(&d.prob, &g) != MG_OK) return MG_ERR_INVALID;
+    if (make_geom(&d.prob, &g) != MG_OK) {
+      char msg[320];
+      std::snprintf(msg, sizeof msg, "level %d: %s", i, mg_last_error());
+      return batch_fail(MG_ERR_INVALID, msg);
+    }
     if (!d.U || !d.psi0 || !d.psi || !d.Uk || !d.sigma || !d.blk_flags || !d.P || !d.X ||
         !d.Y || !d.ws_smooth || !d.ws_trunc) {
       char msg[96];

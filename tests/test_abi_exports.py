@@ -192,3 +192,29 @@ def test_static_truncation_rejects_oversized_problem_before_any_cuda_call(lib):
     st = lib.mg_chiral_truncate_static(ctypes.byref(pc), fake[0], fake[1], fake[2], None,
                                        fake[3], None)
     assert st == 1 and b"built-in" in lib.mg_last_error()
+
+
+def test_batch_descriptors_are_checked_before_any_cuda_call(lib):
+    """mg_batch_create validates its arguments and every level descriptor
+    (the problem and every array) before it tunes or captures anything."""
+    out = ctypes.c_void_p()
+    st = lib.mg_batch_create(None, 0, 0, None, ctypes.byref(out))
+    assert st == 1 and b"no levels" in lib.mg_last_error() and not out.value
+    good = mg.Problem(dims=[4, 4, 4, 4], block=[2, 2, 2, 2], m0=0.0, n_vec=8, k=4,
+                      mr_iters=2)
+    descs = (mg._LevelDesc * 2)()
+    for i, d in enumerate(descs):
+        d.prob = good.c()
+        for j, (name, t) in enumerate(mg._LevelDesc._fields_[1:]):
+            setattr(d, name, 256 * (16 * i + j + 1))
+    st = lib.mg_batch_create(descs, 2, 65, None, ctypes.byref(out))
+    assert st == 1 and b"64 streams" in lib.mg_last_error()
+    descs[1].psi = None
+    st = lib.mg_batch_create(descs, 2, 1, None, ctypes.byref(out))
+    assert st == 1 and b"level 1: NULL array" in lib.mg_last_error()
+    descs[1].psi = 4096
+    descs[0].prob = mg.Problem(dims=[4, 4, 4, 4], block=[3, 2, 2, 2], m0=0.0, n_vec=8, k=4,
+                               mr_iters=2).c()
+    st = lib.mg_batch_create(descs, 2, 1, None, ctypes.byref(out))
+    err = lib.mg_last_error()
+    assert st == 1 and b"level 0: " in err and b"does not divide" in err and not out.value
