@@ -218,3 +218,17 @@ def test_batch_descriptors_are_checked_before_any_cuda_call(lib):
     st = lib.mg_batch_create(descs, 2, 1, None, ctypes.byref(out))
     err = lib.mg_last_error()
     assert st == 1 and b"level 0: " in err and b"does not divide" in err and not out.value
+
+
+def test_generator_and_selftest_arguments_are_checked(lib):
+    pc = mg.Problem(dims=[4, 4, 4, 4], block=[2, 2, 2, 2], m0=0.0, n_vec=8, k=4,
+                    mr_iters=2).c()
+    fake = ctypes.c_void_p(256)
+    for eps in (-0.1, 1.5, float("nan")):
+        st = lib.mg_random_links(ctypes.byref(pc), ctypes.c_double(eps), fake, None)
+        assert st == 1 and b"eps" in lib.mg_last_error(), eps
+    assert lib.mg_random_links(ctypes.byref(pc), ctypes.c_double(0.2), None, None) == 1
+    assert lib.mg_random_starts(ctypes.byref(pc), None, None) == 1
+    for polls in (0, (1 << 20) + 1):
+        assert lib.mg_selftest_timeout(polls, None) == 1
+        assert b"polls" in lib.mg_last_error()
