@@ -57,7 +57,7 @@ struct SuspendTiming {
 };
 
 mg_status batch_fail(mg_status st, const char* what, cudaError_t e = cudaSuccess) {
-  char msg[256];
+  char msg[512];  // the size of the library's error message slot
   if (e != cudaSuccess)
     std::snprintf(msg, sizeof msg, "mg_batch: %s: %s", what, cudaGetErrorString(e));
   else
